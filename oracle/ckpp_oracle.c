@@ -1,0 +1,625 @@
+/*
+ * Cuckoo++ CPU oracle: a plain, slow, single-threaded C implementation of the
+ * method of "Cuckoo++ Hash Tables: High-Performance Hash Tables for Networking
+ * Applications" (Le Scouarnec, 2017).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path may call, link or load
+ * this file; only the tests, the smoke check and the bench's CPU-baseline leg
+ * use it. It shares no code, header or constant generator with the CUDA path.
+ *
+ * What it follows (paper sections):
+ *   Sec. 2     bucketized two-choice cuckoo table: 8 slots per bucket, tags in the
+ *              bucket, key/value in a separate array at an implicit index, lookup
+ *              = primary bucket, then secondary bucket, confirm the full key.
+ *   Sec. 2     insertion: free slot in the primary, else the secondary, else a
+ *              cuckoo path that moves entries to their alternative buckets.
+ *   Sec. 4.1   a 64-bit Bloom filter with two bit indices in every primary bucket
+ *              records the keys of that bucket stored in their secondary bucket;
+ *              a lookup reads the secondary only if both bits are set. A moved
+ *              counter counts those keys; deleting one decrements it and the
+ *              filter is reset to zero when it reaches zero. Moves along a cuckoo
+ *              path update filter and counter like an insertion (primary to
+ *              secondary) or a deletion (secondary to primary).
+ *   Sec. 4.2   16-bit expiration times; an entry is alive iff
+ *              (uint16)(expiry - now) < 1024; lookups ignore dead entries,
+ *              insertions reuse dead slots as if free; a full scan must run at
+ *              least every 64512 time units to delete dead entries.
+ *   Sec. 4.3   tags are 16-bit values derived from the primary hash.
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   hash      : the paper uses CityHash64; this project defines
+ *               H(key, s) = mix(mix(k0 ^ s) ^ k1) with mix = the SplitMix64
+ *               output finaliser (Steele, Lea, Flood, OOPSLA 2014), k0/k1 the
+ *               key's two little-endian 64-bit words. H1 uses the table seed,
+ *               H2 the seed xor 0x9E3779B97F4A7C15.
+ *   buckets   : b1 = ((H1 >> 32) * nb) >> 32, b2 likewise from H2 (multiply-shift
+ *               range reduction, Lemire 2019); if b2 == b1 then b2 = (b1 + 1) mod nb.
+ *   tag       : H1 & 0xFFFF.   Bloom bits: H2 & 63 and (H2 >> 6) & 63.
+ *   slot      : the lowest free (or dead) slot index is taken.
+ *   path      : breadth-first search over buckets from b1 then b2, slots in index
+ *               order, no bucket visited twice, at most 5 moves and 1024 nodes;
+ *               nothing found -> FULL and the table is unchanged.
+ *   upsert    : inserting a key already stored (alive or dead) overwrites value and
+ *               expiry in place; the status is UPDATED when the old entry was
+ *               alive, INSERTED otherwise.
+ *   delete    : DELETED when the key had a live entry, NOT_FOUND otherwise; a dead
+ *               entry found by a delete is removed all the same.
+ *   dead slot : reusing a dead slot first deletes its entry (counter upkeep on
+ *               that entry's primary bucket).
+ *   staleness : every timed call checks (uint32)(now - last_scan) <= 64512, where
+ *               last_scan is the time of the last expire scan (or of the first
+ *               timed call); otherwise it returns OC_ESTALE and does nothing.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* OC_MUTANT plants one known mistake (tests build each mutant and check that
+ * the pins catch it). 0, the default, is the oracle itself. */
+#ifndef OC_MUTANT
+#define OC_MUTANT 0
+#endif
+
+/* per-key outcomes (same numeric values as the library's public contract) */
+enum {
+  OC_INSERTED = 1,
+  OC_UPDATED = 2,
+  OC_FULL = 3,
+  OC_DELETED = 4,
+  OC_NOT_FOUND = 5
+};
+/* call-level errors */
+enum { OC_OK = 0, OC_EINVAL = -1, OC_ESTALE = -3 };
+
+#define OC_ALIVE_WINDOW 1024u  /* Sec. 4.2: expiry at most 1024 units ahead      */
+#define OC_MAX_STALE 64512u    /* Sec. 4.2: 65536 - 1024, the scan period bound   */
+#define OC_BFS_MAX_NODES 1024
+#define OC_BFS_MAX_DEPTH 5
+#define OC_SEED2_XOR 0x9E3779B97F4A7C15ULL
+
+typedef struct {
+  uint8_t key[16];
+  uint64_t value;
+  uint16_t tag;
+  uint16_t expiry;
+  uint8_t busy;
+  uint8_t in_secondary; /* this entry sits in its secondary bucket */
+} oc_slot;
+
+typedef struct {
+  uint64_t bloom; /* Sec. 4.1: 64-bit filter of this bucket's displaced keys */
+  uint32_t moved; /* Sec. 4.1: moved counter                                  */
+} oc_meta;
+
+typedef struct {
+  uint64_t nb;
+  uint32_t slots;
+  uint32_t timers;
+  uint64_t seed;
+  int have_epoch;
+  uint32_t last_scan;
+  oc_slot* slot; /* nb * slots, bucket-major: slot[b * slots + s] */
+  oc_meta* meta; /* nb */
+} oc_table;
+
+/* ---------------------------------------------------------------- hashing */
+
+/* SplitMix64 output finaliser (Steele, Lea, Flood, OOPSLA 2014). */
+uint64_t oc_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+static uint64_t load_le64(const uint8_t* p) {
+  uint64_t v = 0;
+  for (int i = 7; i >= 0; --i) v = (v << 8) | (uint64_t)p[i];
+  return v;
+}
+
+uint64_t oc_hash(const uint8_t* key, uint64_t s) {
+  uint64_t k0 = load_le64(key);
+  uint64_t k1 = load_le64(key + 8);
+  return oc_mix64(oc_mix64(k0 ^ s) ^ k1);
+}
+
+typedef struct {
+  uint64_t b1, b2;
+  uint16_t tag;
+  unsigned bit1, bit2;
+} oc_addr;
+
+static uint64_t reduce(uint64_t h, uint64_t nb) { return ((h >> 32) * nb) >> 32; }
+
+static oc_addr address_of(const oc_table* t, const uint8_t* key) {
+  oc_addr a;
+  uint64_t h1 = oc_hash(key, t->seed);
+  uint64_t h2 = oc_hash(key, t->seed ^ OC_SEED2_XOR);
+  a.b1 = reduce(h1, t->nb);
+  a.b2 = reduce(h2, t->nb);
+#if OC_MUTANT != 11
+  if (a.b2 == a.b1) a.b2 = (a.b1 + 1) % t->nb;
+#endif
+#if OC_MUTANT == 3
+  a.tag = (uint16_t)(h2 & 0xFFFF);
+#else
+  a.tag = (uint16_t)(h1 & 0xFFFF);
+#endif
+  a.bit1 = (unsigned)(h2 & 63);
+  a.bit2 = (unsigned)((h2 >> 6) & 63);
+  return a;
+}
+
+/* Exposed for tests: H1, H2, b1, b2, tag, bit1, bit2 for n keys. */
+void oc_address_batch(uint64_t nb, uint64_t seed, const uint8_t* keys, uint64_t n, uint64_t* h1,
+                      uint64_t* h2, uint64_t* b1, uint64_t* b2, uint16_t* tag, uint8_t* bit1,
+                      uint8_t* bit2) {
+  oc_table t;
+  memset(&t, 0, sizeof t);
+  t.nb = nb;
+  t.seed = seed;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint8_t* k = keys + 16 * i;
+    oc_addr a = address_of(&t, k);
+    if (h1) h1[i] = oc_hash(k, seed);
+    if (h2) h2[i] = oc_hash(k, seed ^ OC_SEED2_XOR);
+    if (b1) b1[i] = a.b1;
+    if (b2) b2[i] = a.b2;
+    if (tag) tag[i] = a.tag;
+    if (bit1) bit1[i] = (uint8_t)a.bit1;
+    if (bit2) bit2[i] = (uint8_t)a.bit2;
+  }
+}
+
+/* ----------------------------------------------------------------- timers */
+
+/* Sec. 4.2: alive iff the 16-bit difference expiry - now is below 1024. */
+int oc_alive(uint16_t expiry, uint32_t now) {
+  uint16_t d = (uint16_t)(expiry - (uint16_t)now);
+#if OC_MUTANT == 5
+  return d <= OC_ALIVE_WINDOW;
+#else
+  return d < OC_ALIVE_WINDOW;
+#endif
+}
+
+static int slot_alive(const oc_table* t, const oc_slot* e, uint32_t now) {
+  return !t->timers || oc_alive(e->expiry, now);
+}
+
+/* A slot an insertion may take: empty, or holding a dead entry (Sec. 4.2). */
+static int slot_free(const oc_table* t, const oc_slot* e, uint32_t now) {
+#if OC_MUTANT == 9
+  (void)now;
+  return !e->busy && t;
+#else
+  return !e->busy || !slot_alive(t, e, now);
+#endif
+}
+
+static int time_check(oc_table* t, uint32_t now) {
+  if (!t->timers) return OC_OK;
+  if (!t->have_epoch) {
+    t->have_epoch = 1;
+    t->last_scan = now;
+  }
+  if ((uint32_t)(now - t->last_scan) > OC_MAX_STALE) return OC_ESTALE;
+  return OC_OK;
+}
+
+/* ------------------------------------------------------------- the table */
+
+oc_table* oc_create(uint64_t nb, uint32_t slots, uint32_t timers, uint64_t seed) {
+  if (nb < 2 || nb > 0xFFFFFFFFULL) return NULL;
+  if (slots != 2 && slots != 4 && slots != 8) return NULL;
+  oc_table* t = (oc_table*)calloc(1, sizeof *t);
+  if (!t) return NULL;
+  t->nb = nb;
+  t->slots = slots;
+  t->timers = timers ? 1u : 0u;
+  t->seed = seed;
+  t->slot = (oc_slot*)calloc(nb * slots, sizeof(oc_slot));
+  t->meta = (oc_meta*)calloc(nb, sizeof(oc_meta));
+  if (!t->slot || !t->meta) {
+    free(t->slot);
+    free(t->meta);
+    free(t);
+    return NULL;
+  }
+  return t;
+}
+
+void oc_destroy(oc_table* t) {
+  if (!t) return;
+  free(t->slot);
+  free(t->meta);
+  free(t);
+}
+
+static oc_slot* at(const oc_table* t, uint64_t b, uint32_t s) { return &t->slot[b * t->slots + s]; }
+
+static int bloom_maybe(const oc_table* t, const oc_addr* a) {
+  uint64_t f = t->meta[a->b1].bloom;
+  return ((f >> a->bit1) & 1u) && ((f >> a->bit2) & 1u);
+}
+
+/* Sec. 4.1: storing a key in its secondary sets its two bits in the primary's
+ * filter and increments the primary's moved counter. */
+static void bloom_add(oc_table* t, const oc_addr* a) {
+  oc_meta* m = &t->meta[a->b1];
+#if OC_MUTANT == 1
+  m->bloom |= (1ULL << a->bit1);
+#else
+  m->bloom |= (1ULL << a->bit1) | (1ULL << a->bit2);
+#endif
+  m->moved += 1;
+}
+
+/* Sec. 4.1: removing a key from its secondary decrements the primary's counter;
+ * at zero the filter is reset to empty. */
+static void bloom_remove(oc_table* t, const oc_addr* a) {
+  oc_meta* m = &t->meta[a->b1];
+  m->moved -= 1;
+#if OC_MUTANT != 2
+  if (m->moved == 0) m->bloom = 0;
+#endif
+}
+
+/* Remove whatever entry occupies (b, s), with counter upkeep. */
+static void remove_entry(oc_table* t, uint64_t b, uint32_t s) {
+  oc_slot* e = at(t, b, s);
+  if (!e->busy) return;
+#if OC_MUTANT != 7
+  if (e->in_secondary) {
+    oc_addr a = address_of(t, e->key);
+    bloom_remove(t, &a);
+  }
+#endif
+  memset(e, 0, sizeof *e);
+}
+
+/* Find the slot of bucket b holding key (alive or dead), or -1. */
+static int find_in_bucket(const oc_table* t, uint64_t b, const uint8_t* key, uint16_t tag) {
+  for (uint32_t s = 0; s < t->slots; ++s) {
+    const oc_slot* e = at(t, b, s);
+    if (e->busy && e->tag == tag && memcmp(e->key, key, 16) == 0) return (int)s;
+  }
+  return -1;
+}
+
+/* Locate key: the primary first, the secondary only when the filter allows. */
+static int locate(const oc_table* t, const uint8_t* key, const oc_addr* a, uint64_t* bucket) {
+  int s = find_in_bucket(t, a->b1, key, a->tag);
+  if (s >= 0) {
+    *bucket = a->b1;
+    return s;
+  }
+#if OC_MUTANT == 8
+  if (!bloom_maybe(t, a)) {
+#else
+  if (bloom_maybe(t, a)) {
+#endif
+    s = find_in_bucket(t, a->b2, key, a->tag);
+    if (s >= 0) {
+      *bucket = a->b2;
+      return s;
+    }
+  }
+  return -1;
+}
+
+static int lowest_free(const oc_table* t, uint64_t b, uint32_t now) {
+  for (uint32_t s = 0; s < t->slots; ++s)
+    if (slot_free(t, at(t, b, s), now)) return (int)s;
+  return -1;
+}
+
+static void store(oc_table* t, uint64_t b, uint32_t s, const uint8_t* key, uint64_t value,
+                  uint16_t expiry, const oc_addr* a) {
+  oc_slot* e = at(t, b, s);
+  memcpy(e->key, key, 16);
+  e->value = value;
+  e->tag = a->tag;
+  e->expiry = t->timers ? expiry : 0;
+  e->busy = 1;
+  e->in_secondary = (b == a->b2) ? 1 : 0;
+  if (e->in_secondary) bloom_add(t, a);
+}
+
+/* Move the entry at (x, s) to the free slot (y, u); y is its other bucket.
+ * Sec. 4.1: a primary-to-secondary move acts like an insertion in the filter,
+ * a secondary-to-primary move like a deletion. */
+static void move_entry(oc_table* t, uint64_t x, uint32_t s, uint64_t y, uint32_t u) {
+  oc_slot moved = *at(t, x, s);
+  oc_addr a = address_of(t, moved.key);
+  if (moved.in_secondary) bloom_remove(t, &a);
+  memset(at(t, x, s), 0, sizeof(oc_slot));
+  oc_slot* d = at(t, y, u);
+  *d = moved;
+#if OC_MUTANT != 6
+  d->in_secondary = (y == a.b2) ? 1 : 0;
+#endif
+  if (d->in_secondary) bloom_add(t, &a);
+}
+
+static uint64_t other_bucket(const oc_table* t, const oc_slot* e, uint64_t here) {
+  oc_addr a = address_of(t, e->key);
+  return here == a.b1 ? a.b2 : a.b1;
+}
+
+typedef struct {
+  uint64_t bucket;
+  int parent;
+  uint32_t slot_in_parent; /* slot of the parent whose entry moves here */
+  int depth;
+} bfs_node;
+
+/* Breadth-first search for a cuckoo path (Sec. 2): returns the node index whose
+ * bucket has a free slot (in *free_slot), or -1. */
+static int bfs(const oc_table* t, const oc_addr* a, uint32_t now, bfs_node* q, uint32_t* free_slot) {
+  int n = 0;
+  q[n++] = (bfs_node){a->b1, -1, 0, 0};
+  q[n++] = (bfs_node){a->b2, -1, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    int f = lowest_free(t, q[i].bucket, now);
+    if (f >= 0) {
+      *free_slot = (uint32_t)f;
+      return i;
+    }
+    if (q[i].depth >= OC_BFS_MAX_DEPTH) continue;
+    for (uint32_t s = 0; s < t->slots && n < OC_BFS_MAX_NODES; ++s) {
+      uint64_t y = other_bucket(t, at(t, q[i].bucket, s), q[i].bucket);
+      int seen = 0;
+      for (int j = 0; j < n && !seen; ++j) seen = (q[j].bucket == y);
+      if (!seen) q[n++] = (bfs_node){y, i, s, q[i].depth + 1};
+    }
+  }
+  return -1;
+}
+
+static int insert_one(oc_table* t, const uint8_t* key, uint64_t value, uint32_t now, uint32_t ttl) {
+  oc_addr a = address_of(t, key);
+  uint16_t expiry = (uint16_t)(now + ttl);
+  uint64_t b;
+  int s = locate(t, key, &a, &b);
+  if (s >= 0) { /* upsert in place */
+    oc_slot* e = at(t, b, (uint32_t)s);
+    int was_alive = slot_alive(t, e, now);
+    e->value = value;
+    if (t->timers) e->expiry = expiry;
+#if OC_MUTANT == 10
+    (void)was_alive;
+    return OC_UPDATED;
+#else
+    return was_alive ? OC_UPDATED : OC_INSERTED;
+#endif
+  }
+  s = lowest_free(t, a.b1, now);
+  if (s >= 0) {
+    remove_entry(t, a.b1, (uint32_t)s);
+    store(t, a.b1, (uint32_t)s, key, value, expiry, &a);
+    return OC_INSERTED;
+  }
+  s = lowest_free(t, a.b2, now);
+  if (s >= 0) {
+    remove_entry(t, a.b2, (uint32_t)s);
+    store(t, a.b2, (uint32_t)s, key, value, expiry, &a);
+    return OC_INSERTED;
+  }
+  bfs_node q[OC_BFS_MAX_NODES];
+  uint32_t hole = 0;
+  int end = bfs(t, &a, now, q, &hole);
+  if (end < 0) return OC_FULL;
+  /* Walk the path backwards: each entry moves into the hole made ahead of it. */
+  remove_entry(t, q[end].bucket, hole);
+  int node = end;
+  while (q[node].parent >= 0) {
+    int par = q[node].parent;
+    move_entry(t, q[par].bucket, q[node].slot_in_parent, q[node].bucket, hole);
+    hole = q[node].slot_in_parent;
+    node = par;
+  }
+  store(t, q[node].bucket, hole, key, value, expiry, &a);
+  return OC_INSERTED;
+}
+
+/* ---------------------------------------------------------- batched calls
+ * A batch is processed key by key in index order (sequential semantics). */
+
+int oc_insert(oc_table* t, const uint8_t* keys, const uint64_t* values, uint64_t n, uint32_t now,
+              uint32_t ttl, uint8_t* status) {
+  if (!t || (n && (!keys || !values || !status)) || ttl >= OC_ALIVE_WINDOW) return OC_EINVAL;
+  int rc = time_check(t, now);
+  if (rc) return rc;
+  for (uint64_t i = 0; i < n; ++i) status[i] = (uint8_t)insert_one(t, keys + 16 * i, values[i], now, ttl);
+  return OC_OK;
+}
+
+int oc_lookup(oc_table* t, const uint8_t* keys, uint64_t n, uint32_t now, uint32_t refresh_ttl,
+              uint64_t* values, uint8_t* found) {
+  if (!t || (n && (!keys || !values || !found)) || refresh_ttl >= OC_ALIVE_WINDOW) return OC_EINVAL;
+  int rc = time_check(t, now);
+  if (rc) return rc;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint8_t* k = keys + 16 * i;
+    oc_addr a = address_of(t, k);
+    uint64_t b;
+    int s = locate(t, k, &a, &b);
+    values[i] = 0;
+    found[i] = 0;
+    if (s < 0) continue;
+    oc_slot* e = at(t, b, (uint32_t)s);
+    if (!slot_alive(t, e, now)) continue; /* Sec. 4.2: dead entries are ignored */
+    values[i] = e->value;
+    found[i] = 1;
+    if (t->timers && refresh_ttl) e->expiry = (uint16_t)(now + refresh_ttl);
+  }
+  return OC_OK;
+}
+
+int oc_delete(oc_table* t, const uint8_t* keys, uint64_t n, uint32_t now, uint8_t* status) {
+  if (!t || (n && (!keys || !status))) return OC_EINVAL;
+  int rc = time_check(t, now);
+  if (rc) return rc;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint8_t* k = keys + 16 * i;
+    oc_addr a = address_of(t, k);
+    uint64_t b;
+    int s = locate(t, k, &a, &b);
+    if (s < 0) {
+      status[i] = OC_NOT_FOUND;
+      continue;
+    }
+    int was_alive = slot_alive(t, at(t, b, (uint32_t)s), now);
+    remove_entry(t, b, (uint32_t)s);
+    status[i] = was_alive ? OC_DELETED : OC_NOT_FOUND;
+  }
+  return OC_OK;
+}
+
+/* Sec. 4.2: scan every bucket and delete dead entries. Returns the count, or a
+ * negative error. */
+int64_t oc_expire(oc_table* t, uint32_t now) {
+  if (!t) return OC_EINVAL;
+  int rc = time_check(t, now);
+  if (rc) return rc;
+  int64_t n = 0;
+  if (t->timers) {
+    for (uint64_t b = 0; b < t->nb; ++b)
+      for (uint32_t s = 0; s < t->slots; ++s) {
+        oc_slot* e = at(t, b, s);
+        if (e->busy && !oc_alive(e->expiry, now)) {
+          remove_entry(t, b, s);
+          ++n;
+        }
+      }
+  }
+  t->last_scan = now;
+  t->have_epoch = 1;
+  return n;
+}
+
+/* -------------------------------------------------- inspection for tests */
+
+/* Number of occupied slots (alive or dead). */
+uint64_t oc_size(const oc_table* t) {
+  uint64_t n = 0;
+  for (uint64_t i = 0; i < t->nb * t->slots; ++i) n += t->slot[i].busy;
+  return n;
+}
+
+/* Copy out every occupied slot: key, value, expiry, bucket, slot, in_secondary. */
+uint64_t oc_dump(const oc_table* t, uint8_t* keys, uint64_t* values, uint16_t* expiry, uint64_t* bucket,
+                 uint8_t* slot, uint8_t* in_secondary) {
+  uint64_t n = 0;
+  for (uint64_t b = 0; b < t->nb; ++b)
+    for (uint32_t s = 0; s < t->slots; ++s) {
+      const oc_slot* e = at(t, b, s);
+      if (!e->busy) continue;
+      if (keys) memcpy(keys + 16 * n, e->key, 16);
+      if (values) values[n] = e->value;
+      if (expiry) expiry[n] = e->expiry;
+      if (bucket) bucket[n] = b;
+      if (slot) slot[n] = (uint8_t)s;
+      if (in_secondary) in_secondary[n] = e->in_secondary;
+      ++n;
+    }
+  return n;
+}
+
+void oc_meta_dump(const oc_table* t, uint64_t* bloom, uint32_t* moved) {
+  for (uint64_t b = 0; b < t->nb; ++b) {
+    bloom[b] = t->meta[b].bloom;
+    moved[b] = t->meta[b].moved;
+  }
+}
+
+/* Count, for n lookup keys, how many read the secondary bucket (filter said
+ * maybe after a primary miss) and how many key/value records were compared.
+ * Lookups are not applied (no refresh). */
+void oc_lookup_probe_counts(const oc_table* t, const uint8_t* keys, uint64_t n, uint32_t now,
+                            uint64_t* n_secondary_reads, uint64_t* n_record_reads) {
+  uint64_t sec = 0, rec = 0;
+  (void)now;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint8_t* k = keys + 16 * i;
+    oc_addr a = address_of(t, k);
+    int hit = 0;
+    for (uint32_t s = 0; s < t->slots && !hit; ++s) {
+      const oc_slot* e = at(t, a.b1, s);
+      if (e->busy && e->tag == a.tag) {
+        ++rec;
+        hit = memcmp(e->key, k, 16) == 0;
+      }
+    }
+    if (hit || !bloom_maybe(t, &a)) continue;
+    ++sec;
+    for (uint32_t s = 0; s < t->slots && !hit; ++s) {
+      const oc_slot* e = at(t, a.b2, s);
+      if (e->busy && e->tag == a.tag) {
+        ++rec;
+        hit = memcmp(e->key, k, 16) == 0;
+      }
+    }
+  }
+  *n_secondary_reads = sec;
+  *n_record_reads = rec;
+}
+
+/* Check the structural invariants of Sec. 2 and Sec. 4.1. Returns 0 when all
+ * hold, else a positive code naming the first violated one:
+ *  1 an entry sits in neither of its two buckets
+ *  2 in_secondary disagrees with the bucket the entry sits in
+ *  3 a stored tag differs from the key's tag
+ *  4 a secondary-resident key's two bits are not set in its primary's filter
+ *  5 a moved counter differs from the number of its displaced keys
+ *  6 a key is stored twice
+ *  7 a zero counter with a non-empty filter (the reset rule) */
+int oc_check_invariants(const oc_table* t, int check_reset, uint64_t* bad_index) {
+  uint64_t total = t->nb * t->slots;
+  uint32_t* count = (uint32_t*)calloc(t->nb, sizeof(uint32_t));
+  if (!count) return -1;
+  int rc = 0;
+  for (uint64_t i = 0; i < total && !rc; ++i) {
+    const oc_slot* e = &t->slot[i];
+    if (!e->busy) continue;
+    uint64_t b = i / t->slots;
+    oc_addr a = address_of(t, e->key);
+    if (b != a.b1 && b != a.b2) rc = 1;
+    else if (e->in_secondary != (b == a.b2)) rc = 2;
+    else if (e->tag != a.tag) rc = 3;
+    else if (e->in_secondary && !bloom_maybe(t, &a)) rc = 4;
+    if (rc) *bad_index = i;
+    if (e->in_secondary) count[a.b1] += 1;
+  }
+  for (uint64_t b = 0; b < t->nb && !rc; ++b) {
+    if (count[b] != t->meta[b].moved) {
+      rc = 5;
+      *bad_index = b;
+    } else if (check_reset && count[b] == 0 && t->meta[b].bloom != 0) {
+      rc = 7;
+      *bad_index = b;
+    }
+  }
+  free(count);
+  if (rc) return rc;
+  /* duplicates: a key can only repeat within its own two buckets */
+  for (uint64_t i = 0; i < total; ++i) {
+    const oc_slot* e = &t->slot[i];
+    if (!e->busy) continue;
+    oc_addr a = address_of(t, e->key);
+    uint64_t bs[2] = {a.b1, a.b2};
+    for (int k = 0; k < 2; ++k)
+      for (uint32_t s = 0; s < t->slots; ++s) {
+        uint64_t j = bs[k] * t->slots + s;
+        if (j != i && t->slot[j].busy && memcmp(t->slot[j].key, e->key, 16) == 0) {
+          *bad_index = i;
+          return 6;
+        }
+      }
+  }
+  return 0;
+}
+
+uint64_t oc_nb(const oc_table* t) { return t->nb; }
+uint32_t oc_slots(const oc_table* t) { return t->slots; }

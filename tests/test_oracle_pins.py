@@ -1,0 +1,168 @@
+"""The CPU oracle against its pins (no GPU).
+
+The oracle is what the CUDA path is checked against, so it is itself pinned
+to things other than itself: published SplitMix64 outputs, the timer arithmetic
+of Sec. 4.2, properties of the hash readings, a brute-force list map on tiny
+tables, the structural invariants of Sec. 2 / Sec. 4.1, and the statistics the
+paper prints (Fig. 2, Fig. 5, Table 2). A mutation test plants known mistakes
+in the oracle and checks that these pins catch every one.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as P
+from oracle.odef import MapTable
+from paper_1712_09624_gb300 import workload as W
+
+
+@pytest.fixture(scope="module")
+def L():
+    return oracle.lib()
+
+
+@pytest.mark.parametrize("check", P.ALL_CHECKS, ids=lambda c: c.__name__)
+def test_pin(L, check):
+    assert check(L) == []
+
+
+# mutant id -> planted mistake (see OC_MUTANT in the oracle source)
+MUTANTS = {
+    1: "filter insertion sets only one of the two bits",
+    2: "filter never reset when the moved counter reaches zero",
+    3: "tag taken from the secondary hash",
+    5: "alive test uses <= 1024",
+    6: "in_secondary flag not updated on a cuckoo move",
+    7: "removal forgets the moved counter",
+    8: "lookup filter test inverted",
+    9: "dead slots not reused by insertion",
+    10: "upsert always reports UPDATED",
+    11: "b2 may equal b1",
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS), ids=lambda m: f"m{m}")
+def test_pins_catch_planted_mistake(tmp_path, mutant):
+    Lm = oracle.load(oracle.build(out=str(tmp_path / f"mut{mutant}.so"), mutant=mutant))
+    failures = []
+    for check in P.ALL_CHECKS:
+        failures += check(Lm)
+    assert failures, f"no pin caught mutant {mutant}: {MUTANTS[mutant]}"
+
+
+def test_odef_matches_oracle_on_fill_and_mixed_ops(L):
+    """O-ckpp against the plain dict definition on a few thousand keys."""
+    nb = 512
+    t = oracle.Table(nb, 8, True, 9)
+    d = MapTable(timers=True)
+    f = W.fill(9, int(0.93 * nb * 8))
+    now = 50
+    for lo in range(0, f.keys.shape[0], 700):
+        k, v = f.keys[lo:lo + 700], f.values[lo:lo + 700]
+        assert (t.insert(k, v, now, 300) == d.insert(k, v, now, 300)).all()
+        now += 40
+        q = W.lookup_batch(9, 500, f, 0.3, batch_id=lo).keys
+        a, b = t.lookup(q, now, 0), d.lookup(q, now, 0)
+        assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
+        dk = f.keys[lo:lo + 50]
+        assert (t.delete(dk, now) == d.delete(dk, now)).all()
+        assert t.check() == 0
+    dump = t.dump()
+    live_t = {bytes(k): int(v) for k, v, e in zip(dump["key"], dump["value"], dump["expiry"])
+              if oracle.alive(int(e), now)}
+    live_d = {k: v for k, (v, e) in d.live(now).items()}
+    assert live_t == live_d
+
+
+def test_estale_window(L):
+    """Sec. 4.2: the table must be scanned at least every 64512 units."""
+    t = oracle.Table(4, 8, True, 1)
+    k = W.make_keys(1, 40, 2)
+    t.insert(k[:1], np.array([1], np.uint64), 100, 10)       # first timed call sets the epoch
+    t.lookup(k, 100 + 64512)                                  # exactly at the bound: allowed
+    with pytest.raises(oracle.OracleError, match="ESTALE"):
+        t.lookup(k, 100 + 64513)
+    assert t.expire(100 + 64000) == 1                         # scan deletes the dead entry
+    t.lookup(k, 100 + 64000 + 64512)
+    with pytest.raises(oracle.OracleError, match="ESTALE"):
+        t.insert(k[1:], np.array([2], np.uint64), 100 + 64000 + 64513, 1)
+
+
+def test_no_timers_ignores_time(L):
+    t = oracle.Table(4, 8, False, 1)
+    k = W.make_keys(1, 41, 3)
+    t.insert(k, np.arange(3, dtype=np.uint64), 0, 0)
+    v, f = t.lookup(k, 10**9)
+    assert f.all() and (v == np.arange(3)).all()
+
+
+def test_bad_geometry_rejected(L):
+    for nb, s in ((1, 8), (0, 8), (4, 3), (4, 16), (2**32, 8)):
+        with pytest.raises(oracle.OracleError):
+            oracle.Table(nb, s)
+
+
+# ---------------------------------------------------- paper statistics
+
+@pytest.fixture(scope="module")
+def fill_stats(L):
+    """Fill a 2^17 x 8 table step by step and record the statistics the paper
+    plots (Fig. 2: fraction in secondary; Fig. 5: moved counters; Table 2: FPR)."""
+    nb = 1 << 17
+    cap = nb * 8
+    t = oracle.Table(nb, 8, False, 7)
+    f = W.fill(7, int(0.95 * cap))
+    neg = W.make_keys(7, W.STREAM_NEGATIVE_KEYS, 200000)
+    out, done = {}, 0
+    for lf in (0.45, 0.6, 0.7, 0.8, 0.95):
+        m = int(lf * cap)
+        st = t.insert(f.keys[done:m], f.values[done:m])
+        assert (st == oracle.INSERTED).all()
+        done = m
+        bloom, moved = t.meta()
+        pop = np.unpackbits(bloom.view(np.uint8)).reshape(-1, 64).sum(1).astype(np.float64)
+        sec_reads, _ = t.probe_counts(neg)
+        hist = np.bincount(moved)
+        out[lf] = dict(
+            f_sec=float(t.dump()["in_secondary"].mean()),
+            fpr_exact=float(((pop / 64.0) ** 2).mean()),
+            fpr_closed=float(sum(hist[c] / nb * (1 - (1 - 1 / 64) ** (2 * c)) ** 2 for c in range(len(hist)))),
+            fpr_measured=sec_reads / neg.shape[0],
+            moved_zero=float((moved == 0).mean()),
+        )
+    assert t.check() == 0
+    return out
+
+
+def test_fig2_fraction_in_secondary(fill_stats):
+    """Sec. 3 / Fig. 2 (8 slots): almost none below LF 0.5, 6% at 0.7, 16% at 0.95.
+    The paper used CityHash64 on a 32M table; the bands allow for the different hash."""
+    assert fill_stats[0.45]["f_sec"] < 0.01
+    assert 0.03 < fill_stats[0.7]["f_sec"] < 0.08
+    assert 0.13 < fill_stats[0.95]["f_sec"] < 0.20
+
+
+def test_table2_bloom_false_positive_rate(fill_stats):
+    """Table 2: FPR 0.0002 / 0.001 / 0.003 at LF 0.6 / 0.8 / 0.95, within x1.6."""
+    for lf, paper in ((0.6, 0.0002), (0.8, 0.001), (0.95, 0.003)):
+        got = fill_stats[lf]["fpr_exact"]
+        assert paper / 1.6 < got < paper * 1.6, (lf, got)
+
+
+def test_fpr_closed_form_and_measured_pass_rate(fill_stats):
+    """The negative-lookup filter pass rate equals mean((popcount/64)^2) (two
+    independent uniform bit indices), and the popcount follows from the moved
+    counters as 64 (1 - (1 - 1/64)^(2c))."""
+    for lf, s in fill_stats.items():
+        exp = s["fpr_exact"]
+        sd = (exp / 200000) ** 0.5
+        assert abs(s["fpr_measured"] - exp) < 4.5 * sd + 1e-6, (lf, s)
+        assert abs(s["fpr_closed"] - exp) <= 0.05 * exp + 1e-6, (lf, s)
+
+
+def test_fig5_moved_counter_zero(fill_stats):
+    """Sec. 4.1 / Fig. 5: at LF 0.95 about half the buckets (the paper: more than
+    50%) have a zero moved counter; this hash gives ~47%, so the band is 0.40-0.60."""
+    assert 0.40 < fill_stats[0.95]["moved_zero"] < 0.60
+    assert fill_stats[0.6]["moved_zero"] > fill_stats[0.95]["moved_zero"]
