@@ -1,0 +1,430 @@
+"""Bulk-lookup throughput of the GB300 Cuckoo++ table.
+
+Workload (the at-scale configuration): 2^24 buckets x 8 slots (134,217,728
+slots) filled to load factor 0.9 with 120,795,955 random 5-tuple keys (value =
+insertion index), then bulk_lookup batches of 2^24 keys with each key negative
+with probability 0.5 (Bernoulli), positives drawn uniformly from the inserted
+keys. A step is one bulk_lookup of one such batch, inputs resident in HBM.
+The table (4.8 GB) and the key batch (256 MB) are both larger than L2, so no
+L2 flush is needed between steps.
+
+One JSON line on rank 0. Beside the headline `value` it reports:
+  e2e        the same lookups through the C ABI from pinned host buffers, the
+             host->device key copy and device->host result copies timed inside;
+  roofline   algorithmic bytes of the lookup kernel (32 B per bucket sector and
+             per key/value record the method reads, counted on the batch by the
+             library's probe-count kernel, plus 25 B of key/result streaming)
+             over its measured duration, against the measured HBM copy peak;
+  pos / neg  the same measurement on all-positive and all-negative batches;
+  mutations  bulk_insert / bulk_delete / expire throughput on the same table;
+  cpu_baseline  the CPU oracle's lookup rate on a bounded sample (rank 0, N=1).
+
+--impl reference times the CPU oracle itself (the reference arm of this
+build): it builds the oracle table of the same workload and times its lookups,
+each step a bounded sample.
+
+Multi-GPU (torchrun): every rank builds and serves its own table (independent,
+share-nothing tables as in the paper's multi-core setting), no collective on
+the data path; value = lookups of all ranks / max time over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Glookups/s at 100M entries LF0.9 (pos/neg), % of random-access HBM roofline"
+UNIT = "Glookups/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--log2-buckets", type=int, default=24)
+    p.add_argument("--load-factor", type=float, default=0.9)
+    p.add_argument("--neg-rate", type=float, default=0.5)
+    p.add_argument("--log2-batch", type=int, default=24)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-side", action="store_true", help="skip pos/neg/e2e/mutation side measurements")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle timing budget")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_src: str, summary: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (sha256 match), else None."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, kernel_src), "rb").read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples with host timestamps."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        inside = [s for t, s in self.samples if t0 <= t <= t1]
+        window = "timed"
+        if not inside:
+            inside = [s for t, s in self.samples if t <= t1]
+            window = "before-and-during"
+        if not inside:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[0]) for s in inside if num(s[0]) is not None]
+        mx = [num(s[1]) for s in inside if num(s[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in inside for i in range(4) if len(s) > 4 + i and "Active" in s[4 + i]
+                          and "Not" not in s[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside), "window": window}
+
+
+# ------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    from paper_1712_09624_gb300 import workload as W
+    from paper_1712_09624_gb300.table import FlowTable
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nb = 1 << args.log2_buckets
+    n_fill = int(args.load_factor * nb * 8)
+    n = 1 << args.log2_batch
+    seed = args.seed + 1000 * rank  # independent tables per rank
+    stream = torch.cuda.current_stream()
+
+    fill = W.fill(seed, n_fill)
+    table = FlowTable(nb, timers=False, seed=seed, device=dev)
+    chunk = 1 << 24
+    ins_times = []
+    for lo in range(0, n_fill, chunk):
+        k = torch.from_numpy(fill.keys[lo:lo + chunk]).to(dev)
+        v = torch.from_numpy(fill.values[lo:lo + chunk].view(np.int64)).to(dev)
+        st = torch.empty(k.shape[0], dtype=torch.uint8, device=dev)
+        ws = table.workspace(k.shape[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K.ckpp_bulk_insert(table.handle, k, v, st, ws, 0, 0, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ins_times.append((k.shape[0], e0.elapsed_time(e1) / 1e3))
+        if not bool((st == K.ST_INSERTED).all()):
+            raise RuntimeError("fill reported a status other than INSERTED")
+    if table.sync_status() != 0:
+        raise RuntimeError("device wait gave up during the fill")
+
+    def batch(neg, bid):
+        q = W.lookup_batch(seed, n, fill, neg, batch_id=bid)
+        return q, torch.from_numpy(q.keys).to(dev)
+
+    q, keys = batch(args.neg_rate, 0)
+    out_v = torch.empty(n, dtype=torch.int64, device=dev)
+    out_f = torch.empty(n, dtype=torch.bool, device=dev)
+
+    def lookup(kk, ov, of):
+        K.ckpp_bulk_lookup(table.handle, kk, ov, of, 0, 0, stream)
+
+    # correctness of the timed configuration against the map definition
+    lookup(keys, out_v, out_f)
+    torch.cuda.synchronize()
+    if not (out_f.cpu().numpy() == q.expect_found).all() or \
+            not (out_v.cpu().numpy().view(np.uint64) == q.expect_value).all():
+        raise RuntimeError("lookup results differ from the workload's key -> value map")
+    counts = table.probe_counts(keys).cpu().numpy()
+    alg_bytes = 32.0 * float(counts.sum()) + 25.0 * n
+
+    def timed(kk, ov, of, steps, warmup):
+        for _ in range(warmup):
+            lookup(kk, ov, of)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.time()
+        e0.record(stream)
+        for _ in range(steps):
+            lookup(kk, ov, of)
+        e1.record(stream)
+        e1.synchronize()
+        t1 = time.time()
+        if world > 1:
+            torch.distributed.barrier()
+        return e0.elapsed_time(e1) / 1e3, t0, t1
+
+    sampler = ClockSampler(local_rank).start() if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    secs, t0, t1 = timed(keys, out_v, out_f, args.steps, args.warmup)
+    time.sleep(0.15 if sampler else 0)
+    if sampler:
+        sampler.stop()
+    if world > 1:
+        t = torch.tensor([secs], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs = float(t.item())
+    per_launch = secs / args.steps
+    value = world * n * args.steps / secs / 1e9
+
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / per_launch / 1e9
+    traffic = profiled_traffic("paper_1712_09624_gb300/csrc/lookup.cu", "lookup_2e24_lf09.md")
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "plain Cuckoo++ at scale: 2^24 buckets x 8 slots, LF 0.9, 16M-key bulk_lookup",
+                   "n_buckets": nb, "slots": 8, "entries": n_fill, "load_factor": args.load_factor,
+                   "batch": n, "neg_rate": args.neg_rate, "timers": False,
+                   "l2": "inputs larger than L2 (table 4.8 GB, keys 256 MB); no flush"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "alg_bytes_per_lookup": round(alg_bytes / n, 3),
+                     "reads_per_lookup": {"primary": float(counts[0] / n), "secondary": float(counts[1] / n),
+                                          "record": float(counts[2] / n)}},
+        "gpu_launches": args.steps,
+    }
+    if sampler:
+        out["clocks"] = sampler.summary(t0, t1)
+
+    if rank == 0 and not args.no_side:
+        side = {}
+        for name, neg in (("pos", 0.0), ("neg", 1.0)):
+            qq, kk = batch(neg, 1 + int(neg))
+            s, _, _ = timed(kk, out_v, out_f, max(10, args.steps // 4), 3)
+            c = table.probe_counts(kk).cpu().numpy()
+            b = 32.0 * float(c.sum()) + 25.0 * n
+            side[name] = {"value": round(n * max(10, args.steps // 4) / s / 1e9, 4), "unit": UNIT,
+                          "alg_bytes_per_lookup": round(b / n, 3),
+                          "frac": round(b / (s / max(10, args.steps // 4)) / 1e9 / peak, 4)}
+        out.update(side)
+        out["e2e"] = e2e_lookup(args, table, q, dev, stream)
+        out["mutations"] = mutation_rates(table, dev, stream, ins_times, seed)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, fill, q, nb, seed)
+    return out
+
+
+def e2e_lookup(args, table, q, dev, stream):
+    """Lookups through the C ABI from pinned host memory: each step copies the
+    keys host->device, looks them up and copies values and flags back."""
+    import torch
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    n = q.keys.shape[0]
+    h_keys = torch.from_numpy(q.keys).pin_memory()
+    h_vals = torch.empty(n, dtype=torch.int64).pin_memory()
+    h_found = torch.empty(n, dtype=torch.bool).pin_memory()
+    d_keys = torch.empty((n, 16), dtype=torch.uint8, device=dev)
+    d_vals = torch.empty(n, dtype=torch.int64, device=dev)
+    d_found = torch.empty(n, dtype=torch.bool, device=dev)
+    steps = max(5, args.steps // 10)
+
+    def one():
+        d_keys.copy_(h_keys, non_blocking=True)
+        K.ckpp_bulk_lookup(table.handle, d_keys, d_vals, d_found, 0, 0, stream)
+        h_vals.copy_(d_vals, non_blocking=True)
+        h_found.copy_(d_found, non_blocking=True)
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    ok = bool((h_found.numpy() == q.expect_found).all())
+    return {"value": round(n * steps / secs / 1e9, 4), "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+            "d2h_bytes_per_step": 9 * n, "steps": steps, "results_match": ok}
+
+
+def mutation_rates(table, dev, stream, ins_times, seed):
+    """Insert (during the fill), delete and expire rates on the same table."""
+    import torch
+
+    from paper_1712_09624_gb300 import workload as W
+    from paper_1712_09624_gb300.table import FlowTable
+    n_ins = sum(c for c, _ in ins_times)
+    t_ins = sum(s for _, s in ins_times)
+    out = {"insert_fill_Mops": round(n_ins / t_ins / 1e6, 1)}
+    # delete + reinsert of 1M resident keys
+    fill_keys = W.make_keys(seed, W.STREAM_INSERT_KEYS, 1 << 20)
+    k = torch.from_numpy(fill_keys).to(dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    st = table.delete(k, 0, stream)
+    e[1].record(stream)
+    st2 = table.insert(k, torch.arange(k.shape[0], dtype=torch.int64, device=dev), 0, 0, stream)
+    e[2].record(stream)
+    e[2].synchronize()
+    out["delete_Mops"] = round(k.shape[0] / (e[0].elapsed_time(e[1]) / 1e3) / 1e6, 1)
+    out["insert_at_lf0.9_Mops"] = round(k.shape[0] / (e[1].elapsed_time(e[2]) / 1e3) / 1e6, 1)
+    out["delete_ok"] = bool((st == 4).all())
+    out["reinsert_ok"] = bool((st2 == 1).all())
+    # expiration scan over a timers table of the same bucket count
+    tt = FlowTable(table.n_buckets, timers=True, seed=seed, device=dev)
+    e[0].record(stream)
+    tt.expire(100, stream)
+    e[1].record(stream)
+    e[1].synchronize()
+    secs = e[0].elapsed_time(e[1]) / 1e3
+    out["expire_scan_GBs"] = round(table.n_buckets * 64 / secs / 1e9, 1)
+    del tt
+    return out
+
+
+def cpu_baseline(args, fill, q, nb, seed):
+    """The CPU oracle (plain single-threaded C) on the same table and a bounded
+    sample of the same lookup batch."""
+    import oracle
+    o = oracle.Table(nb, 8, False, seed)
+    t0 = time.time()
+    o.insert(fill.keys, fill.values)
+    build_s = time.time() - t0
+    sample = q.keys[: 1 << 21]
+    done, t0 = 0, time.time()
+    while time.time() - t0 < args.cpu_seconds:
+        o.lookup(sample)
+        done += sample.shape[0]
+    secs = time.time() - t0
+    o.close()
+    return {"value": round(done / secs / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} lookups ({sample.shape[0]}-key slices of the timed batch, neg {args.neg_rate}) "
+                      f"on the oracle table of the same fill ({fill.keys.shape[0]} keys, built in {build_s:.0f} s)"}
+
+
+# ------------------------------------------------------- reference arm
+
+def run_reference(args):
+    import oracle
+    from paper_1712_09624_gb300 import workload as W
+    nb = 1 << args.log2_buckets
+    n_fill = int(args.load_factor * nb * 8)
+    fill = W.fill(args.seed, n_fill)
+    o = oracle.Table(nb, 8, False, args.seed)
+    o.insert(fill.keys, fill.values)
+    q = W.lookup_batch(args.seed, 1 << args.log2_batch, fill, args.neg_rate)
+    per_step = 1 << 20  # bounded sample per step
+    sample = q.keys[:per_step]
+    for _ in range(args.warmup):
+        o.lookup(sample)
+    t0 = time.time()
+    for _ in range(args.steps):
+        v, f = o.lookup(sample)
+    secs = time.time() - t0
+    value = per_step * args.steps / secs / 1e9
+    desc = f"{per_step} lookups per step from the 16M-key batch (neg {args.neg_rate}) on the oracle table " \
+           f"({n_fill} keys, 2^{args.log2_buckets} buckets)"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "plain Cuckoo++ at scale: 2^24 buckets x 8 slots, LF 0.9, 16M-key bulk_lookup",
+                       "n_buckets": nb, "entries": n_fill, "batch": 1 << args.log2_batch,
+                       "neg_rate": args.neg_rate},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * ckpp.h -- C ABI of the GB300 Cuckoo++ flow-table library (libckpp.so).
+ *
+ * The method is Cuckoo++ (Le Scouarnec, "Cuckoo++ Hash Tables: High-Performance
+ * Hash Tables for Networking Applications", 2017): a bucketized two-choice
+ * cuckoo hash table of 8-slot buckets whose primary bucket carries a 64-bit
+ * Bloom filter of the keys displaced to their secondary bucket (Sec. 4.1), with
+ * optional 16-bit expiration timers (Sec. 4.2).
+ *
+ * Conventions shared by every call below:
+ *  - All array arguments are DEVICE pointers owned by the caller (e.g. torch
+ *    tensors); the library never frees them. The table handle is host memory
+ *    owned by the library (ckpp_create / ckpp_destroy).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and never synchronise the device, except ckpp_stats and
+ *    ckpp_sync_status, which say so.
+ *  - Return value: CKPP_OK (0) or a negative CKPP_E* code. A call that returns an
+ *    error launched nothing. Per-key outcomes go to status arrays, never to the
+ *    return value.
+ *  - Errors found on the device (a bounded wait that gave up) are latched in the
+ *    table's device status word; ckpp_sync_status reads and clears it.
+ *  - Calls on one table must be ordered (one stream, or events): the table is a
+ *    single-writer structure, as in the paper's share-nothing setting (Sec. 2).
+ *  - Batches hold at most 2^32 - 1 keys.
+ *  - Timers: with CKPP_TIMERS, `now` is the caller's time in quantised units
+ *    (Sec. 4.2, e.g. 30 s); an entry inserted with ttl expires after now + ttl
+ *    and is alive iff (uint16)(expiry - now) < 1024, so ttl <= 1023. A full
+ *    ckpp_expire scan must run at least every 64512 units; a call whose `now` is
+ *    more than 64512 units past the last scan (or the first timed call) returns
+ *    CKPP_ESTALE. Without CKPP_TIMERS, now/ttl/refresh_ttl are ignored.
+ */
+#ifndef CKPP_H
+#define CKPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without including the CUDA runtime headers. */
+typedef struct CUstream_st* ckpp_stream_t;
+
+#define CKPP_ABI_VERSION 1
+
+/* return codes */
+#define CKPP_OK 0
+#define CKPP_EINVAL (-1)  /* bad geometry, NULL or misaligned pointer, buffer too small, n too large */
+#define CKPP_ECUDA (-2)   /* a CUDA launch or runtime call failed */
+#define CKPP_ESTALE (-3)  /* `now` is more than 64512 units past the last expire scan */
+#define CKPP_EBUSY (-4)   /* a bounded device wait gave up (latched; see ckpp_sync_status) */
+
+/* per-key status codes (uint8) */
+#define CKPP_ST_INSERTED 1  /* the key had no live entry; it now has one            */
+#define CKPP_ST_UPDATED 2   /* the key had a live entry; value and expiry replaced  */
+#define CKPP_ST_FULL 3      /* no free slot and no cuckoo path found; table unchanged for this key */
+#define CKPP_ST_DELETED 4   /* the key had a live entry; it is gone                 */
+#define CKPP_ST_NOT_FOUND 5 /* the key had no live entry                            */
+#define CKPP_ST_BUSY 6      /* a bounded lock wait gave up; the key was not processed */
+
+/* geometry flags */
+#define CKPP_TIMERS 1u
+
+/* A 5-tuple flow key: 16 bytes, 16-byte aligned in arrays, little endian,
+ * pad bytes must be zero (they are hashed and compared like the rest). */
+typedef struct ckpp_key {
+  uint32_t src_ip;
+  uint32_t dst_ip;
+  uint16_t src_port;
+  uint16_t dst_port;
+  uint8_t proto;
+  uint8_t pad[3];
+} ckpp_key;
+
+/* Table geometry. n_buckets in [2, 2^32 - 1]; slots_per_bucket must be 8
+ * (Sec. 4.3: 8 16-bit tags per bucket); flags: CKPP_TIMERS or 0; seed selects
+ * the hash functions. */
+typedef struct ckpp_geometry {
+  uint64_t n_buckets;
+  uint32_t slots_per_bucket;
+  uint32_t flags;
+  uint64_t seed;
+} ckpp_geometry;
+
+typedef struct ckpp_table ckpp_table;
+
+/* Table statistics (Fig. 2, Fig. 5 and Table 2 of the paper are built from these). */
+typedef struct ckpp_stats {
+  uint64_t n_buckets;
+  uint64_t n_slots;
+  uint64_t n_occupied;      /* busy slots, alive or dead                          */
+  uint64_t n_live;          /* busy and alive at `now`                            */
+  uint64_t n_in_secondary;  /* busy slots whose entry sits in its secondary bucket */
+  uint64_t n_moved_zero;    /* buckets whose moved counter is 0                   */
+  uint64_t moved_sum;       /* sum of moved counters (= n_in_secondary)           */
+  uint64_t bloom_bits_set;  /* total set bits over all filters                    */
+  uint64_t bloom_pop_sq;    /* sum over buckets of popcount(filter)^2             */
+  uint64_t moved_hist[16];  /* buckets with moved counter c (c = 15: 15 or more)  */
+} ckpp_stats;
+
+/* Bytes of device memory a table of this geometry needs (0 if the geometry is
+ * invalid). Layout: a 256-byte header, n_buckets bucket records (32 bytes, or 64
+ * with CKPP_TIMERS), then n_buckets * 8 key/value records of 32 bytes at the
+ * implicit index bucket * 8 + slot (Sec. 4.3). */
+size_t ckpp_required_bytes(const ckpp_geometry* geometry);
+
+/* Device workspace bytes an insert or delete batch of n keys needs (scratch for
+ * resolving in-batch duplicate keys and for the displacement pass). */
+size_t ckpp_workspace_bytes(uint64_t n);
+
+/* Create a table in the caller's device buffer dev_buf (at least
+ * ckpp_required_bytes, 256-byte aligned) and clear it on `stream`. The buffer
+ * must outlive the handle and stay untouched by the caller. On success *out
+ * receives a host handle. Errors: CKPP_EINVAL (geometry, NULL, size, alignment),
+ * CKPP_ECUDA. */
+int ckpp_create(ckpp_table** out, const ckpp_geometry* geometry, void* dev_buf, size_t bytes,
+                ckpp_stream_t stream);
+
+/* Release the host handle. Does not free dev_buf and does not synchronise: the
+ * caller must not reuse dev_buf before the table's queued work has finished. */
+int ckpp_destroy(ckpp_table* table);
+
+/* Batched lookup (Sec. 2, Sec. 4.1 and Fig. 4): for every key i, read the primary
+ * bucket, compare tags, confirm the full key in the key/value array; on a miss
+ * test the two Bloom bits of the primary's filter and read the secondary bucket
+ * only if both are set. With timers dead entries are ignored (Sec. 4.2) and,
+ * if refresh_ttl > 0, a hit sets the entry's expiry to now + refresh_ttl.
+ *   keys      [n] ckpp_key, 16-byte aligned
+ *   out_vals  [n] uint64, 8-byte aligned: the value, or 0 on a miss
+ *   out_found [n] uint8: 1 on a hit, 0 on a miss
+ * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
+int ckpp_bulk_lookup(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint64_t* out_vals,
+                     uint8_t* out_found, uint32_t now, uint16_t refresh_ttl, ckpp_stream_t stream);
+
+/* Batched insert-or-update (Sec. 2 cuckoo insertion; Sec. 4.1 filter and moved
+ * counter upkeep, including moves along a cuckoo path; Sec. 4.2 dead slots are
+ * reused as free). The batch has the result of inserting keys one by one in
+ * index order: the last occurrence of a key supplies its value, the first
+ * occurrence reports INSERTED or UPDATED and later ones UPDATED. A key that finds
+ * no slot and no cuckoo path reports FULL (every occurrence) and leaves the table
+ * unchanged for that key.
+ *   keys   [n] ckpp_key, 16-byte aligned;  vals [n] uint64, 8-byte aligned
+ *   status [n] uint8 out: CKPP_ST_INSERTED / UPDATED / FULL / BUSY
+ *   ttl    expiry = now + ttl, ttl <= 1023 (timers only)
+ *   workspace: device memory of at least ckpp_workspace_bytes(n) bytes,
+ *   256-byte aligned, used only while the call's work runs on `stream`.
+ * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
+int ckpp_bulk_insert(ckpp_table* table, const ckpp_key* keys, const uint64_t* vals, uint64_t n,
+                     uint32_t now, uint16_t ttl, uint8_t* status, void* workspace, size_t workspace_bytes,
+                     ckpp_stream_t stream);
+
+/* Batched delete (Sec. 4.1: deleting a key stored in its secondary bucket
+ * decrements the primary's moved counter and resets the filter at zero). The
+ * first occurrence of a key in the batch reports DELETED if it had a live entry,
+ * every other occurrence NOT_FOUND. A dead entry of the key is removed as well.
+ *   keys [n] ckpp_key, 16-byte aligned;  status [n] uint8 out
+ *   workspace as for ckpp_bulk_insert.
+ * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
+int ckpp_bulk_delete(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32_t now, uint8_t* status,
+                     void* workspace, size_t workspace_bytes, ckpp_stream_t stream);
+
+/* Expiration scan (Sec. 4.2): delete every dead entry of every bucket, with
+ * moved-counter upkeep, and record `now` as the last scan time. If
+ * d_n_expired is not NULL, the number of deleted entries is ADDED to the
+ * device uint64 it points to. No-op scan (but the time is recorded) without
+ * timers. Errors: CKPP_EINVAL, CKPP_ECUDA. */
+int ckpp_expire(ckpp_table* table, uint32_t now, uint64_t* d_n_expired, ckpp_stream_t stream);
+
+/* Table statistics at time `now`, written to host memory. Synchronises
+ * `stream`. Errors: CKPP_EINVAL, CKPP_ECUDA. */
+int ckpp_stats_get(ckpp_table* table, uint32_t now, ckpp_stats* host_out, ckpp_stream_t stream);
+
+/* For a lookup batch, count the memory reads the method makes without
+ * performing the lookup (no refresh): d_counts[0] += primary bucket reads (n),
+ * d_counts[1] += secondary bucket reads, d_counts[2] += key/value record reads.
+ * d_counts is a device uint64[3]. Used to state a batch's algorithmic bytes.
+ * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
+int ckpp_lookup_probe_counts(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32_t now,
+                             uint64_t* d_counts, ckpp_stream_t stream);
+
+/* Synchronise `stream`, then read and clear the table's latched device error
+ * word: CKPP_OK, or CKPP_EBUSY if a bounded wait gave up since the last call.
+ * Errors: CKPP_EINVAL, CKPP_ECUDA. */
+int ckpp_sync_status(ckpp_table* table, ckpp_stream_t stream);
+
+/* Geometry of an existing table (host copy). Errors: CKPP_EINVAL. */
+int ckpp_get_geometry(const ckpp_table* table, ckpp_geometry* out);
+
+/* Time of the last expire scan (or first timed call) and whether one was set. */
+int ckpp_get_last_scan(const ckpp_table* table, uint32_t* last_scan, int* have_epoch);
+
+/* Static text for a return code. */
+const char* ckpp_error_string(int code);
+
+/* CKPP_ABI_VERSION of the loaded library. */
+int ckpp_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKPP_H */

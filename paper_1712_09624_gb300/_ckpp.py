@@ -1,0 +1,201 @@
+"""ctypes binding of libckpp.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls
+(include/ckpp.h) and takes torch CUDA tensors in place of device pointers; all
+work happens in the library's kernels. If the library is missing the import of
+this module fails with a RuntimeError naming the build step: there is no
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libckpp.so")
+
+CKPP_OK, CKPP_EINVAL, CKPP_ECUDA, CKPP_ESTALE, CKPP_EBUSY = 0, -1, -2, -3, -4
+ST_INSERTED, ST_UPDATED, ST_FULL, ST_DELETED, ST_NOT_FOUND, ST_BUSY = 1, 2, 3, 4, 5, 6
+CKPP_TIMERS = 1
+SLOTS = 8
+
+
+class ckpp_geometry(C.Structure):
+    _fields_ = [("n_buckets", C.c_uint64), ("slots_per_bucket", C.c_uint32), ("flags", C.c_uint32),
+                ("seed", C.c_uint64)]
+
+
+class ckpp_stats(C.Structure):
+    _fields_ = [("n_buckets", C.c_uint64), ("n_slots", C.c_uint64), ("n_occupied", C.c_uint64),
+                ("n_live", C.c_uint64), ("n_in_secondary", C.c_uint64), ("n_moved_zero", C.c_uint64),
+                ("moved_sum", C.c_uint64), ("bloom_bits_set", C.c_uint64), ("bloom_pop_sq", C.c_uint64),
+                ("moved_hist", C.c_uint64 * 16)]
+
+
+class CkppError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_lib.ckpp_error_string(code).decode()} ({code})")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1712_09624_gb300.build` "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    vp, u64, u32, u16, sz = C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint16, C.c_size_t
+    gp = C.POINTER(ckpp_geometry)
+    sigs = {
+        "ckpp_required_bytes": (sz, [gp]),
+        "ckpp_workspace_bytes": (sz, [u64]),
+        "ckpp_create": (C.c_int, [C.POINTER(vp), gp, vp, sz, vp]),
+        "ckpp_destroy": (C.c_int, [vp]),
+        "ckpp_bulk_lookup": (C.c_int, [vp, vp, u64, vp, vp, u32, u16, vp]),
+        "ckpp_bulk_insert": (C.c_int, [vp, vp, vp, u64, u32, u16, vp, vp, sz, vp]),
+        "ckpp_bulk_delete": (C.c_int, [vp, vp, u64, u32, vp, vp, sz, vp]),
+        "ckpp_expire": (C.c_int, [vp, u32, vp, vp]),
+        "ckpp_stats_get": (C.c_int, [vp, u32, C.POINTER(ckpp_stats), vp]),
+        "ckpp_lookup_probe_counts": (C.c_int, [vp, vp, u64, u32, vp, vp]),
+        "ckpp_sync_status": (C.c_int, [vp, vp]),
+        "ckpp_get_geometry": (C.c_int, [vp, gp]),
+        "ckpp_get_last_scan": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int)]),
+        "ckpp_error_string": (C.c_char_p, [C.c_int]),
+        "ckpp_abi_version": (C.c_int, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+_lib = _load()
+EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_destroy", "ckpp_bulk_lookup",
+            "ckpp_bulk_insert", "ckpp_bulk_delete", "ckpp_expire", "ckpp_stats_get", "ckpp_lookup_probe_counts",
+            "ckpp_sync_status", "ckpp_get_geometry", "ckpp_get_last_scan", "ckpp_error_string",
+            "ckpp_abi_version")
+
+
+def library():
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != CKPP_OK:
+        raise CkppError(rc, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else t.data_ptr()
+
+
+def _dev(t: torch.Tensor, name: str, dtype=None):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    return t
+
+
+def geometry(n_buckets: int, timers: bool = False, seed: int = 0) -> ckpp_geometry:
+    return ckpp_geometry(n_buckets, SLOTS, CKPP_TIMERS if timers else 0, seed)
+
+
+def ckpp_required_bytes(geo: ckpp_geometry) -> int:
+    return int(_lib.ckpp_required_bytes(C.byref(geo)))
+
+
+def ckpp_workspace_bytes(n: int) -> int:
+    return int(_lib.ckpp_workspace_bytes(n))
+
+
+def ckpp_create(geo: ckpp_geometry, buf: torch.Tensor, stream=None) -> int:
+    _dev(buf, "buf", torch.uint8)
+    h = C.c_void_p()
+    _check(_lib.ckpp_create(C.byref(h), C.byref(geo), _ptr(buf), buf.numel(), _stream(stream)), "ckpp_create")
+    return h.value
+
+
+def ckpp_destroy(handle: int):
+    _check(_lib.ckpp_destroy(handle), "ckpp_destroy")
+
+
+def ckpp_bulk_lookup(handle: int, keys: torch.Tensor, out_vals: torch.Tensor, out_found: torch.Tensor,
+                     now: int = 0, refresh_ttl: int = 0, stream=None):
+    n = keys.shape[0]
+    _dev(keys, "keys", torch.uint8)
+    _dev(out_vals, "out_vals", (torch.int64, torch.uint64))
+    _dev(out_found, "out_found", (torch.uint8, torch.bool))
+    _check(_lib.ckpp_bulk_lookup(handle, _ptr(keys), n, _ptr(out_vals), _ptr(out_found), now, refresh_ttl,
+                                 _stream(stream)), "ckpp_bulk_lookup")
+
+
+def ckpp_bulk_insert(handle: int, keys: torch.Tensor, vals: torch.Tensor, status: torch.Tensor,
+                     workspace: torch.Tensor, now: int = 0, ttl: int = 0, stream=None):
+    n = keys.shape[0]
+    _dev(keys, "keys", torch.uint8)
+    _dev(vals, "vals", (torch.int64, torch.uint64))
+    _dev(status, "status", torch.uint8)
+    _dev(workspace, "workspace", torch.uint8)
+    _check(_lib.ckpp_bulk_insert(handle, _ptr(keys), _ptr(vals), n, now, ttl, _ptr(status), _ptr(workspace),
+                                 workspace.numel(), _stream(stream)), "ckpp_bulk_insert")
+
+
+def ckpp_bulk_delete(handle: int, keys: torch.Tensor, status: torch.Tensor, workspace: torch.Tensor,
+                     now: int = 0, stream=None):
+    n = keys.shape[0]
+    _dev(keys, "keys", torch.uint8)
+    _dev(status, "status", torch.uint8)
+    _dev(workspace, "workspace", torch.uint8)
+    _check(_lib.ckpp_bulk_delete(handle, _ptr(keys), n, now, _ptr(status), _ptr(workspace), workspace.numel(),
+                                 _stream(stream)), "ckpp_bulk_delete")
+
+
+def ckpp_expire(handle: int, now: int, d_n_expired: torch.Tensor | None = None, stream=None):
+    if d_n_expired is not None:
+        _dev(d_n_expired, "d_n_expired", (torch.int64, torch.uint64))
+    _check(_lib.ckpp_expire(handle, now, _ptr(d_n_expired), _stream(stream)), "ckpp_expire")
+
+
+def ckpp_stats_get(handle: int, now: int = 0, stream=None) -> dict:
+    s = ckpp_stats()
+    _check(_lib.ckpp_stats_get(handle, now, C.byref(s), _stream(stream)), "ckpp_stats_get")
+    out = {name: getattr(s, name) for name, _ in ckpp_stats._fields_ if name != "moved_hist"}
+    out["moved_hist"] = list(s.moved_hist)
+    return out
+
+
+def ckpp_lookup_probe_counts(handle: int, keys: torch.Tensor, d_counts: torch.Tensor, now: int = 0, stream=None):
+    _dev(keys, "keys", torch.uint8)
+    _dev(d_counts, "d_counts", (torch.int64, torch.uint64))
+    _check(_lib.ckpp_lookup_probe_counts(handle, _ptr(keys), keys.shape[0], now, _ptr(d_counts), _stream(stream)),
+           "ckpp_lookup_probe_counts")
+
+
+def ckpp_sync_status(handle: int, stream=None) -> int:
+    rc = _lib.ckpp_sync_status(handle, _stream(stream))
+    if rc not in (CKPP_OK, CKPP_EBUSY):
+        _check(rc, "ckpp_sync_status")
+    return rc
+
+
+def ckpp_get_last_scan(handle: int) -> tuple[int, bool]:
+    t = C.c_uint32()
+    e = C.c_int()
+    _check(_lib.ckpp_get_last_scan(handle, C.byref(t), C.byref(e)), "ckpp_get_last_scan")
+    return t.value, bool(e.value)
+
+
+def ckpp_abi_version() -> int:
+    return int(_lib.ckpp_abi_version())

@@ -1,0 +1,47 @@
+// Internal launchers of the GB300 Cuckoo++ kernels (host side, C++).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ckpp_device.cuh"
+
+namespace ckpp {
+
+// Device scratch for one insert or delete batch (carved out of the caller's
+// workspace buffer, see workspace_layout in api.cu).
+struct Workspace {
+  uint32_t* counters;   // [0] pending count, [1] fixup count, [2] fixup overflow flag
+  uint32_t* set_first;  // [m] open-addressing set of batch keys: lowest batch index of the key
+  uint32_t* set_last;   // [m] highest batch index of the key
+  uint32_t* slot_of;    // [n] set position of each batch key
+  uint32_t* pending;    // [n] leaders left for the displacement pass
+  uint32_t* fixup;      // [fix_cap] buckets whose moved counter fell to 0 off-lock
+  uint32_t m_mask;      // m - 1 (m a power of two >= 2n)
+  uint32_t fix_cap;
+};
+
+cudaError_t launch_init_header(uint8_t* base, uint64_t nb, uint32_t slots, uint32_t flags, uint64_t seed,
+                               cudaStream_t s);
+
+cudaError_t launch_lookup(const TableView& t, const uint8_t* keys, uint64_t n, uint64_t* out_vals,
+                          uint8_t* out_found, uint32_t now, uint32_t refresh_ttl, cudaStream_t s);
+
+cudaError_t launch_probe_counts(const TableView& t, const uint8_t* keys, uint64_t n, uint32_t now,
+                                unsigned long long* counts, cudaStream_t s);
+
+cudaError_t launch_dedup(const TableView& t, const uint8_t* keys, uint64_t n, const Workspace& ws,
+                         cudaStream_t s);
+
+cudaError_t launch_insert(const TableView& t, const uint8_t* keys, const uint64_t* vals, uint64_t n,
+                          uint32_t now, uint32_t expiry, uint8_t* status, const Workspace& ws, cudaStream_t s);
+
+cudaError_t launch_delete(const TableView& t, const uint8_t* keys, uint64_t n, uint32_t now, uint8_t* status,
+                          const Workspace& ws, cudaStream_t s);
+
+cudaError_t launch_expire(const TableView& t, uint32_t now, unsigned long long* n_expired, cudaStream_t s);
+
+// out: 7 sums + 16 histogram bins (uint64), zeroed by the caller.
+cudaError_t launch_stats(const TableView& t, uint32_t now, unsigned long long* out, cudaStream_t s);
+
+}  // namespace ckpp

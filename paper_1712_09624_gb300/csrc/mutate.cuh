@@ -1,0 +1,150 @@
+// Device helpers shared by the mutating kernels (insert, delete, expire):
+// bucket locks, bucket snapshots, slot placement and removal with the moved
+// counter and Bloom filter upkeep of Sec. 4.1.
+//
+// Concurrency rules of the insert kernels (one table, one batch at a time):
+//  * a bucket's busy / in_secondary bits, tags, expiries and records change only
+//    while its lock bit (ctrl bit 31) is held; the new ctrl word is published
+//    by the unlocking exchange;
+//  * Bloom bits of bucket p are set only while p's lock is held, so a filter
+//    reset done under p's lock cannot erase a concurrent insertion's bits;
+//  * a moved counter may be decremented without its bucket's lock (when a dead
+//    entry is overwritten elsewhere); a decrement that reaches zero off-lock
+//    queues the bucket for a reset pass that runs after the batch.
+// Every wait is bounded: a lock not taken after kLockSpins tries returns false
+// and the caller reports CKPP_ST_BUSY and latches kErrLockTimeout.
+#pragma once
+
+#include "ckpp_kernels.h"
+
+namespace ckpp {
+
+__device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint32_t& ctrl) {
+  uint32_t* c = ctrl_ptr(t, b);
+  for (int i = 0; i < kLockSpins; ++i) {
+    const uint32_t old = atomicOr(c, kLockBit);
+    if (!(old & kLockBit)) {
+      __threadfence();
+      ctrl = old;
+      return true;
+    }
+    __nanosleep(32u << (i < 5 ? i : 5));
+  }
+  return false;
+}
+
+__device__ __forceinline__ void unlock_bucket(const TableView& t, uint32_t b, uint32_t ctrl) {
+  __threadfence();
+  atomicExch(ctrl_ptr(t, b), ctrl & ~kLockBit);
+}
+
+// Lock two distinct buckets in index order (no lock cycles). cx/cy receive the
+// ctrl words of x and y.
+__device__ __forceinline__ bool lock_pair(const TableView& t, uint32_t x, uint32_t y, uint32_t& cx, uint32_t& cy) {
+  const uint32_t lo = x < y ? x : y, hi = x < y ? y : x;
+  uint32_t clo, chi;
+  if (!lock_bucket(t, lo, clo)) return false;
+  if (!lock_bucket(t, hi, chi)) {
+    unlock_bucket(t, lo, clo);
+    return false;
+  }
+  cx = (x == lo) ? clo : chi;
+  cy = (x == lo) ? chi : clo;
+  return true;
+}
+
+__device__ __forceinline__ void unlock_pair(const TableView& t, uint32_t x, uint32_t y, uint32_t cx, uint32_t cy) {
+  if (x < y) {
+    unlock_bucket(t, y, cy);
+    unlock_bucket(t, x, cx);
+  } else {
+    unlock_bucket(t, x, cx);
+    unlock_bucket(t, y, cy);
+  }
+}
+
+// Coherent snapshot of a bucket: hot sector and (with timers) the 8 expiries.
+struct Snap {
+  uint64_t w[4];
+  uint64_t e0, e1;
+};
+
+__device__ __forceinline__ void snap_bucket(const TableView& t, uint32_t b, Snap& s) {
+  ld256_cg(bucket_ptr(t, b), s.w);
+  if (t.timers) {
+    ld128_cg(expiry_ptr(t, b, 0), s.e0, s.e1);
+  } else {
+    s.e0 = s.e1 = 0;
+  }
+}
+
+__device__ __forceinline__ uint32_t snap_expiry(const Snap& s, uint32_t slot) {
+  const uint64_t e = slot < 4 ? s.e0 : s.e1;
+  return (uint32_t)(e >> (16 * (slot & 3))) & 0xFFFFu;
+}
+
+// Slots an insertion may take: empty, or busy with a dead entry (Sec. 4.2).
+__device__ __forceinline__ uint32_t free_mask(const TableView& t, uint32_t ctrl, const Snap& s, uint32_t now) {
+  const uint32_t busy = ctrl & kBusyMask;
+  uint32_t f = ~busy & kBusyMask;
+  if (t.timers) f |= busy & ~alive_mask(s.e0, s.e1, now) & kBusyMask;
+  return f;
+}
+
+// Slot of bucket b holding key k (alive or dead), or -1.
+__device__ __forceinline__ int find_key(const TableView& t, uint32_t b, uint32_t ctrl, const Snap& s, const Key& k,
+                                        uint32_t tag) {
+  uint32_t cand = tag_mask(s.w[0], s.w[1], tag) & ctrl & kBusyMask;
+  while (cand) {
+    const int slot = __ffs(cand) - 1;
+    cand &= cand - 1;
+    uint64_t r[4];
+    ld256_cg(record_ptr(t, b, slot), r);
+    if (same_key(r, k)) return slot;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void push_fixup(const Workspace& ws, uint32_t b) {
+  const uint32_t idx = atomicAdd(ws.counters + 1, 1u);
+  if (idx < ws.fix_cap) {
+    ws.fixup[idx] = b;
+  } else {
+    atomicExch(ws.counters + 2, 1u);
+  }
+}
+
+// Remove the (dead) entry in slot s of locked bucket b: if it sits in its
+// secondary bucket its primary's moved counter is decremented (Sec. 4.1).
+__device__ __forceinline__ void evict_entry(const TableView& t, uint32_t b, uint32_t s, uint32_t& ctrl,
+                                            const Workspace& ws) {
+  if ((ctrl >> (kInsecShift + s)) & 1u) {
+    uint64_t r[4];
+    ld256_cg(record_ptr(t, b, s), r);
+    const Key k{r[0], r[1]};
+    const Addr a = address_of(k, t.nb, t.seed);
+    const uint32_t old = atomicSub(moved_ptr(t, a.b1), 1u);
+    if (old == 1u) push_fixup(ws, a.b1);
+  }
+  ctrl &= ~((1u << s) | (1u << (kInsecShift + s)));
+}
+
+// Store a new entry in free slot s of locked bucket b; if b is the key's
+// secondary bucket, set its two bits in the primary's filter and increment the
+// primary's moved counter (Sec. 4.1). The caller holds the primary's lock too.
+__device__ __forceinline__ void place_entry(const TableView& t, uint32_t b, uint32_t s, const Key& k, uint64_t v,
+                                            const Addr& a, uint32_t expiry, uint32_t& ctrl) {
+  st256_cg(record_ptr(t, b, s), k.k0, k.k1, v, 0ull);
+  st16_cg(tag_ptr(t, b, s), a.tag);
+  if (t.timers) st16_cg(expiry_ptr(t, b, s), expiry);
+  ctrl |= 1u << s;
+  if (b == a.b2) {
+    ctrl |= 1u << (kInsecShift + s);
+    atomicOr(reinterpret_cast<unsigned long long*>(bloom_ptr(t, a.b1)), (unsigned long long)a.bits);
+    atomicAdd(moved_ptr(t, a.b1), 1u);
+  } else {
+    ctrl &= ~(1u << (kInsecShift + s));
+  }
+}
+
+}  // namespace ckpp

@@ -1,0 +1,103 @@
+"""FlowTable: a Cuckoo++ flow table in one torch-allocated device buffer.
+
+A thin convenience layer over the C ABI (``_ckpp``): it owns the table's
+device buffer and a reusable workspace, converts numpy inputs to device
+tensors and allocates outputs. Every operation runs in libckpp's kernels.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _ckpp as K
+
+
+def as_device_keys(keys, device) -> torch.Tensor:
+    if isinstance(keys, np.ndarray):
+        keys = torch.from_numpy(np.ascontiguousarray(keys, dtype=np.uint8).reshape(-1, 16))
+    if keys.dtype != torch.uint8 or keys.dim() != 2 or keys.shape[1] != 16:
+        raise ValueError("keys must be uint8 [n, 16]")
+    return keys.to(device, non_blocking=True).contiguous()
+
+
+def as_device_values(values, device) -> torch.Tensor:
+    if isinstance(values, np.ndarray):
+        values = torch.from_numpy(np.ascontiguousarray(values).astype(np.uint64).view(np.int64))
+    if values.dtype not in (torch.int64, torch.uint64):
+        raise ValueError("values must be 64-bit integers")
+    return values.to(device, non_blocking=True).contiguous()
+
+
+class FlowTable:
+    """A table of 8-slot buckets (capacity 8 * n_buckets) on one GPU."""
+
+    def __init__(self, n_buckets: int, timers: bool = False, seed: int = 0, device=None, stream=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.geo = K.geometry(n_buckets, timers, seed)
+        nbytes = K.ckpp_required_bytes(self.geo)
+        if nbytes == 0:
+            raise ValueError(f"invalid geometry: n_buckets={n_buckets}")
+        self.n_buckets, self.timers, self.seed = n_buckets, timers, seed
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.handle = K.ckpp_create(self.geo, self.buf, stream)
+        self._ws = None
+
+    @property
+    def capacity(self) -> int:
+        return self.n_buckets * K.SLOTS
+
+    def workspace(self, n: int) -> torch.Tensor:
+        need = K.ckpp_workspace_bytes(n)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def insert(self, keys, values, now: int = 0, ttl: int = 0, stream=None) -> torch.Tensor:
+        k = as_device_keys(keys, self.device)
+        v = as_device_values(values, self.device)
+        status = torch.empty(k.shape[0], dtype=torch.uint8, device=self.device)
+        K.ckpp_bulk_insert(self.handle, k, v, status, self.workspace(k.shape[0]), now, ttl, stream)
+        return status
+
+    def lookup(self, keys, now: int = 0, refresh_ttl: int = 0, stream=None):
+        k = as_device_keys(keys, self.device)
+        vals = torch.empty(k.shape[0], dtype=torch.int64, device=self.device)
+        found = torch.empty(k.shape[0], dtype=torch.bool, device=self.device)
+        K.ckpp_bulk_lookup(self.handle, k, vals, found, now, refresh_ttl, stream)
+        return vals, found
+
+    def delete(self, keys, now: int = 0, stream=None) -> torch.Tensor:
+        k = as_device_keys(keys, self.device)
+        status = torch.empty(k.shape[0], dtype=torch.uint8, device=self.device)
+        K.ckpp_bulk_delete(self.handle, k, status, self.workspace(k.shape[0]), now, stream)
+        return status
+
+    def expire(self, now: int, stream=None) -> torch.Tensor:
+        count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        K.ckpp_expire(self.handle, now, count, stream)
+        return count
+
+    def stats(self, now: int = 0, stream=None) -> dict:
+        return K.ckpp_stats_get(self.handle, now, stream)
+
+    def probe_counts(self, keys, now: int = 0, stream=None) -> torch.Tensor:
+        """[primary bucket reads, secondary bucket reads, record reads] of a lookup batch."""
+        k = as_device_keys(keys, self.device)
+        counts = torch.zeros(3, dtype=torch.int64, device=self.device)
+        K.ckpp_lookup_probe_counts(self.handle, k, counts, now, stream)
+        return counts
+
+    def sync_status(self, stream=None) -> int:
+        return K.ckpp_sync_status(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            K.ckpp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,117 @@
+"""Host-side decoder of the GPU table layout, for checking a downloaded table.
+
+Test code: it reads the bytes of a table buffer (the layout documented in
+include/ckpp.h and the CUDA sources) into numpy arrays and checks them with the
+oracle's hash (``oracle.address``), so the structural invariants of Sec. 2 and
+Sec. 4.1 are verified on what the kernels actually wrote.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+HEADER = 256
+SLOTS = 8
+
+
+class Decoded:
+    def __init__(self, buf: np.ndarray, n_buckets: int, timers: bool, seed: int):
+        self.nb, self.timers, self.seed = n_buckets, timers, seed
+        bb = 64 if timers else 32
+        hdr = buf[:HEADER]
+        self.magic = int(hdr[0:4].view(np.uint32)[0])
+        self.err = int(hdr[32:36].view(np.uint32)[0])
+        bk = buf[HEADER:HEADER + n_buckets * bb].reshape(n_buckets, bb)
+        self.tags = np.ascontiguousarray(bk[:, 0:16]).view(np.uint16).reshape(n_buckets, 8)
+        self.bloom = np.ascontiguousarray(bk[:, 16:24]).view(np.uint64).reshape(n_buckets)
+        self.ctrl = np.ascontiguousarray(bk[:, 24:28]).view(np.uint32).reshape(n_buckets)
+        self.moved = np.ascontiguousarray(bk[:, 28:32]).view(np.uint32).reshape(n_buckets)
+        if timers:
+            self.expiry = np.ascontiguousarray(bk[:, 32:48]).view(np.uint16).reshape(n_buckets, 8)
+            self.bucket_reserved = bk[:, 48:64]
+        else:
+            self.expiry = np.zeros((n_buckets, 8), np.uint16)
+            self.bucket_reserved = np.zeros((n_buckets, 0), np.uint8)
+        off = HEADER + n_buckets * bb
+        rec = buf[off:off + n_buckets * SLOTS * 32].reshape(n_buckets * SLOTS, 32)
+        self.rec_key = rec[:, 0:16]
+        self.rec_value = np.ascontiguousarray(rec[:, 16:24]).view(np.uint64).reshape(-1)
+        self.rec_reserved = np.ascontiguousarray(rec[:, 24:32]).view(np.uint64).reshape(-1)
+        bits = np.arange(8, dtype=np.uint32)
+        self.busy = ((self.ctrl[:, None] >> bits) & 1).astype(bool)
+        self.insec = ((self.ctrl[:, None] >> (bits + 8)) & 1).astype(bool)
+
+    def occupied(self):
+        """Flat slot indices (bucket * 8 + slot) of busy slots."""
+        return np.nonzero(self.busy.reshape(-1))[0]
+
+    def alive(self, now: int) -> np.ndarray:
+        if not self.timers:
+            return np.ones((self.nb, 8), bool)
+        d = (self.expiry.astype(np.int64) - (now & 0xFFFF)) & 0xFFFF
+        return d < 1024
+
+    def live(self, now: int) -> dict:
+        """key bytes -> (value, expiry) of every live entry."""
+        idx = np.nonzero((self.busy & self.alive(now)).reshape(-1))[0]
+        exp = self.expiry.reshape(-1)
+        return {self.rec_key[i].tobytes(): (int(self.rec_value[i]), int(exp[i]) if self.timers else 0) for i in idx}
+
+    def check(self, check_reset: bool = True, bucket_sample: np.ndarray | None = None) -> list[str]:
+        """Structural invariants; returns failure messages (empty = all hold)."""
+        bad = []
+        if self.magic != 0x50504B43:
+            bad.append("bad magic")
+        if (self.ctrl & 0x7FFF0000).any() or (self.ctrl & 0x80000000).any():
+            bad.append("lock bit or unused ctrl bits set")
+        if (self.insec & ~self.busy).any():
+            bad.append("in_secondary set on an empty slot")
+        occ = self.occupied()
+        if bucket_sample is not None:
+            sel = np.isin(occ // SLOTS, bucket_sample)
+            occ = occ[sel]
+        keys = self.rec_key[occ]
+        a = oracle.address(keys, self.nb, self.seed)
+        b = occ // SLOTS
+        s = occ % SLOTS
+        if not ((b == a["b1"]) | (b == a["b2"])).all():
+            bad.append("an entry sits in neither of its buckets")
+        insec = self.insec[b, s]
+        if not (insec == (b == a["b2"])).all():
+            bad.append("in_secondary flag disagrees with the bucket")
+        if not (self.tags[b, s] == a["tag"]).all():
+            bad.append("stored tag differs from the key's tag")
+        if (self.rec_reserved[occ] != 0).any():
+            bad.append("record reserved bytes not zero")
+        bits = (np.uint64(1) << a["bit1"].astype(np.uint64)) | (np.uint64(1) << a["bit2"].astype(np.uint64))
+        p = a["b1"][insec]
+        if not ((self.bloom[p] & bits[insec]) == bits[insec]).all():
+            bad.append("a displaced key's bits are missing from its primary's filter")
+        if bucket_sample is None:
+            cnt = np.bincount(p.astype(np.int64), minlength=self.nb)
+            if not (cnt == self.moved).all():
+                bad.append("moved counter differs from the number of displaced keys")
+            kv = np.ascontiguousarray(keys).view(np.dtype((np.void, 16))).reshape(-1)
+            if np.unique(kv).shape[0] != kv.shape[0]:
+                bad.append("a key is stored twice")
+            if check_reset and ((self.moved == 0) & (self.bloom != 0)).any():
+                bad.append("zero moved counter with a non-empty filter")
+        return bad
+
+
+def download(table) -> Decoded:
+    import torch
+    torch.cuda.synchronize()
+    return Decoded(table.buf.cpu().numpy(), table.n_buckets, table.timers, table.seed)
+
+
+def oracle_live(t: "oracle.Table", now: int) -> dict:
+    d = t.dump()
+    out = {}
+    for i in range(d["value"].shape[0]):
+        e = int(d["expiry"][i])
+        if (not t.timers) or ((e - now) & 0xFFFF) < 1024:
+            out[d["key"][i].tobytes()] = (int(d["value"][i]), e if t.timers else 0)
+    return out

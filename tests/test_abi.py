@@ -1,0 +1,56 @@
+"""The C ABI library loads and exports every entry point include/ckpp.h
+declares; host-only calls behave as documented (no GPU needed)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ckpp.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ckpp_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_1712_09624_gb300 import build
+    build.build()
+    from paper_1712_09624_gb300 import _ckpp
+    return _ckpp
+
+
+def test_every_declared_symbol_is_exported(K):
+    names = declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(K.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in ckpp.h but not exported"
+    assert set(K.EXPORTED) == set(names)
+
+
+def test_host_only_calls(K):
+    assert K.ckpp_abi_version() == 1
+    g = K.geometry(1 << 24)
+    assert K.ckpp_required_bytes(g) == 256 + (1 << 24) * 32 + (1 << 27) * 32
+    gt = K.geometry(1 << 24, timers=True)
+    assert K.ckpp_required_bytes(gt) == 256 + (1 << 24) * 64 + (1 << 27) * 32
+    for bad in (K.geometry(1), K.geometry(0), K.geometry(1 << 32)):
+        assert K.ckpp_required_bytes(bad) == 0
+    wrong_slots = K.ckpp_geometry(1024, 4, 0, 0)
+    assert K.ckpp_required_bytes(wrong_slots) == 0
+    assert K.ckpp_workspace_bytes(0) > 0
+    assert K.ckpp_workspace_bytes(1 << 20) >= 8 * (1 << 21) + 8 * (1 << 20)
+    assert K.ckpp_workspace_bytes((1 << 30) + 1) == 0
+    lib = K.library()
+    assert lib.ckpp_error_string(-3).decode().startswith("more than 64512")
+    # argument checks return before touching the device
+    h = ctypes.c_void_p()
+    assert lib.ckpp_create(ctypes.byref(h), ctypes.byref(g), None, 0, None) == K.CKPP_EINVAL
+    assert lib.ckpp_destroy(None) == K.CKPP_EINVAL
+    assert lib.ckpp_bulk_lookup(None, None, 0, None, None, 0, 0, None) == K.CKPP_EINVAL
