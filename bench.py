@@ -283,8 +283,12 @@ def run_ours(args, rank, world, local_rank):
 
 
 def e2e_lookup(args, table, q, dev, stream):
-    """Lookups through the C ABI from pinned host memory: each step copies the
-    keys host->device, looks them up and copies values and flags back."""
+    """Lookups through the C ABI with HOST buffers: the keys sit in pinned host
+    memory and the results go to pinned host memory. ckpp_bulk_lookup reads and
+    writes them in place over NVLink-C2C, so every step moves 16 B per key
+    host->device and 9 B per key device->host inside the timed region. The
+    staged variant (explicit copies around a device-buffer lookup) is reported
+    beside it."""
     import torch
 
     from paper_1712_09624_gb300 import _ckpp as K
@@ -292,30 +296,41 @@ def e2e_lookup(args, table, q, dev, stream):
     h_keys = torch.from_numpy(q.keys).pin_memory()
     h_vals = torch.empty(n, dtype=torch.int64).pin_memory()
     h_found = torch.empty(n, dtype=torch.bool).pin_memory()
+    steps = max(5, args.steps // 10)
+
+    def run(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def zero_copy():
+        K.ckpp_bulk_lookup(table.handle, h_keys, h_vals, h_found, 0, 0, stream)
+
+    secs = run(zero_copy)
+    ok = bool((h_found.numpy() == q.expect_found).all()) and \
+        bool((h_vals.numpy().view(np.uint64) == q.expect_value).all())
     d_keys = torch.empty((n, 16), dtype=torch.uint8, device=dev)
     d_vals = torch.empty(n, dtype=torch.int64, device=dev)
     d_found = torch.empty(n, dtype=torch.bool, device=dev)
-    steps = max(5, args.steps // 10)
 
-    def one():
+    def staged():
         d_keys.copy_(h_keys, non_blocking=True)
         K.ckpp_bulk_lookup(table.handle, d_keys, d_vals, d_found, 0, 0, stream)
         h_vals.copy_(d_vals, non_blocking=True)
         h_found.copy_(d_found, non_blocking=True)
 
-    for _ in range(3):
-        one()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        one()
-    e1.record(stream)
-    e1.synchronize()
-    secs = e0.elapsed_time(e1) / 1e3
-    ok = bool((h_found.numpy() == q.expect_found).all())
+    secs_staged = run(staged)
     return {"value": round(n * steps / secs / 1e9, 4), "unit": UNIT, "h2d_bytes_per_step": 16 * n,
-            "d2h_bytes_per_step": 9 * n, "steps": steps, "results_match": ok}
+            "d2h_bytes_per_step": 9 * n, "steps": steps, "results_match": ok,
+            "path": "ckpp_bulk_lookup on pinned host buffers (in-place over NVLink-C2C)",
+            "staged_copies_value": round(n * steps / secs_staged / 1e9, 4)}
 
 
 def mutation_rates(table, dev, stream, ins_times, seed):

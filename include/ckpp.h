@@ -129,6 +129,11 @@ int ckpp_destroy(ckpp_table* table);
  *   keys      [n] ckpp_key, 16-byte aligned
  *   out_vals  [n] uint64, 8-byte aligned: the value, or 0 on a miss
  *   out_found [n] uint8: 1 on a hit, 0 on a miss
+ * Unlike the other calls, keys / out_vals / out_found may also be pinned host
+ * memory (cudaHostAlloc or cudaHostRegister): the kernel then reads the keys
+ * and writes the results in place over the host link (NVLink-C2C on GB300),
+ * with no staging copy; the caller must not touch them until the stream
+ * reaches the call's completion. Pageable host memory is rejected (EINVAL).
  * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
 int ckpp_bulk_lookup(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint64_t* out_vals,
                      uint8_t* out_found, uint32_t now, uint16_t refresh_ttl, ckpp_stream_t stream);

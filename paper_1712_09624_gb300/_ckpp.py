@@ -131,12 +131,25 @@ def ckpp_destroy(handle: int):
     _check(_lib.ckpp_destroy(handle), "ckpp_destroy")
 
 
+def _dev_or_pinned(t: torch.Tensor, name: str, dtype):
+    if t.is_cuda:
+        return _dev(t, name, dtype)
+    if not t.is_pinned():
+        raise ValueError(f"{name} must be a CUDA tensor or pinned host memory")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    return t
+
+
 def ckpp_bulk_lookup(handle: int, keys: torch.Tensor, out_vals: torch.Tensor, out_found: torch.Tensor,
                      now: int = 0, refresh_ttl: int = 0, stream=None):
+    """Device tensors, or pinned host tensors read/written in place by the kernel."""
     n = keys.shape[0]
-    _dev(keys, "keys", torch.uint8)
-    _dev(out_vals, "out_vals", (torch.int64, torch.uint64))
-    _dev(out_found, "out_found", (torch.uint8, torch.bool))
+    _dev_or_pinned(keys, "keys", torch.uint8)
+    _dev_or_pinned(out_vals, "out_vals", (torch.int64, torch.uint64))
+    _dev_or_pinned(out_found, "out_found", (torch.uint8, torch.bool))
     _check(_lib.ckpp_bulk_lookup(handle, _ptr(keys), n, _ptr(out_vals), _ptr(out_found), now, refresh_ttl,
                                  _stream(stream)), "ckpp_bulk_lookup")
 

@@ -100,6 +100,19 @@ int time_check(ckpp_table* t, uint32_t now) {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CKPP_OK : CKPP_ECUDA; }
 
+// Where a buffer lives: 0 device (or managed), 1 pinned host memory mapped
+// into the device's address space, -1 not reachable by the device.
+int residency(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 0;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer == p) return 1;
+  return -1;
+}
+
 int check_keys(const ckpp_key* keys, uint64_t n) {
   if (n > kMaxBatch) return CKPP_EINVAL;
   if (n && (!keys || !aligned(keys, 16))) return CKPP_EINVAL;
@@ -155,8 +168,11 @@ int ckpp_bulk_lookup(ckpp_table* t, const ckpp_key* keys, uint64_t n, uint64_t* 
   if (n && (!out_vals || !out_found || !aligned(out_vals, 8))) return CKPP_EINVAL;
   if (int rc = time_check(t, now)) return rc;
   if (!n) return CKPP_OK;
+  const int rk = residency(keys), rv = residency(out_vals), rf = residency(out_found);
+  if (rk < 0 || rv < 0 || rf < 0) return CKPP_EINVAL;
+  const bool host_io = rk == 1 || rv == 1 || rf == 1;
   return cuda_rc(launch_lookup(t->view, reinterpret_cast<const uint8_t*>(keys), n, out_vals, out_found, now,
-                               refresh_ttl, reinterpret_cast<cudaStream_t>(stream)));
+                               refresh_ttl, host_io, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int ckpp_bulk_insert(ckpp_table* t, const ckpp_key* keys, const uint64_t* vals, uint64_t n, uint32_t now,

@@ -24,8 +24,10 @@ struct Workspace {
 cudaError_t launch_init_header(uint8_t* base, uint64_t nb, uint32_t slots, uint32_t flags, uint64_t seed,
                                cudaStream_t s);
 
+// host_io: keys and outputs are pinned host memory (read and written in place
+// over NVLink-C2C).
 cudaError_t launch_lookup(const TableView& t, const uint8_t* keys, uint64_t n, uint64_t* out_vals,
-                          uint8_t* out_found, uint32_t now, uint32_t refresh_ttl, cudaStream_t s);
+                          uint8_t* out_found, uint32_t now, uint32_t refresh_ttl, bool host_io, cudaStream_t s);
 
 cudaError_t launch_probe_counts(const TableView& t, const uint8_t* keys, uint64_t n, uint32_t now,
                                 unsigned long long* counts, cudaStream_t s);

@@ -11,8 +11,9 @@
 //             the primary, else of the secondary; leaders with two full buckets
 //             are queued for phase 2.
 //   phase2  - per queued leader: breadth-first search for a cuckoo path without
-//             locks, then execute it backwards, one move at a time, each under
-//             the locks of its two buckets with the move re-validated; retry a
+//             locks (queue in shared memory), then lock every bucket of the path
+//             plus the key's primary, re-validate the path, and move the entries
+//             backwards and store the key, all under those locks; retry a
 //             bounded number of times, else FULL.
 //   fixup   - reset the filter of buckets whose moved counter reached zero off
 //             their lock (the reset of Sec. 4.1, deferred so that it never races
@@ -26,9 +27,7 @@ namespace ckpp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBfsNodes = 128;
-constexpr int kBfsDepth = 4;
-constexpr int kPathAttempts = 8;
+constexpr int kPathAttempts = 16;
 
 __device__ __forceinline__ Key load_key(const uint8_t* keys, uint64_t i) {
   uint64_t a, b;
@@ -128,6 +127,12 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableView t, const uin
 }
 
 // --------------------------------------------------------------- phase 2
+constexpr int kP2Threads = 64;
+constexpr int kBfsNodes = 96;                 // per thread, in shared memory (64 x 96 x 8 B = 48 KB)
+constexpr int kBfsDepth = 4;                  // at most 4 moves
+constexpr int kPathBuckets = kBfsDepth + 1;
+constexpr int kMaxLocks = kPathBuckets + 1;   // the path plus the key's primary
+
 struct Node {
   uint32_t bucket;
   int16_t parent;
@@ -159,85 +164,133 @@ __device__ int try_place(const TableView& t, const Key& k, uint64_t v, const Add
   return placed;
 }
 
-// Breadth-first search over buckets from b1 and b2 (lock-free reads; the moves
-// re-validate). Returns the index of a node whose bucket has a free or dead
-// slot (in hole), or -1.
+// Breadth-first search over buckets from b1 and b2 (lock-free reads; the path
+// is re-validated under its locks). Returns the index of a node whose bucket
+// has a free or dead slot (in hole), or -1.
 __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, Node* q, uint32_t& hole) {
   int nq = 0;
   q[nq++] = Node{a.b1, -1, 0, 0};
   q[nq++] = Node{a.b2, -1, 0, 0};
   for (int qi = 0; qi < nq; ++qi) {
+    const Node cur = q[qi];
     Snap s;
-    snap_bucket(t, q[qi].bucket, s);
-    const uint32_t ctrl = (uint32_t)s.w[3];
-    const uint32_t f = free_mask(t, ctrl, s, now);
+    snap_bucket(t, cur.bucket, s);
+    const uint32_t f = free_mask(t, (uint32_t)s.w[3], s, now);
     if (f) {
       hole = __ffs(f) - 1;
       return qi;
     }
-    if (q[qi].depth >= kBfsDepth) continue;
+    if (cur.depth >= kBfsDepth) continue;
     for (uint32_t sl = 0; sl < kSlots && nq < kBfsNodes; ++sl) {
       uint64_t r[4];
-      ld256_cg(record_ptr(t, q[qi].bucket, sl), r);
+      ld256_cg(record_ptr(t, cur.bucket, sl), r);
       const Addr e = address_of(Key{r[0], r[1]}, t.nb, t.seed);
-      const uint32_t y = (e.b1 == q[qi].bucket) ? e.b2 : e.b1;
+      const uint32_t y = (e.b1 == cur.bucket) ? e.b2 : e.b1;
       bool seen = false;
       for (int j = 0; j < nq; ++j) seen |= (q[j].bucket == y);
-      if (!seen) q[nq++] = Node{y, (int16_t)qi, (uint8_t)sl, (uint8_t)(q[qi].depth + 1)};
+      if (!seen) q[nq++] = Node{y, (int16_t)qi, (uint8_t)sl, (uint8_t)(cur.depth + 1)};
     }
   }
   return -1;
 }
 
-// Move the entry in slot sx of bucket x to free (or dead) slot sy of its other
-// bucket y, under both locks, after re-validating both. Sec. 4.1: a move from
-// the primary to the secondary sets the entry's bits in the primary's filter
-// and increments its counter; the reverse move decrements the counter and
-// resets the filter at zero. 1 moved, 0 stale path, -1 lock timeout.
-__device__ int move_entry(const TableView& t, uint32_t x, uint32_t sx, uint32_t y, uint32_t sy, uint32_t now,
-                          const Workspace& ws) {
-  uint32_t cx, cy;
-  if (!lock_pair(t, x, y, cx, cy)) return -1;
-  int ok = 0;
-  if ((cx >> sx) & 1u) {
-    uint64_t r[4];
-    ld256_cg(record_ptr(t, x, sx), r);
-    const Addr e = address_of(Key{r[0], r[1]}, t.nb, t.seed);
-    const bool from_primary = (e.b1 == x);
-    const bool valid_src = from_primary ? (e.b2 == y) : (e.b2 == x && e.b1 == y);
-    bool dst_free = !((cy >> sy) & 1u);
-    uint32_t dst_exp = 0;
-    if (!dst_free && t.timers) {
-      dst_exp = ld16_cg(expiry_ptr(t, y, sy));
-      dst_free = !alive16(dst_exp, now);
-    }
-    if (valid_src && dst_free) {
-      if ((cy >> sy) & 1u) evict_entry(t, y, sy, cy, ws);
-      st256_cg(record_ptr(t, y, sy), r[0], r[1], r[2], r[3]);
-      st16_cg(tag_ptr(t, y, sy), e.tag);
-      if (t.timers) st16_cg(expiry_ptr(t, y, sy), ld16_cg(expiry_ptr(t, x, sx)));
-      cy |= 1u << sy;
-      if (from_primary) {
-        cy |= 1u << (kInsecShift + sy);
-        atomicOr(reinterpret_cast<unsigned long long*>(bloom_ptr(t, x)), (unsigned long long)e.bits);
-        atomicAdd(moved_ptr(t, x), 1u);
-      } else {
-        cy &= ~(1u << (kInsecShift + sy));
-        if (atomicSub(moved_ptr(t, y), 1u) == 1u) {
-          atomicExch(reinterpret_cast<unsigned long long*>(bloom_ptr(t, y)), 0ull);
-        }
-      }
-      cx &= ~((1u << sx) | (1u << (kInsecShift + sx)));
-      ok = 1;
-    }
+// Move the entry in slot sx of locked bucket x to the free slot sy of locked
+// bucket y, its other bucket. Sec. 4.1: a move from the primary to the
+// secondary sets the entry's bits in the primary's filter and increments its
+// counter; the reverse move decrements the counter and resets the filter at
+// zero (safe: filter bits of y are only ever set under y's lock, held here).
+__device__ void move_locked(const TableView& t, uint32_t x, uint32_t sx, uint32_t& cx, uint32_t y, uint32_t sy,
+                            uint32_t& cy) {
+  uint64_t r[4];
+  ld256_cg(record_ptr(t, x, sx), r);
+  const Addr e = address_of(Key{r[0], r[1]}, t.nb, t.seed);
+  st256_cg(record_ptr(t, y, sy), r[0], r[1], r[2], r[3]);
+  st16_cg(tag_ptr(t, y, sy), e.tag);
+  if (t.timers) st16_cg(expiry_ptr(t, y, sy), ld16_cg(expiry_ptr(t, x, sx)));
+  cy |= 1u << sy;
+  if (e.b1 == x) {
+    cy |= 1u << (kInsecShift + sy);
+    atomicOr(reinterpret_cast<unsigned long long*>(bloom_ptr(t, x)), (unsigned long long)e.bits);
+    atomicAdd(moved_ptr(t, x), 1u);
+  } else {
+    cy &= ~(1u << (kInsecShift + sy));
+    if (atomicSub(moved_ptr(t, y), 1u) == 1u) atomicExch(reinterpret_cast<unsigned long long*>(bloom_ptr(t, y)), 0ull);
   }
-  unlock_pair(t, x, y, cx, cy);
-  return ok;
+  cx &= ~((1u << sx) | (1u << (kInsecShift + sx)));
 }
 
-__global__ void __launch_bounds__(128) insert_phase2(TableView t, const uint8_t* __restrict__ keys,
-                                                     const uint64_t* __restrict__ vals, uint32_t now, uint32_t expiry,
-                                                     uint8_t* __restrict__ status, Workspace ws) {
+// Execute a cuckoo path atomically: lock every bucket on it plus the key's
+// primary (in index order), check that each entry still sits where the search
+// saw it and still has the next bucket as its other bucket and that the end
+// slot is still free or dead, then move the entries backwards (each into the
+// hole ahead of it) and store the new key in the hole left in the root bucket.
+// path[0] is the root (b1 or b2), path[len] the bucket with the hole; slot[j]
+// is the slot of path[j] whose entry moves to path[j + 1].
+// 1 placed, 0 stale path, -1 lock timeout.
+__device__ int execute_path(const TableView& t, const uint32_t (&path)[kPathBuckets],
+                            const uint32_t (&slot)[kPathBuckets], int len, uint32_t hole, const Key& k, uint64_t v,
+                            const Addr& a, uint32_t now, uint32_t expiry, const Workspace& ws) {
+  uint32_t lk[kMaxLocks], cw[kMaxLocks];
+  int nl = 0;
+  bool has_b1 = false;
+  for (int j = 0; j <= len; ++j) {
+    lk[nl++] = path[j];
+    has_b1 |= (path[j] == a.b1);
+  }
+  if (!has_b1) lk[nl++] = a.b1;
+  for (int i = 1; i < nl; ++i)  // insertion sort: a global lock order
+    for (int j = i; j > 0 && lk[j - 1] > lk[j]; --j) {
+      const uint32_t tmp = lk[j];
+      lk[j] = lk[j - 1];
+      lk[j - 1] = tmp;
+    }
+  for (int i = 0; i < nl; ++i) {
+    if (!lock_bucket(t, lk[i], cw[i])) {
+      for (int j = i - 1; j >= 0; --j) unlock_bucket(t, lk[j], cw[j]);
+      return -1;
+    }
+  }
+  auto idx = [&](uint32_t b) {
+    int r = 0;
+    for (int i = 0; i < nl; ++i) r = (lk[i] == b) ? i : r;
+    return r;
+  };
+  bool ok = true;
+  for (int j = 0; j < len && ok; ++j) {
+    if (!((cw[idx(path[j])] >> slot[j]) & 1u)) {
+      ok = false;
+      break;
+    }
+    uint64_t r[4];
+    ld256_cg(record_ptr(t, path[j], slot[j]), r);
+    const Addr e = address_of(Key{r[0], r[1]}, t.nb, t.seed);
+    const uint32_t other = (e.b1 == path[j]) ? e.b2 : (e.b2 == path[j] ? e.b1 : 0xFFFFFFFFu);
+    ok = (other == path[j + 1]);
+  }
+  const int ie = idx(path[len]);
+  const bool end_busy = (cw[ie] >> hole) & 1u;
+  if (ok && end_busy) ok = t.timers && !alive16(ld16_cg(expiry_ptr(t, path[len], hole)), now);
+  int rc = 0;
+  if (ok) {
+    if (end_busy) evict_entry(t, path[len], hole, cw[ie], ws);
+    uint32_t dst_s = hole;
+    for (int j = len - 1; j >= 0; --j) {
+      move_locked(t, path[j], slot[j], cw[idx(path[j])], path[j + 1], dst_s, cw[idx(path[j + 1])]);
+      dst_s = slot[j];
+    }
+    place_entry(t, path[0], dst_s, k, v, a, expiry, cw[idx(path[0])]);
+    rc = 1;
+  }
+  for (int i = nl - 1; i >= 0; --i) unlock_bucket(t, lk[i], cw[i]);
+  return rc;
+}
+
+__global__ void __launch_bounds__(kP2Threads) insert_phase2(TableView t, const uint8_t* __restrict__ keys,
+                                                            const uint64_t* __restrict__ vals, uint32_t now,
+                                                            uint32_t expiry, uint8_t* __restrict__ status,
+                                                            Workspace ws) {
+  __shared__ Node queues[kP2Threads][kBfsNodes];
+  Node* q = queues[threadIdx.x];
   const uint32_t count = ld32_cg(ws.counters + 0);
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
     const uint32_t i = ws.pending[j];
@@ -245,7 +298,6 @@ __global__ void __launch_bounds__(128) insert_phase2(TableView t, const uint8_t*
     const Key k = load_key(keys, i);
     const Addr a = address_of(k, t.nb, t.seed);
     uint8_t st = kStFull;
-    Node q[kBfsNodes];
     for (int attempt = 0; attempt < kPathAttempts; ++attempt) {
       const int placed = try_place(t, k, v, a, now, expiry, ws);
       if (placed != 0) {
@@ -253,18 +305,17 @@ __global__ void __launch_bounds__(128) insert_phase2(TableView t, const uint8_t*
         break;
       }
       uint32_t hole = 0;
-      int node = bfs(t, a, now, q, hole);
-      if (node < 0) break;  // no cuckoo path within the search bound: FULL
-      // Execute the path backwards: each entry moves into the hole ahead of it.
-      int r = 1;
-      while (q[node].parent >= 0 && r > 0) {
-        const int par = q[node].parent;
-        r = move_entry(t, q[par].bucket, q[node].slot, q[node].bucket, hole, now, ws);
-        hole = q[node].slot;
-        node = par;
+      const int end = bfs(t, a, now, q, hole);
+      if (end < 0) break;  // no cuckoo path within the search bound: FULL
+      uint32_t path[kPathBuckets], slot[kPathBuckets];
+      const int len = q[end].depth;
+      for (int node = end; node >= 0; node = q[node].parent) {
+        path[q[node].depth] = q[node].bucket;
+        if (q[node].depth > 0) slot[q[node].depth - 1] = q[node].slot;
       }
-      if (r < 0) {
-        st = kStBusy;
+      const int r = execute_path(t, path, slot, len, hole, k, v, a, now, expiry, ws);
+      if (r != 0) {
+        st = r > 0 ? kStInserted : kStBusy;
         break;
       }
     }
@@ -351,8 +402,8 @@ cudaError_t launch_insert(const TableView& t, const uint8_t* keys, const uint64_
   if (e != cudaSuccess) return e;
   insert_phase1<<<grid_for(n, kThreads), kThreads, 0, s>>>(t, keys, vals, n, now, expiry, status, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const unsigned p2_blocks = (unsigned)std::min<uint64_t>(grid_for(n, 128), 152 * 4);
-  insert_phase2<<<p2_blocks, 128, 0, s>>>(t, keys, vals, now, expiry, status, ws);
+  const unsigned p2_blocks = (unsigned)std::min<uint64_t>(grid_for(n, kP2Threads), 152 * 4);
+  insert_phase2<<<p2_blocks, kP2Threads, 0, s>>>(t, keys, vals, now, expiry, status, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bloom_fixup<<<152 * 2, 256, 0, s>>>(t, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -33,7 +33,10 @@ __device__ __forceinline__ int confirm(const TableView& t, uint32_t b, uint32_t 
   return -1;
 }
 
-template <bool kTimers, bool kCount>
+// kHostIO: keys and results live in pinned host memory, reached over
+// NVLink-C2C by the loads and stores themselves (no staging copy); such keys
+// are read with plain loads, without the read-only path or L2 hints.
+template <bool kTimers, bool kCount, bool kHostIO>
 __global__ void __launch_bounds__(256) lookup_kernel(TableView t, const uint8_t* __restrict__ keys, uint64_t n,
                                                      uint64_t* __restrict__ out_vals,
                                                      uint8_t* __restrict__ out_found, uint32_t now,
@@ -43,7 +46,13 @@ __global__ void __launch_bounds__(256) lookup_kernel(TableView t, const uint8_t*
   if (i < n) {
     const uint64_t keep = policy_evict_last();
     const uint64_t stream = policy_evict_first();
-    const Key k = ld_key_ro(keys + 16 * i, stream);
+    Key k;
+    if (kHostIO) {
+      const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(keys + 16 * i);
+      k = Key{kk.x, kk.y};
+    } else {
+      k = ld_key_ro(keys + 16 * i, stream);
+    }
     const Addr a = address_of(k, t.nb, t.seed);
     uint64_t h[4], rec[4];
     uint32_t expiry = 0;
@@ -86,19 +95,23 @@ __global__ void __launch_bounds__(256) lookup_kernel(TableView t, const uint8_t*
 
 constexpr int kLookupThreads = 256;
 
-template <bool kTimers, bool kCount>
+template <bool kTimers, bool kCount, bool kHostIO = false>
 cudaError_t launch(const TableView& t, const uint8_t* keys, uint64_t n, uint64_t* out_vals, uint8_t* out_found,
                    uint32_t now, uint32_t refresh_ttl, unsigned long long* counts, cudaStream_t s) {
   const uint64_t blocks = (n + kLookupThreads - 1) / kLookupThreads;
-  lookup_kernel<kTimers, kCount><<<(unsigned)blocks, kLookupThreads, 0, s>>>(t, keys, n, out_vals, out_found, now,
-                                                                            refresh_ttl, counts);
+  lookup_kernel<kTimers, kCount, kHostIO><<<(unsigned)blocks, kLookupThreads, 0, s>>>(
+      t, keys, n, out_vals, out_found, now, refresh_ttl, counts);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_lookup(const TableView& t, const uint8_t* keys, uint64_t n, uint64_t* out_vals,
-                          uint8_t* out_found, uint32_t now, uint32_t refresh_ttl, cudaStream_t s) {
+                          uint8_t* out_found, uint32_t now, uint32_t refresh_ttl, bool host_io, cudaStream_t s) {
+  if (host_io) {
+    if (t.timers) return launch<true, false, true>(t, keys, n, out_vals, out_found, now, refresh_ttl, nullptr, s);
+    return launch<false, false, true>(t, keys, n, out_vals, out_found, now, 0, nullptr, s);
+  }
   if (t.timers) return launch<true, false>(t, keys, n, out_vals, out_found, now, refresh_ttl, nullptr, s);
   return launch<false, false>(t, keys, n, out_vals, out_found, now, 0, nullptr, s);
 }

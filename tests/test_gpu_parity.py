@@ -198,6 +198,25 @@ def test_near_full_tiny_table_stays_consistent(K):
     assert g.sync_status() == 0
 
 
+@pytest.mark.parametrize("timers", [False, True])
+def test_single_batch_fill_to_lf095(timers):
+    """One batch taking an empty table to LF 0.95 (heavy concurrent cuckoo
+    displacement): every key INSERTED, invariants hold, the live set is exact."""
+    nb = 1 << 16
+    m = int(0.95 * nb * 8)
+    f = W.fill(41, m)
+    g = FT(nb, timers=timers, seed=41)
+    st = g.insert(f.keys, f.values, 5, 900 if timers else 0).cpu().numpy()
+    assert (st == oracle.INSERTED).all(), np.unique(st, return_counts=True)
+    assert g.sync_status() == 0
+    d = download(g)
+    assert d.check() == []
+    live = d.live(5)
+    assert len(live) == m
+    v, fd = g.lookup(f.keys, 5)
+    assert fd.cpu().numpy().all() and (np_vals(v) == f.values).all()
+
+
 def test_two_bucket_table():
     """The smallest table (2 buckets): every key's buckets are {0, 1}."""
     keys = W.make_keys(32, 62, 16)
