@@ -138,6 +138,70 @@ int ckpp_destroy(ckpp_table* table);
 int ckpp_bulk_lookup(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint64_t* out_vals,
                      uint8_t* out_found, uint32_t now, uint16_t refresh_ttl, ckpp_stream_t stream);
 
+/* Lookup strategies. CKPP_LOOKUP_BLOOM is Cuckoo++ (Sec. 4.1) and what
+ * ckpp_bulk_lookup does; the other two are the strategies of Sec. 3 on the same
+ * table, kept for measuring what the filter saves: OPTIMISTIC reads the
+ * secondary bucket after every primary miss, PESSIMISTIC reads both buckets of
+ * every key. All three return identical results. */
+#define CKPP_LOOKUP_BLOOM 0
+#define CKPP_LOOKUP_OPTIMISTIC 1
+#define CKPP_LOOKUP_PESSIMISTIC 2
+
+/* ckpp_bulk_lookup with an explicit strategy (device buffers only).
+ * Errors: CKPP_EINVAL (also for an unknown variant), CKPP_ESTALE, CKPP_ECUDA. */
+int ckpp_bulk_lookup_variant(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint64_t* out_vals,
+                             uint8_t* out_found, uint32_t now, uint16_t refresh_ttl, int variant,
+                             ckpp_stream_t stream);
+
+/* ---- Batched form: many tables, one launch --------------------------------
+ * One persistent kernel serves the lookup jobs of many independent tables (the
+ * GPU counterpart of the paper's one private table per core, Sec. 2 and 5.3).
+ * Jobs live in device memory and may change between launches, so the launch can
+ * be captured in a CUDA graph once and replayed. */
+#define CKPP_BATCH_MAX_JOBS 8192
+
+typedef struct ckpp_lookup_job {
+  const ckpp_key* keys; /* device, 16-byte aligned, n keys */
+  uint64_t* out_vals;   /* device, n values (0 on a miss) */
+  uint8_t* out_found;   /* device, n flags */
+  uint32_t n;           /* keys in this job (0 allowed) */
+  uint32_t table;       /* index into the batch's table list; jobs naming no table are skipped */
+} ckpp_lookup_job;
+
+/* Kernel configuration: threads per key 1, 2, 4 or 8; group depth (keys in
+ * flight per thread) 1, 2 or 4 with one thread per key, else 1; persistent
+ * blocks per SM 1..16. */
+typedef struct ckpp_batch_tuning {
+  uint32_t threads_per_key;
+  uint32_t group_depth;
+  uint32_t blocks_per_sm;
+  uint32_t reserved;
+} ckpp_batch_tuning;
+
+typedef struct ckpp_batch ckpp_batch;
+
+/* Device bytes of a batch descriptor for n_tables tables. */
+size_t ckpp_batch_bytes(uint32_t n_tables);
+
+/* Describe tables[0..n_tables) (handles of tables on the current device) in
+ * dev_buf (>= ckpp_batch_bytes, 256-byte aligned, caller-owned) on `stream`.
+ * The tables must outlive the batch. Errors: CKPP_EINVAL, CKPP_ECUDA. */
+int ckpp_batch_create(ckpp_batch** out, ckpp_table* const* tables, uint32_t n_tables, void* dev_buf, size_t bytes,
+                      ckpp_stream_t stream);
+
+/* Release the host handle (dev_buf stays the caller's). */
+int ckpp_batch_destroy(ckpp_batch* batch);
+
+/* Look up every job's keys in its table (filter-pruned, as ckpp_bulk_lookup,
+ * without refresh) in one launch. d_jobs: device array of at least max_jobs
+ * jobs; d_n_jobs: NULL (use max_jobs) or a device uint32 job count, clamped to
+ * max_jobs. tuning: NULL for the default (1 thread per key, depth 1, 4 blocks
+ * per SM). The job data is not validated on the host: every job's pointers must
+ * be valid device memory. Errors: CKPP_EINVAL (max_jobs above
+ * CKPP_BATCH_MAX_JOBS, bad tuning), CKPP_ESTALE (a timers table), CKPP_ECUDA. */
+int ckpp_batch_lookup(ckpp_batch* batch, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,
+                      uint32_t now, const ckpp_batch_tuning* tuning, ckpp_stream_t stream);
+
 /* Batched insert-or-update (Sec. 2 cuckoo insertion; Sec. 4.1 filter and moved
  * counter upkeep, including moves along a cuckoo path; Sec. 4.2 dead slots are
  * reused as free). The batch has the result of inserting keys one by one in
@@ -176,12 +240,13 @@ int ckpp_expire(ckpp_table* table, uint32_t now, uint64_t* d_n_expired, ckpp_str
  * `stream`. Errors: CKPP_EINVAL, CKPP_ECUDA. */
 int ckpp_stats_get(ckpp_table* table, uint32_t now, ckpp_stats* host_out, ckpp_stream_t stream);
 
-/* For a lookup batch, count the memory reads the method makes without
- * performing the lookup (no refresh): d_counts[0] += primary bucket reads (n),
- * d_counts[1] += secondary bucket reads, d_counts[2] += key/value record reads.
- * d_counts is a device uint64[3]. Used to state a batch's algorithmic bytes.
+/* For a lookup batch, count the memory reads a lookup strategy (variant, see
+ * ckpp_bulk_lookup_variant) makes without performing the lookup (no refresh):
+ * d_counts[0] += primary bucket reads (n), d_counts[1] += secondary bucket
+ * reads, d_counts[2] += key/value record reads. d_counts is a device
+ * uint64[3]. Used to state a batch's algorithmic bytes.
  * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
-int ckpp_lookup_probe_counts(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32_t now,
+int ckpp_lookup_probe_counts(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32_t now, int variant,
                              uint64_t* d_counts, ckpp_stream_t stream);
 
 /* Synchronise `stream`, then read and clear the table's latched device error

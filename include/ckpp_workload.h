@@ -1,0 +1,43 @@
+/*
+ * ckpp_workload.h -- device-side generator of the synthetic 5-tuple traffic
+ * (libckpp_workload.so). Not part of the method: it draws the same inputs as
+ * paper_1712_09624_gb300/workload.py, bit for bit, directly in device memory,
+ * so that workloads of billions of keys need no host generation or upload.
+ *
+ * Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random
+ * Numbers: As Easy as 1, 2, 3", SC'11), key (seed, stream); raw output t is word
+ * t % 4 of the block for counter t / 4 + 1 (the stream numpy's Philox bit
+ * generator produces). Key layout as ckpp_key in ckpp.h.
+ *
+ * All output pointers are caller-owned device memory; calls are asynchronous
+ * on `stream`. Return: 0, or -1 for bad arguments, -2 for a CUDA error.
+ */
+#ifndef CKPP_WORKLOAD_H
+#define CKPP_WORKLOAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ckpp_wl_stream_t;
+
+/* Keys first .. first+n-1 of the fill of `seed` (workload.fill(seed, m).keys
+ * for any m > first+n-1) into out_keys [n][16] (16-byte aligned), and their
+ * values (= index) into out_vals [n] if not NULL. */
+int ckpp_wl_fill_keys(uint64_t seed, uint64_t first, uint64_t n, uint8_t* out_keys, uint64_t* out_vals,
+                      ckpp_wl_stream_t stream);
+
+/* workload.lookup_batch(seed, n, workload.fill(seed, n_inserted), neg_rate,
+ * batch_id): keys [n][16], expected found flags [n] and values [n] (either
+ * expectation pointer may be NULL). */
+int ckpp_wl_lookup_batch(uint64_t seed, uint64_t batch_id, uint64_t n, uint64_t n_inserted, double neg_rate,
+                         uint8_t* out_keys, uint8_t* expect_found, uint64_t* expect_value, ckpp_wl_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKPP_WORKLOAD_H */

@@ -73,8 +73,12 @@ enum { OC_OK = 0, OC_EINVAL = -1, OC_ESTALE = -3 };
 
 #define OC_ALIVE_WINDOW 1024u  /* Sec. 4.2: expiry at most 1024 units ahead      */
 #define OC_MAX_STALE 64512u    /* Sec. 4.2: 65536 - 1024, the scan period bound   */
+#ifndef OC_BFS_MAX_NODES
 #define OC_BFS_MAX_NODES 1024
+#endif
+#ifndef OC_BFS_MAX_DEPTH
 #define OC_BFS_MAX_DEPTH 5
+#endif
 #define OC_SEED2_XOR 0x9E3779B97F4A7C15ULL
 
 typedef struct {

@@ -35,6 +35,21 @@ class ckpp_stats(C.Structure):
                 ("moved_hist", C.c_uint64 * 16)]
 
 
+class ckpp_lookup_job(C.Structure):
+    _fields_ = [("keys", C.c_void_p), ("out_vals", C.c_void_p), ("out_found", C.c_void_p), ("n", C.c_uint32),
+                ("table", C.c_uint32)]
+
+
+class ckpp_batch_tuning(C.Structure):
+    _fields_ = [("threads_per_key", C.c_uint32), ("group_depth", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+LOOKUP_BLOOM, LOOKUP_OPTIMISTIC, LOOKUP_PESSIMISTIC = 0, 1, 2
+BATCH_MAX_JOBS = 8192
+JOB_BYTES = C.sizeof(ckpp_lookup_job)
+
+
 class CkppError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {_lib.ckpp_error_string(code).decode()} ({code})")
@@ -58,7 +73,12 @@ def _load():
         "ckpp_bulk_delete": (C.c_int, [vp, vp, u64, u32, vp, vp, sz, vp]),
         "ckpp_expire": (C.c_int, [vp, u32, vp, vp]),
         "ckpp_stats_get": (C.c_int, [vp, u32, C.POINTER(ckpp_stats), vp]),
-        "ckpp_lookup_probe_counts": (C.c_int, [vp, vp, u64, u32, vp, vp]),
+        "ckpp_lookup_probe_counts": (C.c_int, [vp, vp, u64, u32, C.c_int, vp, vp]),
+        "ckpp_bulk_lookup_variant": (C.c_int, [vp, vp, u64, vp, vp, u32, u16, C.c_int, vp]),
+        "ckpp_batch_bytes": (sz, [u32]),
+        "ckpp_batch_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), u32, vp, sz, vp]),
+        "ckpp_batch_destroy": (C.c_int, [vp]),
+        "ckpp_batch_lookup": (C.c_int, [vp, vp, u32, vp, u32, C.POINTER(ckpp_batch_tuning), vp]),
         "ckpp_sync_status": (C.c_int, [vp, vp]),
         "ckpp_get_geometry": (C.c_int, [vp, gp]),
         "ckpp_get_last_scan": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int)]),
@@ -76,7 +96,8 @@ _lib = _load()
 EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_destroy", "ckpp_bulk_lookup",
             "ckpp_bulk_insert", "ckpp_bulk_delete", "ckpp_expire", "ckpp_stats_get", "ckpp_lookup_probe_counts",
             "ckpp_sync_status", "ckpp_get_geometry", "ckpp_get_last_scan", "ckpp_error_string",
-            "ckpp_abi_version")
+            "ckpp_abi_version", "ckpp_bulk_lookup_variant", "ckpp_batch_bytes",
+            "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup")
 
 
 def library():
@@ -189,11 +210,51 @@ def ckpp_stats_get(handle: int, now: int = 0, stream=None) -> dict:
     return out
 
 
-def ckpp_lookup_probe_counts(handle: int, keys: torch.Tensor, d_counts: torch.Tensor, now: int = 0, stream=None):
+def ckpp_lookup_probe_counts(handle: int, keys: torch.Tensor, d_counts: torch.Tensor, now: int = 0,
+                             variant: int = LOOKUP_BLOOM, stream=None):
     _dev(keys, "keys", torch.uint8)
     _dev(d_counts, "d_counts", (torch.int64, torch.uint64))
-    _check(_lib.ckpp_lookup_probe_counts(handle, _ptr(keys), keys.shape[0], now, _ptr(d_counts), _stream(stream)),
-           "ckpp_lookup_probe_counts")
+    _check(_lib.ckpp_lookup_probe_counts(handle, _ptr(keys), keys.shape[0], now, variant, _ptr(d_counts),
+                                         _stream(stream)), "ckpp_lookup_probe_counts")
+
+
+def ckpp_bulk_lookup_variant(handle: int, keys: torch.Tensor, out_vals: torch.Tensor, out_found: torch.Tensor,
+                             now: int = 0, refresh_ttl: int = 0, variant: int = LOOKUP_BLOOM, stream=None):
+    _dev(keys, "keys", torch.uint8)
+    _dev(out_vals, "out_vals", (torch.int64, torch.uint64))
+    _dev(out_found, "out_found", (torch.uint8, torch.bool))
+    _check(_lib.ckpp_bulk_lookup_variant(handle, _ptr(keys), keys.shape[0], _ptr(out_vals), _ptr(out_found), now,
+                                         refresh_ttl, variant, _stream(stream)), "ckpp_bulk_lookup_variant")
+
+
+def ckpp_batch_bytes(n_tables: int) -> int:
+    return int(_lib.ckpp_batch_bytes(n_tables))
+
+
+def ckpp_batch_create(handles, buf: torch.Tensor, stream=None) -> int:
+    _dev(buf, "buf", torch.uint8)
+    arr = (C.c_void_p * len(handles))(*handles)
+    h = C.c_void_p()
+    _check(_lib.ckpp_batch_create(C.byref(h), arr, len(handles), _ptr(buf), buf.numel(), _stream(stream)),
+           "ckpp_batch_create")
+    return h.value
+
+
+def ckpp_batch_destroy(handle: int):
+    _check(_lib.ckpp_batch_destroy(handle), "ckpp_batch_destroy")
+
+
+def ckpp_batch_lookup(handle: int, d_jobs: torch.Tensor, max_jobs: int, d_n_jobs: torch.Tensor | None = None,
+                      now: int = 0, tuning: tuple[int, int, int] | None = None, stream=None):
+    """d_jobs: device uint8 tensor holding max_jobs ckpp_lookup_job records."""
+    _dev(d_jobs, "d_jobs", torch.uint8)
+    if d_jobs.numel() < max_jobs * JOB_BYTES:
+        raise ValueError("d_jobs holds fewer than max_jobs jobs")
+    if d_n_jobs is not None:
+        _dev(d_n_jobs, "d_n_jobs", (torch.int32, torch.uint32))
+    tn = None if tuning is None else C.byref(ckpp_batch_tuning(tuning[0], tuning[1], tuning[2], 0))
+    _check(_lib.ckpp_batch_lookup(handle, _ptr(d_jobs), max_jobs, _ptr(d_n_jobs), now, tn, _stream(stream)),
+           "ckpp_batch_lookup")
 
 
 def ckpp_sync_status(handle: int, stream=None) -> int:

@@ -18,7 +18,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libckpp.so")
+WL_LIB = os.path.join(HERE, "libckpp_workload.so")
 HEADER = os.path.join(ROOT, "include", "ckpp.h")
+WL_HEADER = os.path.join(ROOT, "include", "ckpp_workload.h")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
@@ -36,16 +38,14 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))) + [HEADER]
-    if not force and not _stale(LIB, sources + headers + [__file__]):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def _build_lib(lib: str, sources: list[str], headers: list[str], objdir: str, force: bool, verbose: bool) -> str:
+    if not force and not _stale(lib, sources + headers + [__file__]):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -58,13 +58,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, len(sources))) as ex:
         objs = list(ex.map(compile_one, sources))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Build libckpp.so (the method) and libckpp_workload.so (device-side
+    synthetic traffic); returns the path of libckpp.so."""
+    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))) + [HEADER]
+    wl_sources = sorted(glob.glob(os.path.join(CSRC, "workload", "*.cu")))
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        f1 = ex.submit(_build_lib, LIB, sources, headers, BUILD, force, verbose)
+        f2 = ex.submit(_build_lib, WL_LIB, wl_sources, [WL_HEADER], os.path.join(BUILD, "workload"), force, verbose)
+        f2.result()
+        return f1.result()
 
 
 if __name__ == "__main__":

@@ -5,121 +5,13 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
-#include "../../include/ckpp.h"
-#include "ckpp_kernels.h"
+#include "api_internal.h"
 
 using namespace ckpp;
+using namespace ckpp::api;
 
-struct ckpp_table {
-  ckpp_geometry geo;
-  uint8_t* base;
-  size_t bytes;
-  TableView view;
-  int have_epoch;
-  uint32_t last_scan;
-};
-
-namespace {
-
-constexpr size_t kAlign = 256;
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
-
-bool geometry_ok(const ckpp_geometry* g) {
-  return g && g->n_buckets >= 2 && g->n_buckets <= 0xFFFFFFFFull && g->slots_per_bucket == kSlots &&
-         (g->flags & ~CKPP_TIMERS) == 0;
-}
-
-uint32_t bucket_shift(const ckpp_geometry* g) { return (g->flags & CKPP_TIMERS) ? 6u : 5u; }
-
-size_t table_bytes(const ckpp_geometry* g) {
-  return kHeaderBytes + (size_t)g->n_buckets * ((size_t)1 << bucket_shift(g)) +
-         (size_t)g->n_buckets * kSlots * kRecordBytes;
-}
-
-// Workspace of an n-key batch: counters | set_first[m] | set_last[m] |
-// slot_of[n] | pending[n] | fixup[fix_cap], each part 256-byte aligned.
-struct WsLayout {
-  uint64_t m;
-  uint32_t fix_cap;
-  size_t off_first, off_last, off_slot, off_pending, off_fixup, total;
-};
-
-WsLayout ws_layout(uint64_t n) {
-  WsLayout L;
-  uint64_t m = 64;
-  while (m < 2 * n) m <<= 1;
-  L.m = m;
-  L.fix_cap = (uint32_t)std::min<uint64_t>(n, 1ull << 22) + 64;
-  size_t off = kAlign;  // counters
-  L.off_first = off;
-  off = align_up(off + 4 * m, kAlign);
-  L.off_last = off;
-  off = align_up(off + 4 * m, kAlign);
-  L.off_slot = off;
-  off = align_up(off + 4 * n, kAlign);
-  L.off_pending = off;
-  off = align_up(off + 4 * n, kAlign);
-  L.off_fixup = off;
-  off = align_up(off + 4 * (size_t)L.fix_cap, kAlign);
-  L.total = off;
-  return L;
-}
-
-int prepare_workspace(uint64_t n, void* workspace, size_t bytes, cudaStream_t s, Workspace& ws) {
-  const WsLayout L = ws_layout(n);
-  if (!workspace || bytes < L.total || !aligned(workspace, kAlign)) return CKPP_EINVAL;
-  uint8_t* w = static_cast<uint8_t*>(workspace);
-  ws.counters = reinterpret_cast<uint32_t*>(w);
-  ws.set_first = reinterpret_cast<uint32_t*>(w + L.off_first);
-  ws.set_last = reinterpret_cast<uint32_t*>(w + L.off_last);
-  ws.slot_of = reinterpret_cast<uint32_t*>(w + L.off_slot);
-  ws.pending = reinterpret_cast<uint32_t*>(w + L.off_pending);
-  ws.fixup = reinterpret_cast<uint32_t*>(w + L.off_fixup);
-  ws.m_mask = (uint32_t)(L.m - 1);
-  ws.fix_cap = L.fix_cap;
-  if (cudaMemsetAsync(w, 0, kAlign, s) != cudaSuccess) return CKPP_ECUDA;
-  if (cudaMemsetAsync(ws.set_first, 0xFF, 4 * L.m, s) != cudaSuccess) return CKPP_ECUDA;
-  if (cudaMemsetAsync(ws.set_last, 0, 4 * L.m, s) != cudaSuccess) return CKPP_ECUDA;
-  return CKPP_OK;
-}
-
-// Sec. 4.2: a timed call more than 64512 units after the last scan could see
-// expired 16-bit timers wrap around and revive.
-int time_check(ckpp_table* t, uint32_t now) {
-  if (!(t->geo.flags & CKPP_TIMERS)) return CKPP_OK;
-  if (!t->have_epoch) {
-    t->have_epoch = 1;
-    t->last_scan = now;
-  }
-  return (uint32_t)(now - t->last_scan) > kMaxStale ? CKPP_ESTALE : CKPP_OK;
-}
-
-int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CKPP_OK : CKPP_ECUDA; }
-
-// Where a buffer lives: 0 device (or managed), 1 pinned host memory mapped
-// into the device's address space, -1 not reachable by the device.
-int residency(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 0;
-  if (a.type == cudaMemoryTypeHost && a.devicePointer == p) return 1;
-  return -1;
-}
-
-int check_keys(const ckpp_key* keys, uint64_t n) {
-  if (n > kMaxBatch) return CKPP_EINVAL;
-  if (n && (!keys || !aligned(keys, 16))) return CKPP_EINVAL;
-  return CKPP_OK;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -172,7 +64,18 @@ int ckpp_bulk_lookup(ckpp_table* t, const ckpp_key* keys, uint64_t n, uint64_t* 
   if (rk < 0 || rv < 0 || rf < 0) return CKPP_EINVAL;
   const bool host_io = rk == 1 || rv == 1 || rf == 1;
   return cuda_rc(launch_lookup(t->view, reinterpret_cast<const uint8_t*>(keys), n, out_vals, out_found, now,
-                               refresh_ttl, host_io, reinterpret_cast<cudaStream_t>(stream)));
+                               refresh_ttl, host_io, CKPP_LOOKUP_BLOOM, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ckpp_bulk_lookup_variant(ckpp_table* t, const ckpp_key* keys, uint64_t n, uint64_t* out_vals, uint8_t* out_found,
+                             uint32_t now, uint16_t refresh_ttl, int variant, ckpp_stream_t stream) {
+  if (!t || check_keys(keys, n) || refresh_ttl >= kAliveWindow) return CKPP_EINVAL;
+  if (variant < CKPP_LOOKUP_BLOOM || variant > CKPP_LOOKUP_PESSIMISTIC) return CKPP_EINVAL;
+  if (n && (!out_vals || !out_found || !aligned(out_vals, 8))) return CKPP_EINVAL;
+  if (int rc = time_check(t, now)) return rc;
+  if (!n) return CKPP_OK;
+  return cuda_rc(launch_lookup(t->view, reinterpret_cast<const uint8_t*>(keys), n, out_vals, out_found, now,
+                               refresh_ttl, false, variant, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int ckpp_bulk_insert(ckpp_table* t, const ckpp_key* keys, const uint64_t* vals, uint64_t n, uint32_t now,
@@ -233,14 +136,76 @@ int ckpp_stats_get(ckpp_table* t, uint32_t now, ckpp_stats* out, ckpp_stream_t s
   return CKPP_OK;
 }
 
-int ckpp_lookup_probe_counts(ckpp_table* t, const ckpp_key* keys, uint64_t n, uint32_t now, uint64_t* d_counts,
-                             ckpp_stream_t stream) {
+int ckpp_lookup_probe_counts(ckpp_table* t, const ckpp_key* keys, uint64_t n, uint32_t now, int variant,
+                             uint64_t* d_counts, ckpp_stream_t stream) {
   if (!t || check_keys(keys, n) || !d_counts || !aligned(d_counts, 8)) return CKPP_EINVAL;
+  if (variant < CKPP_LOOKUP_BLOOM || variant > CKPP_LOOKUP_PESSIMISTIC) return CKPP_EINVAL;
   if (int rc = time_check(t, now)) return rc;
   if (!n) return CKPP_OK;
-  return cuda_rc(launch_probe_counts(t->view, reinterpret_cast<const uint8_t*>(keys), n, now,
+  return cuda_rc(launch_probe_counts(t->view, reinterpret_cast<const uint8_t*>(keys), n, now, variant,
                                      reinterpret_cast<unsigned long long*>(d_counts),
                                      reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ------------------------------------------------------------ batched form
+
+struct ckpp_batch {
+  std::vector<ckpp_table*> tables;
+  std::vector<TableView> host_views;  // kept alive for the copy to the device
+  TableView* dev_views;
+  int sms;
+};
+
+size_t ckpp_batch_bytes(uint32_t n_tables) { return align_up((size_t)n_tables * sizeof(TableView), kAlign); }
+
+int ckpp_batch_create(ckpp_batch** out, ckpp_table* const* tables, uint32_t n_tables, void* dev_buf, size_t bytes,
+                      ckpp_stream_t stream) {
+  if (!out || !tables || n_tables == 0 || !dev_buf || !aligned(dev_buf, kAlign) ||
+      bytes < ckpp_batch_bytes(n_tables))
+    return CKPP_EINVAL;
+  for (uint32_t i = 0; i < n_tables; ++i)
+    if (!tables[i]) return CKPP_EINVAL;
+  ckpp_batch* b = new (std::nothrow) ckpp_batch;
+  if (!b) return CKPP_EINVAL;
+  b->tables.assign(tables, tables + n_tables);
+  b->host_views.resize(n_tables);
+  for (uint32_t i = 0; i < n_tables; ++i) b->host_views[i] = tables[i]->view;
+  b->dev_views = static_cast<TableView*>(dev_buf);
+  int dev = 0;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      prepare_batched_lookup() != cudaSuccess ||
+      cudaMemcpyAsync(b->dev_views, b->host_views.data(), n_tables * sizeof(TableView), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    delete b;
+    return CKPP_ECUDA;
+  }
+  *out = b;
+  return CKPP_OK;
+}
+
+int ckpp_batch_destroy(ckpp_batch* b) {
+  if (!b) return CKPP_EINVAL;
+  delete b;
+  return CKPP_OK;
+}
+
+int ckpp_batch_lookup(ckpp_batch* b, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,
+                      uint32_t now, const ckpp_batch_tuning* tuning, ckpp_stream_t stream) {
+  if (!b || max_jobs > kBatchMaxJobs || (max_jobs && !d_jobs)) return CKPP_EINVAL;
+  ckpp_batch_tuning tn = tuning ? *tuning : ckpp_batch_tuning{1, 1, 4, 0};
+  const uint32_t T = tn.threads_per_key, G = tn.group_depth;
+  if (!(T == 1 || T == 2 || T == 4 || T == 8) || !(G == 1 || G == 2 || G == 4) || (T > 1 && G > 1) ||
+      tn.blocks_per_sm < 1 || tn.blocks_per_sm > 16)
+    return CKPP_EINVAL;
+  for (ckpp_table* t : b->tables)
+    if (int rc = time_check(t, now)) return rc;
+  if (!max_jobs) return CKPP_OK;
+  return cuda_rc(launch_batched_lookup(b->dev_views, (uint32_t)b->tables.size(), d_jobs, d_n_jobs, max_jobs, now,
+                                       (int)T, (int)G, tn.blocks_per_sm * (uint32_t)b->sms,
+                                       reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int ckpp_sync_status(ckpp_table* t, ckpp_stream_t stream) {

@@ -35,6 +35,7 @@ constexpr uint32_t kInsecShift = 8;
 constexpr uint32_t kLockBit = 0x80000000u;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint64_t kMaxBatch = 1ull << 30;
+constexpr uint32_t kBatchMaxJobs = 8192;  // jobs per batched launch (prefix sums in shared memory)
 
 // header fields (byte offsets)
 constexpr uint32_t kHdrMagic = 0, kHdrAbi = 4, kHdrBuckets = 8, kHdrSlots = 16, kHdrFlags = 20, kHdrSeed = 24,

@@ -11,11 +11,13 @@ namespace ckpp {
 // Device scratch for one insert or delete batch (carved out of the caller's
 // workspace buffer, see workspace_layout in api.cu).
 struct Workspace {
-  uint32_t* counters;   // [0] pending count, [1] fixup count, [2] fixup overflow flag
+  uint32_t* counters;   // [0] pending count, [1] fixup count, [2] fixup overflow flag, [3] retry count,
+                        // [4] count of the last displacement pass (its list reuses `pending`)
   uint32_t* set_first;  // [m] open-addressing set of batch keys: lowest batch index of the key
   uint32_t* set_last;   // [m] highest batch index of the key
   uint32_t* slot_of;    // [n] set position of each batch key
   uint32_t* pending;    // [n] leaders left for the displacement pass
+  uint32_t* retry;      // [n] leaders the first displacement pass could not place
   uint32_t* fixup;      // [fix_cap] buckets whose moved counter fell to 0 off-lock
   uint32_t m_mask;      // m - 1 (m a power of two >= 2n)
   uint32_t fix_cap;
@@ -25,12 +27,21 @@ cudaError_t launch_init_header(uint8_t* base, uint64_t nb, uint32_t slots, uint3
                                cudaStream_t s);
 
 // host_io: keys and outputs are pinned host memory (read and written in place
-// over NVLink-C2C).
+// over NVLink-C2C). variant: 0 Cuckoo++ (filter-pruned), 1 optimistic,
+// 2 pessimistic (probe.cuh).
 cudaError_t launch_lookup(const TableView& t, const uint8_t* keys, uint64_t n, uint64_t* out_vals,
-                          uint8_t* out_found, uint32_t now, uint32_t refresh_ttl, bool host_io, cudaStream_t s);
+                          uint8_t* out_found, uint32_t now, uint32_t refresh_ttl, bool host_io, int variant,
+                          cudaStream_t s);
 
-cudaError_t launch_probe_counts(const TableView& t, const uint8_t* keys, uint64_t n, uint32_t now,
+cudaError_t launch_probe_counts(const TableView& t, const uint8_t* keys, uint64_t n, uint32_t now, int variant,
                                 unsigned long long* counts, cudaStream_t s);
+
+// Batched form (batched.cu): tables [n_tables] in device memory, jobs a device
+// array of ckpp_lookup_job, n_jobs NULL or a device count (clamped to max_jobs).
+cudaError_t prepare_batched_lookup();
+cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, const void* jobs, const uint32_t* n_jobs,
+                                  uint32_t max_jobs, uint32_t now, int threads_per_key, int group_depth,
+                                  uint32_t blocks, cudaStream_t s);
 
 cudaError_t launch_dedup(const TableView& t, const uint8_t* keys, uint64_t n, const Workspace& ws,
                          cudaStream_t s);

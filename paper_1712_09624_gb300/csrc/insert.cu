@@ -14,7 +14,9 @@
 //             locks (queue in shared memory), then lock every bucket of the path
 //             plus the key's primary, re-validate the path, and move the entries
 //             backwards and store the key, all under those locks; retry a
-//             bounded number of times, else FULL.
+//             bounded number of times. Keys still unplaced get a second pass by
+//             a single block, then a last pass by a single thread (no
+//             contention); only then FULL.
 //   fixup   - reset the filter of buckets whose moved counter reached zero off
 //             their lock (the reset of Sec. 4.1, deferred so that it never races
 //             a concurrent setter).
@@ -127,10 +129,14 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableView t, const uin
 }
 
 // --------------------------------------------------------------- phase 2
+// Search budgets of the three displacement passes (queue in shared memory,
+// at most 48 KB per block): the contended first pass searches 96 buckets up
+// to 4 moves deep per thread; the single-block second pass 192 buckets, 5
+// moves; the single-thread last pass 2048 buckets, 6 moves (the sequential
+// CPU reference searches 1024 buckets, 5 moves).
 constexpr int kP2Threads = 64;
-constexpr int kBfsNodes = 96;                 // per thread, in shared memory (64 x 96 x 8 B = 48 KB)
-constexpr int kBfsDepth = 4;                  // at most 4 moves
-constexpr int kPathBuckets = kBfsDepth + 1;
+constexpr int kMaxDepth = 6;
+constexpr int kPathBuckets = kMaxDepth + 1;
 constexpr int kMaxLocks = kPathBuckets + 1;   // the path plus the key's primary
 
 struct Node {
@@ -167,6 +173,7 @@ __device__ int try_place(const TableView& t, const Key& k, uint64_t v, const Add
 // Breadth-first search over buckets from b1 and b2 (lock-free reads; the path
 // is re-validated under its locks). Returns the index of a node whose bucket
 // has a free or dead slot (in hole), or -1.
+template <int kBfsNodes, int kBfsDepth>
 __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, Node* q, uint32_t& hole) {
   int nq = 0;
   q[nq++] = Node{a.b1, -1, 0, 0};
@@ -285,15 +292,23 @@ __device__ int execute_path(const TableView& t, const uint32_t (&path)[kPathBuck
   return rc;
 }
 
-__global__ void __launch_bounds__(kP2Threads) insert_phase2(TableView t, const uint8_t* __restrict__ keys,
-                                                            const uint64_t* __restrict__ vals, uint32_t now,
-                                                            uint32_t expiry, uint8_t* __restrict__ status,
-                                                            Workspace ws) {
-  __shared__ Node queues[kP2Threads][kBfsNodes];
+// Displacement pass over `list` (count in *count). Keys that find no path
+// are appended to `retry` (when given) for a second, low-contention pass;
+// otherwise they are FULL.
+template <int kThreadsPerBlock, int kBfsNodes, int kBfsDepth>
+__global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableView t, const uint8_t* __restrict__ keys,
+                                                                  const uint64_t* __restrict__ vals, uint32_t now,
+                                                                  uint32_t expiry, uint8_t* __restrict__ status,
+                                                                  Workspace ws, const uint32_t* list,
+                                                                  const uint32_t* count_ptr, uint32_t* retry,
+                                                                  uint32_t* retry_count) {
+  static_assert(kThreadsPerBlock * kBfsNodes * sizeof(Node) <= 48 * 1024, "BFS queues exceed 48 KB");
+  static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
+  __shared__ Node queues[kThreadsPerBlock][kBfsNodes];
   Node* q = queues[threadIdx.x];
-  const uint32_t count = ld32_cg(ws.counters + 0);
+  const uint32_t count = ld32_cg(count_ptr);
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
-    const uint32_t i = ws.pending[j];
+    const uint32_t i = list[j];
     const uint64_t v = vals[ws.set_last[ws.slot_of[i]]];
     const Key k = load_key(keys, i);
     const Addr a = address_of(k, t.nb, t.seed);
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(kP2Threads) insert_phase2(TableView t, const u
         break;
       }
       uint32_t hole = 0;
-      const int end = bfs(t, a, now, q, hole);
+      const int end = bfs<kBfsNodes, kBfsDepth>(t, a, now, q, hole);
       if (end < 0) break;  // no cuckoo path within the search bound: FULL
       uint32_t path[kPathBuckets], slot[kPathBuckets];
       const int len = q[end].depth;
@@ -318,6 +333,10 @@ __global__ void __launch_bounds__(kP2Threads) insert_phase2(TableView t, const u
         st = r > 0 ? kStInserted : kStBusy;
         break;
       }
+    }
+    if (st == kStFull && retry) {
+      retry[atomicAdd(retry_count, 1u)] = i;
+      continue;
     }
     if (st == kStBusy) latch_error(t, kErrLockTimeout);
     status[i] = st;
@@ -403,7 +422,18 @@ cudaError_t launch_insert(const TableView& t, const uint8_t* keys, const uint64_
   insert_phase1<<<grid_for(n, kThreads), kThreads, 0, s>>>(t, keys, vals, n, now, expiry, status, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const unsigned p2_blocks = (unsigned)std::min<uint64_t>(grid_for(n, kP2Threads), 152 * 4);
-  insert_phase2<<<p2_blocks, kP2Threads, 0, s>>>(t, keys, vals, now, expiry, status, ws);
+  insert_phase2<kP2Threads, 96, 4><<<p2_blocks, kP2Threads, 0, s>>>(t, keys, vals, now, expiry, status, ws,
+                                                                    ws.pending, ws.counters + 0, ws.retry,
+                                                                    ws.counters + 3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // second pass, one block: the keys the contended pass could not place
+  insert_phase2<32, 192, 5><<<1, 32, 0, s>>>(t, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 3,
+                                             ws.pending, ws.counters + 4);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // last pass, one thread: no contention left and the widest search; a key
+  // is FULL only if it finds no path
+  insert_phase2<1, 2048, 6><<<1, 1, 0, s>>>(t, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 4,
+                                            nullptr, nullptr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bloom_fixup<<<152 * 2, 256, 0, s>>>(t, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -81,12 +81,21 @@ class FlowTable:
     def stats(self, now: int = 0, stream=None) -> dict:
         return K.ckpp_stats_get(self.handle, now, stream)
 
-    def probe_counts(self, keys, now: int = 0, stream=None) -> torch.Tensor:
-        """[primary bucket reads, secondary bucket reads, record reads] of a lookup batch."""
+    def probe_counts(self, keys, now: int = 0, variant: int = K.LOOKUP_BLOOM, stream=None) -> torch.Tensor:
+        """[primary bucket reads, secondary bucket reads, record reads] a lookup
+        strategy makes on a batch."""
         k = as_device_keys(keys, self.device)
         counts = torch.zeros(3, dtype=torch.int64, device=self.device)
-        K.ckpp_lookup_probe_counts(self.handle, k, counts, now, stream)
+        K.ckpp_lookup_probe_counts(self.handle, k, counts, now, variant, stream)
         return counts
+
+    def lookup_variant(self, keys, variant: int, now: int = 0, stream=None):
+        """Lookup with an explicit strategy (Cuckoo++, optimistic, pessimistic)."""
+        k = as_device_keys(keys, self.device)
+        vals = torch.empty(k.shape[0], dtype=torch.int64, device=self.device)
+        found = torch.empty(k.shape[0], dtype=torch.bool, device=self.device)
+        K.ckpp_bulk_lookup_variant(self.handle, k, vals, found, now, 0, variant, stream)
+        return vals, found
 
     def sync_status(self, stream=None) -> int:
         return K.ckpp_sync_status(self.handle, stream)

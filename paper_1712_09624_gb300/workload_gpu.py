@@ -1,0 +1,59 @@
+"""Device-side twin of ``workload``: the same seeded keys, lookup batches and
+expected answers, drawn directly in device memory by libckpp_workload.so
+(include/ckpp_workload.h). Used where a workload is too large to draw on the
+host (billions of keys); tests check it against ``workload`` bit for bit."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libckpp_workload.so")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1712_09624_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    u64, vp = C.c_uint64, C.c_void_p
+    L.ckpp_wl_fill_keys.restype = C.c_int
+    L.ckpp_wl_fill_keys.argtypes = [u64, u64, u64, vp, vp, vp]
+    L.ckpp_wl_lookup_batch.restype = C.c_int
+    L.ckpp_wl_lookup_batch.argtypes = [u64, u64, u64, u64, C.c_double, vp, vp, vp, vp]
+    return L
+
+
+_lib = _load()
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def fill_keys(seed: int, first: int, n: int, device, stream=None, with_values: bool = True):
+    """Keys [first, first+n) of workload.fill(seed, .) and their values."""
+    keys = torch.empty((n, 16), dtype=torch.uint8, device=device)
+    vals = torch.empty(n, dtype=torch.int64, device=device) if with_values else None
+    rc = _lib.ckpp_wl_fill_keys(seed & (2**64 - 1), first, n, keys.data_ptr() if n else None,
+                                vals.data_ptr() if (vals is not None and n) else None, _stream(stream))
+    if rc:
+        raise RuntimeError(f"ckpp_wl_fill_keys failed ({rc})")
+    return keys, vals
+
+
+def lookup_batch(seed: int, n: int, n_inserted: int, neg_rate: float, batch_id: int = 0, device=None, stream=None):
+    """workload.lookup_batch(seed, n, workload.fill(seed, n_inserted), neg_rate, batch_id) on the device:
+    (keys, expect_found uint8, expect_value int64)."""
+    keys = torch.empty((n, 16), dtype=torch.uint8, device=device)
+    found = torch.empty(n, dtype=torch.uint8, device=device)
+    value = torch.empty(n, dtype=torch.int64, device=device)
+    rc = _lib.ckpp_wl_lookup_batch(seed & (2**64 - 1), batch_id, n, n_inserted, float(neg_rate),
+                                   keys.data_ptr() if n else None, found.data_ptr() if n else None,
+                                   value.data_ptr() if n else None, _stream(stream))
+    if rc:
+        raise RuntimeError(f"ckpp_wl_lookup_batch failed ({rc})")
+    return keys, found, value

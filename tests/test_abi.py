@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "ckpp.h")
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = open(HEADER).read()  # the method's ABI (ckpp_workload.h is checked separately)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(ckpp_[a-z_0-9]+)\s*\(", text)))
 
@@ -23,6 +23,17 @@ def K():
     build.build()
     from paper_1712_09624_gb300 import _ckpp
     return _ckpp
+
+
+def test_workload_library_exports(K):
+    from paper_1712_09624_gb300 import build
+    text = open(os.path.join(ROOT, "include", "ckpp_workload.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = sorted(set(re.findall(r"\b(ckpp_wl_[a-z_0-9]+)\s*\(", text)))
+    assert names == ["ckpp_wl_fill_keys", "ckpp_wl_lookup_batch"]
+    lib = ctypes.CDLL(build.WL_LIB)
+    for name in names:
+        assert hasattr(lib, name)
 
 
 def test_every_declared_symbol_is_exported(K):

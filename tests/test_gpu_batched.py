@@ -1,0 +1,144 @@
+"""Lookup strategies and the batched form against the plain lookup and the
+oracle (needs a GB300)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1712_09624_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+def FT(*a, **kw):
+    from paper_1712_09624_gb300.table import FlowTable
+    return FlowTable(*a, **kw)
+
+
+def test_lookup_strategies_agree_and_count_reads():
+    """Sec. 3 / Sec. 4.1: optimistic, pessimistic and Cuckoo++ lookups return the
+    same answers; they differ only in secondary-bucket reads."""
+    from paper_1712_09624_gb300 import _ckpp as K
+    nb = 1 << 14
+    f = W.fill(51, int(0.9 * nb * 8))
+    g = FT(nb, seed=51)
+    o = oracle.Table(nb, 8, False, 51)
+    g.insert(f.keys, f.values)
+    o.insert(f.keys, f.values)
+    q = W.lookup_batch(51, 100003, f, 0.5)
+    ov, of = o.lookup(q.keys)
+    counts = {}
+    for variant in (K.LOOKUP_BLOOM, K.LOOKUP_OPTIMISTIC, K.LOOKUP_PESSIMISTIC):
+        v, fd = g.lookup_variant(q.keys, variant)
+        assert (fd.cpu().numpy() == of).all() and (v.cpu().numpy().view(np.uint64) == ov).all()
+        counts[variant] = g.probe_counts(q.keys, variant=variant).cpu().numpy()
+    n = q.keys.shape[0]
+    misses_in_primary = counts[K.LOOKUP_OPTIMISTIC][1]
+    assert counts[K.LOOKUP_PESSIMISTIC][1] == n
+    assert counts[K.LOOKUP_BLOOM][1] < misses_in_primary < n
+    sec_bloom, _ = o.probe_counts(q.keys)
+    assert counts[K.LOOKUP_BLOOM][1] == sec_bloom or abs(int(counts[K.LOOKUP_BLOOM][1]) - sec_bloom) < 0.01 * n
+    # every variant reads the same records for keys it finds; negatives add only tag false matches
+    assert counts[K.LOOKUP_PESSIMISTIC][2] >= counts[K.LOOKUP_BLOOM][2]
+
+
+def make_tables(n_tables, seed):
+    rng = np.random.default_rng(seed)
+    tables, fills = [], []
+    for i in range(n_tables):
+        nb = int(rng.choice([2, 3, 17, 256, 1000, 4099, 20000]))
+        timers = bool(rng.random() < 0.3)
+        m = int(0.85 * nb * 8)
+        f = W.fill(seed * 1000 + i, m)
+        t = FT(nb, timers=timers, seed=seed * 1000 + i)
+        st = t.insert(f.keys, f.values, 10, 900 if timers else 0).cpu().numpy()
+        assert (st == 1).all()
+        tables.append(t)
+        fills.append(f)
+    return tables, fills
+
+
+def plain_results(tables, qs):
+    out = []
+    for ti, keys in qs:
+        v, fd = tables[ti].lookup(keys, 20)
+        out.append((v.clone(), fd.to(torch.uint8).clone()))
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch_setup():
+    from paper_1712_09624_gb300.batched import BatchedLookup
+    tables, fills = make_tables(40, 52)
+    rng = np.random.default_rng(53)
+    qs = []
+    for ti in range(len(tables)):
+        n = int(rng.choice([0, 1, 31, 32, 33, 1000, 4097]))
+        q = W.lookup_batch(52 * 1000 + ti, n, fills[ti], 0.3, batch_id=1)
+        qs.append((ti, torch.from_numpy(q.keys).cuda()))
+    qs.append((7, torch.from_numpy(W.lookup_batch(9, 500, fills[7], 0.3).keys).cuda()))  # a second job on one table
+    return BatchedLookup(tables, max_jobs=64), tables, qs
+
+
+@pytest.mark.parametrize("tuning", [(1, 1, 4), (1, 2, 4), (1, 4, 2), (2, 1, 4), (4, 1, 4), (8, 1, 2), (1, 1, 1)])
+def test_batched_equals_plain_per_table(batch_setup, tuning):
+    batch, tables, qs = batch_setup
+    ref = plain_results(tables, qs)
+    outs = [(torch.full((k.shape[0],), -7, dtype=torch.int64, device="cuda"),
+             torch.full((k.shape[0],), 9, dtype=torch.uint8, device="cuda")) for _, k in qs]
+    batch.set_jobs([(ti, k, ov, of) for (ti, k), (ov, of) in zip(qs, outs)])
+    batch.launch(20, tuning)
+    torch.cuda.synchronize()
+    for (rv, rf), (ov, of) in zip(ref, outs):
+        assert torch.equal(rv, ov) and torch.equal(rf, of)
+
+
+def test_batched_skips_jobs_without_table_and_replays_graph(batch_setup):
+    batch, tables, qs = batch_setup
+    ref = plain_results(tables, qs)
+    outs = [(torch.full((k.shape[0],), -7, dtype=torch.int64, device="cuda"),
+             torch.full((k.shape[0],), 9, dtype=torch.uint8, device="cuda")) for _, k in qs]
+    jobs = [(ti, k, ov, of) for (ti, k), (ov, of) in zip(qs, outs)]
+    bad_keys = qs[5][1]
+    bad_out = (torch.full((bad_keys.shape[0],), -7, dtype=torch.int64, device="cuda"),
+               torch.full((bad_keys.shape[0],), 9, dtype=torch.uint8, device="cuda"))
+    batch.set_jobs(jobs[:10] + [(len(tables) + 3, bad_keys, *bad_out)])
+    batch.capture(20)
+    batch.replay()
+    torch.cuda.synchronize()
+    for (rv, rf), (ov, of) in zip(ref[:10], outs[:10]):
+        assert torch.equal(rv, ov) and torch.equal(rf, of)
+    assert bool((bad_out[0] == -7).all()) and bool((bad_out[1] == 9).all())
+    # rewrite the jobs, replay the same graph
+    outs2 = [(torch.zeros(k.shape[0], dtype=torch.int64, device="cuda"),
+              torch.zeros(k.shape[0], dtype=torch.uint8, device="cuda")) for _, k in qs]
+    batch.set_jobs([(ti, k, ov, of) for (ti, k), (ov, of) in zip(qs, outs2)])
+    batch.replay()
+    torch.cuda.synchronize()
+    for (rv, rf), (ov, of) in zip(ref, outs2):
+        assert torch.equal(rv, ov) and torch.equal(rf, of)
+
+
+def test_batched_matches_oracle_small():
+    """Batched results against the oracle on a few small tables."""
+    from paper_1712_09624_gb300.batched import BatchedLookup
+    tables, fills, ors = [], [], []
+    for i, nb in enumerate((5, 300, 2048)):
+        f = W.fill(60 + i, int(0.9 * nb * 8))
+        t = FT(nb, seed=60 + i)
+        t.insert(f.keys, f.values)
+        o = oracle.Table(nb, 8, False, 60 + i)
+        o.insert(f.keys, f.values)
+        tables.append(t), fills.append(f), ors.append(o)
+    b = BatchedLookup(tables)
+    qs = [W.lookup_batch(70 + i, 3000, fills[i], 0.3) for i in range(3)]
+    outs = [(torch.empty(3000, dtype=torch.int64, device="cuda"), torch.empty(3000, dtype=torch.uint8, device="cuda"))
+            for _ in range(3)]
+    b.set_jobs([(i, torch.from_numpy(qs[i].keys).cuda(), *outs[i]) for i in range(3)])
+    b.launch()
+    torch.cuda.synchronize()
+    for i in range(3):
+        ov, of = ors[i].lookup(qs[i].keys)
+        assert (outs[i][1].cpu().numpy() == of).all()
+        assert (outs[i][0].cpu().numpy().view(np.uint64) == ov).all()

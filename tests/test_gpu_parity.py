@@ -125,18 +125,25 @@ def run_stream(seed, nb, timers, n_batches, max_batch, pool_factor, max_lf=0.9):
     for step in range(n_batches):
         r = rng.random()
         n = int(rng.integers(1, max_batch + 1))
-        keys = pool[rng.integers(0, pool.shape[0], n)]
+        is_insert = (0.1 <= r < 0.5) if timers else (r < 0.5)
+        if is_insert:
+            # keep the load factor at or below max_lf, where both sides must place every key
+            n = min(n, int(max_lf * cap) - o.size())
+        keys = pool[rng.integers(0, pool.shape[0], max(n, 0))]
         if timers and r < 0.1:
             now += int(rng.integers(1, 400))
             cnt = g.expire(now).item()
             ocnt = o.expire(now)
             assert cnt >= 0 and ocnt >= 0
-        elif r < 0.5 and o.size() < max_lf * cap:
+        elif r < 0.5:
+            if n <= 0:
+                continue
             vals = rng.integers(0, 2**63, n, dtype=np.int64).astype(np.uint64)
             ttl = int(rng.integers(1, 1024)) if timers else 0
             gs = g.insert(keys, vals, now, ttl).cpu().numpy()
             os_ = o.insert(keys, vals, now, ttl)
-            assert (gs == os_).all(), f"step {step}: insert statuses differ"
+            bad = np.nonzero(gs != os_)[0]
+            assert bad.size == 0, f"step {step}: insert statuses differ at {bad[:8]}: gpu {gs[bad[:8]]} oracle {os_[bad[:8]]}"
         elif r < 0.8:
             refresh = int(rng.integers(0, 1024)) if (timers and rng.random() < 0.3) else 0
             gv, gf = g.lookup(keys, now, refresh)

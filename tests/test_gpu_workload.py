@@ -1,0 +1,28 @@
+"""The device-side traffic generator draws exactly what workload.py draws."""
+
+import numpy as np
+import pytest
+
+from paper_1712_09624_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed,first,n", [(1, 0, 1), (1, 0, 1001), (7, 3, 4097), (2**40 + 5, 12345, 777)])
+def test_fill_keys_match_host(seed, first, n):
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    k, v = WG.fill_keys(seed, first, n, "cuda")
+    ref = W.fill(seed, first + n)
+    assert (k.cpu().numpy() == ref.keys[first:]).all()
+    assert (v.cpu().numpy().view(np.uint64) == ref.values[first:]).all()
+
+
+@pytest.mark.parametrize("seed,n,m,neg,bid", [(1, 5000, 3000, 0.5, 0), (3, 4097, 100, 0.3, 7), (4, 999, 0, 0.2, 1),
+                                             (5, 2048, 70000, 0.0, 2), (6, 2048, 70000, 1.0, 3)])
+def test_lookup_batch_matches_host(seed, n, m, neg, bid):
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    k, f, v = WG.lookup_batch(seed, n, m, neg, bid, device="cuda")
+    ref = W.lookup_batch(seed, n, W.fill(seed, m), neg, batch_id=bid)
+    assert (k.cpu().numpy() == ref.keys).all()
+    assert (f.cpu().numpy() == ref.expect_found).all()
+    assert (v.cpu().numpy().view(np.uint64) == ref.expect_value).all()
