@@ -229,6 +229,30 @@ int ckpp_bulk_insert(ckpp_table* table, const ckpp_key* keys, const uint64_t* va
 int ckpp_bulk_delete(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32_t now, uint8_t* status,
                      void* workspace, size_t workspace_bytes, ckpp_stream_t stream);
 
+/* Largest batch ckpp_bulk_insert_noalloc accepts. */
+#define CKPP_NOALLOC_MAX_KEYS 65536
+
+/* Bulk insert for callers that cannot allocate device memory. No counterpart
+ * in the paper: it is ckpp_bulk_insert with the same semantics, arguments and
+ * status codes, minus the workspace. Its scratch is a fixed device array built
+ * into libckpp.so (about 2 MB, enough for CKPP_NOALLOC_MAX_KEYS keys), which
+ * every GPU that loads the library holds until the process exits. It suits
+ * callers that own no allocator when they insert: a data-plane thread that must
+ * never call cudaMalloc/cudaFree (cudaFree can stall the whole device), or a
+ * plugin whose host framework owns all device memory.
+ *  - n > CKPP_NOALLOC_MAX_KEYS returns CKPP_EINVAL (split the batch).
+ *  - The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ *    routine. It clears the parts of the array that must start at zero.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture. Call with the table's device current.
+ *  - All calls share the one array: calls whose work overlaps on the GPU
+ *    (different streams, or several tables at once) race and corrupt each
+ *    other's results. Order them on one stream or with events.
+ * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
+int ckpp_bulk_insert_noalloc(ckpp_table* table, const ckpp_key* keys, const uint64_t* vals, uint64_t n,
+                             uint32_t now, uint16_t ttl, uint8_t* status, ckpp_stream_t stream);
+
 /* Expiration scan (Sec. 4.2): delete every dead entry of every bucket, with
  * moved-counter upkeep, and record `now` as the last scan time. If
  * d_n_expired is not NULL, the number of deleted entries is ADDED to the

@@ -71,6 +71,7 @@ def _load():
         "ckpp_bulk_lookup": (C.c_int, [vp, vp, u64, vp, vp, u32, u16, vp]),
         "ckpp_bulk_insert": (C.c_int, [vp, vp, vp, u64, u32, u16, vp, vp, sz, vp]),
         "ckpp_bulk_delete": (C.c_int, [vp, vp, u64, u32, vp, vp, sz, vp]),
+        "ckpp_bulk_insert_noalloc": (C.c_int, [vp, vp, vp, u64, u32, u16, vp, vp]),
         "ckpp_expire": (C.c_int, [vp, u32, vp, vp]),
         "ckpp_stats_get": (C.c_int, [vp, u32, C.POINTER(ckpp_stats), vp]),
         "ckpp_lookup_probe_counts": (C.c_int, [vp, vp, u64, u32, C.c_int, vp, vp]),
@@ -96,8 +97,9 @@ _lib = _load()
 EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_destroy", "ckpp_bulk_lookup",
             "ckpp_bulk_insert", "ckpp_bulk_delete", "ckpp_expire", "ckpp_stats_get", "ckpp_lookup_probe_counts",
             "ckpp_sync_status", "ckpp_get_geometry", "ckpp_get_last_scan", "ckpp_error_string",
-            "ckpp_abi_version", "ckpp_bulk_lookup_variant", "ckpp_batch_bytes",
+            "ckpp_abi_version", "ckpp_bulk_insert_noalloc", "ckpp_bulk_lookup_variant", "ckpp_batch_bytes",
             "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup")
+NOALLOC_MAX_KEYS = 65536
 
 
 def library():
@@ -184,6 +186,19 @@ def ckpp_bulk_insert(handle: int, keys: torch.Tensor, vals: torch.Tensor, status
     _dev(workspace, "workspace", torch.uint8)
     _check(_lib.ckpp_bulk_insert(handle, _ptr(keys), _ptr(vals), n, now, ttl, _ptr(status), _ptr(workspace),
                                  workspace.numel(), _stream(stream)), "ckpp_bulk_insert")
+
+
+def ckpp_bulk_insert_noalloc(handle: int, keys: torch.Tensor, vals: torch.Tensor, status: torch.Tensor,
+                             now: int = 0, ttl: int = 0, stream=None):
+    """Insert without a workspace, for callers that cannot allocate device
+    memory: the library's built-in scratch array (at most NOALLOC_MAX_KEYS keys
+    per call; calls that overlap on the GPU must not share it)."""
+    n = keys.shape[0]
+    _dev(keys, "keys", torch.uint8)
+    _dev(vals, "vals", (torch.int64, torch.uint64))
+    _dev(status, "status", torch.uint8)
+    _check(_lib.ckpp_bulk_insert_noalloc(handle, _ptr(keys), _ptr(vals), n, now, ttl, _ptr(status),
+                                         _stream(stream)), "ckpp_bulk_insert_noalloc")
 
 
 def ckpp_bulk_delete(handle: int, keys: torch.Tensor, status: torch.Tensor, workspace: torch.Tensor,
