@@ -64,9 +64,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side", action="store_true", help="skip pos/neg/e2e/mutation side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle timing budget")
-    p.add_argument("--workload", default="scale", choices=["scale", "batched", "sweep"],
+    p.add_argument("--workload", default="scale", choices=["scale", "batched", "sweep", "random-read"],
                    help="scale: the headline at-scale lookup (default); batched: many tables in one launch vs "
-                        "one launch per table; sweep: load factor x negative rate x lookup strategy grid")
+                        "one launch per table; sweep: load factor x negative rate x lookup strategy grid; "
+                        "random-read: the GPU's random 32/64-byte read ceiling")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
     return p.parse_args()
 
@@ -83,17 +84,30 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel_src: str, summary: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source (sha256 match), else None."""
+LOOKUP_SOURCES = ("paper_1712_09624_gb300/csrc/lookup.cu", "paper_1712_09624_gb300/csrc/probe.cuh",
+                  "paper_1712_09624_gb300/csrc/ckpp_device.cuh")
+
+
+def sources_sha256(paths=LOOKUP_SOURCES) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(summary: str):
+    """Per-launch DRAM bytes of the lookup kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (sha256 over the
+    files the kernel is built from), else None."""
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
-        src = open(os.path.join(ROOT, kernel_src), "rb").read()
+        current = sources_sha256()
     except OSError:
         return None
-    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m = re.search(r"sources_sha256:\s*([0-9a-f]{64})", text)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != hashlib.sha256(src).hexdigest():
+    if not m or not t or m.group(1) != current:
         return None
     return float(t.group(1))
 
@@ -248,7 +262,7 @@ def run_ours(args, rank, world, local_rank):
 
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / per_launch / 1e9
-    traffic = profiled_traffic("paper_1712_09624_gb300/csrc/lookup.cu", "lookup_2e24_lf09.md")
+    traffic = profiled_traffic("lookup_kernel_2e24_lf09_traffic.md")
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 5), "higher_is_better": True,
@@ -349,11 +363,13 @@ def mutation_rates(table, dev, stream, ins_times, seed):
     # delete + reinsert of 1M resident keys
     fill_keys = W.make_keys(seed, W.STREAM_INSERT_KEYS, 1 << 20)
     k = torch.from_numpy(fill_keys).to(dev)
+    vals = torch.arange(k.shape[0], dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record(stream)
     st = table.delete(k, 0, stream)
     e[1].record(stream)
-    st2 = table.insert(k, torch.arange(k.shape[0], dtype=torch.int64, device=dev), 0, 0, stream)
+    st2 = table.insert(k, vals, 0, 0, stream)
     e[2].record(stream)
     e[2].synchronize()
     out["delete_Mops"] = round(k.shape[0] / (e[0].elapsed_time(e[1]) / 1e3) / 1e6, 1)
@@ -611,11 +627,45 @@ def run_sweep(args):
                        "n_buckets": nb, "batch": n}, "cells": cells}
 
 
+def run_random_read(args):
+    """Random-read ceiling of this GPU: 2^26 independent reads of 32 or 64
+    bytes at random aligned offsets of buffers from 64 MiB (L2-resident) to
+    8 GiB, timed with CUDA events."""
+    import torch
+
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    n = 1 << 26
+    buf = torch.ones(8 << 30, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    rows = []
+    for size in (64 << 20, 512 << 20, 1 << 30, 4 << 30, 8 << 30):
+        view = buf[:size]
+        for unit in (32, 64):
+            for w in range(3):
+                WG.random_read(view, unit, n, w + 1, sink, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for r in range(10):
+                WG.random_read(view, unit, n, 100 + r, sink, stream)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3 / 10
+            rows.append({"buffer_MiB": size >> 20, "unit_B": unit, "greads_per_s": round(n / sec / 1e9, 2),
+                         "useful_GBs": round(n * unit / sec / 1e9, 1)})
+    big = [r for r in rows if r["buffer_MiB"] == 8192 and r["unit_B"] == 32][0]
+    return {"metric": "random 32-byte reads per second (8 GiB buffer)", "value": big["greads_per_s"],
+            "unit": "Greads/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "random-read probe, 2^26 reads per launch"}, "rows": rows}
+
+
 def main():
     args = parse()
     if args.workload != "scale" and args.impl == "ours":
-        out = run_batched(args) if args.workload == "batched" else run_sweep(args)
-        print(json.dumps(out), flush=True)
+        run = {"batched": run_batched, "sweep": run_sweep, "random-read": run_random_read}[args.workload]
+        print(json.dumps(run(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

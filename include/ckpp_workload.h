@@ -36,6 +36,13 @@ int ckpp_wl_fill_keys(uint64_t seed, uint64_t first, uint64_t n, uint8_t* out_ke
 int ckpp_wl_lookup_batch(uint64_t seed, uint64_t batch_id, uint64_t n, uint64_t n_inserted, double neg_rate,
                          uint8_t* out_keys, uint8_t* expect_found, uint64_t* expect_value, ckpp_wl_stream_t stream);
 
+/* Random-read probe (measurement, not traffic): n independent reads of `unit`
+ * bytes (32 or 64) at scrambled unit-aligned offsets of buf (`bytes` a power
+ * of two, 64-byte aligned device memory). sink: device uint64 that the loads
+ * feed (left unchanged in practice). Time it with events on `stream`. */
+int ckpp_wl_random_read(const uint8_t* buf, uint64_t bytes, uint32_t unit, uint64_t n, uint64_t seed,
+                        uint64_t* sink, ckpp_wl_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,8 @@ def _load():
     L.ckpp_wl_fill_keys.argtypes = [u64, u64, u64, vp, vp, vp]
     L.ckpp_wl_lookup_batch.restype = C.c_int
     L.ckpp_wl_lookup_batch.argtypes = [u64, u64, u64, u64, C.c_double, vp, vp, vp, vp]
+    L.ckpp_wl_random_read.restype = C.c_int
+    L.ckpp_wl_random_read.argtypes = [vp, u64, C.c_uint32, u64, u64, vp, vp]
     return L
 
 
@@ -57,3 +59,10 @@ def lookup_batch(seed: int, n: int, n_inserted: int, neg_rate: float, batch_id: 
     if rc:
         raise RuntimeError(f"ckpp_wl_lookup_batch failed ({rc})")
     return keys, found, value
+
+
+def random_read(buf: torch.Tensor, unit: int, n: int, seed: int, sink: torch.Tensor, stream=None):
+    """Launch the random-read probe over the whole of buf (a power-of-two-sized uint8 CUDA tensor)."""
+    rc = _lib.ckpp_wl_random_read(buf.data_ptr(), buf.numel(), unit, n, seed, sink.data_ptr(), _stream(stream))
+    if rc:
+        raise RuntimeError(f"ckpp_wl_random_read failed ({rc})")
