@@ -64,10 +64,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side", action="store_true", help="skip pos/neg/e2e/mutation side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle timing budget")
-    p.add_argument("--workload", default="scale", choices=["scale", "batched", "sweep", "random-read"],
+    p.add_argument("--workload", default="scale", choices=["scale", "batched", "sweep", "random-read", "served"],
                    help="scale: the headline at-scale lookup (default); batched: many tables in one launch vs "
                         "one launch per table; sweep: load factor x negative rate x lookup strategy grid; "
-                        "random-read: the GPU's random 32/64-byte read ceiling")
+                        "random-read: the GPU's random 32/64-byte read ceiling; served: continuous-batching "
+                        "request loop vs one launch per burst")
+    p.add_argument("--serve-seconds", type=float, default=0.2, help="served: seconds of offered traffic")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
     return p.parse_args()
 
@@ -661,10 +663,38 @@ def run_random_read(args):
             "config": {"workload": "random-read probe, 2^26 reads per launch"}, "rows": rows}
 
 
+def run_served(args):
+    """Served form: 64 ports of Poisson packet bursts (32..4096 keys, 2 G
+    lookups/s offered, 10% inserts of new flows, 20% unknown flows) against
+    256 tables of 500M slots in total, served by the continuous-batching loop
+    and by one plain launch per burst; latency percentiles and throughput."""
+    import torch
+
+    from paper_1712_09624_gb300.serve import ServeConfig, Service
+    torch.cuda.set_device(0)
+    cfg = ServeConfig(duration_s=args.serve_seconds, seed=args.seed)
+    out = {}
+    for mode in ("batched", "plain"):
+        svc = Service(cfg)
+        r = svc.run(mode)
+        r.update(svc.check())
+        out[mode] = r
+        del svc
+        torch.cuda.empty_cache()
+    b = out["batched"]
+    return {"metric": "served Glookups/s and latency (continuous batching)", "value": b["achieved_glookups"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "served form: 64 ports, Poisson bursts of 32..4096 keys, 2 G lookups/s offered, "
+                                   "256 tables / 500M slots, 10% inserts", "duration_s": cfg.duration_s,
+                       "footprint_budget_bytes": cfg.footprint_bytes},
+            "batched": b, "plain_per_burst": out["plain"]}
+
+
 def main():
     args = parse()
     if args.workload != "scale" and args.impl == "ours":
-        run = {"batched": run_batched, "sweep": run_sweep, "random-read": run_random_read}[args.workload]
+        run = {"batched": run_batched, "sweep": run_sweep, "random-read": run_random_read,
+               "served": run_served}[args.workload]
         print(json.dumps(run(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

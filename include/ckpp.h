@@ -58,6 +58,7 @@ typedef struct CUstream_st* ckpp_stream_t;
 #define CKPP_ST_DELETED 4   /* the key had a live entry; it is gone                 */
 #define CKPP_ST_NOT_FOUND 5 /* the key had no live entry                            */
 #define CKPP_ST_BUSY 6      /* a bounded lock wait gave up; the key was not processed */
+#define CKPP_ST_NO_TABLE 7  /* batch calls: the key's table index names no table of the batch */
 
 /* geometry flags */
 #define CKPP_TIMERS 1u
@@ -191,6 +192,21 @@ int ckpp_batch_create(ckpp_batch** out, ckpp_table* const* tables, uint32_t n_ta
 
 /* Release the host handle (dev_buf stays the caller's). */
 int ckpp_batch_destroy(ckpp_batch* batch);
+
+/* Insert (as ckpp_bulk_insert) keys bound for many tables of a batch in one
+ * call: key i goes to the batch's table table_ids[i] (device uint32 [n]); the
+ * same key bound for two tables is two keys. Statuses as ckpp_bulk_insert, plus
+ * CKPP_ST_NO_TABLE for an index beyond the batch's tables. Workspace as for
+ * ckpp_bulk_insert (ckpp_workspace_bytes(n)). Errors: CKPP_EINVAL, CKPP_ESTALE
+ * (a timers table), CKPP_ECUDA. */
+int ckpp_batch_insert(ckpp_batch* batch, const ckpp_key* keys, const uint32_t* table_ids, const uint64_t* vals,
+                      uint64_t n, uint32_t now, uint16_t ttl, uint8_t* status, void* workspace,
+                      size_t workspace_bytes, ckpp_stream_t stream);
+
+/* Delete (as ckpp_bulk_delete) keys of many tables of a batch in one call;
+ * key i belongs to table table_ids[i]. Errors as ckpp_batch_insert. */
+int ckpp_batch_delete(ckpp_batch* batch, const ckpp_key* keys, const uint32_t* table_ids, uint64_t n, uint32_t now,
+                      uint8_t* status, void* workspace, size_t workspace_bytes, ckpp_stream_t stream);
 
 /* Look up every job's keys in its table (filter-pruned, as ckpp_bulk_lookup,
  * without refresh) in one launch. d_jobs: device array of at least max_jobs

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libckpp.so")
 
 CKPP_OK, CKPP_EINVAL, CKPP_ECUDA, CKPP_ESTALE, CKPP_EBUSY = 0, -1, -2, -3, -4
-ST_INSERTED, ST_UPDATED, ST_FULL, ST_DELETED, ST_NOT_FOUND, ST_BUSY = 1, 2, 3, 4, 5, 6
+ST_INSERTED, ST_UPDATED, ST_FULL, ST_DELETED, ST_NOT_FOUND, ST_BUSY, ST_NO_TABLE = 1, 2, 3, 4, 5, 6, 7
 CKPP_TIMERS = 1
 SLOTS = 8
 
@@ -80,6 +80,8 @@ def _load():
         "ckpp_batch_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), u32, vp, sz, vp]),
         "ckpp_batch_destroy": (C.c_int, [vp]),
         "ckpp_batch_lookup": (C.c_int, [vp, vp, u32, vp, u32, C.POINTER(ckpp_batch_tuning), vp]),
+        "ckpp_batch_insert": (C.c_int, [vp, vp, vp, vp, u64, u32, u16, vp, vp, sz, vp]),
+        "ckpp_batch_delete": (C.c_int, [vp, vp, vp, u64, u32, vp, vp, sz, vp]),
         "ckpp_sync_status": (C.c_int, [vp, vp]),
         "ckpp_get_geometry": (C.c_int, [vp, gp]),
         "ckpp_get_last_scan": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int)]),
@@ -98,7 +100,8 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_bulk_insert", "ckpp_bulk_delete", "ckpp_expire", "ckpp_stats_get", "ckpp_lookup_probe_counts",
             "ckpp_sync_status", "ckpp_get_geometry", "ckpp_get_last_scan", "ckpp_error_string",
             "ckpp_abi_version", "ckpp_bulk_insert_noalloc", "ckpp_bulk_lookup_variant", "ckpp_batch_bytes",
-            "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup")
+            "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup", "ckpp_batch_insert",
+            "ckpp_batch_delete")
 NOALLOC_MAX_KEYS = 65536
 
 
@@ -257,6 +260,29 @@ def ckpp_batch_create(handles, buf: torch.Tensor, stream=None) -> int:
 
 def ckpp_batch_destroy(handle: int):
     _check(_lib.ckpp_batch_destroy(handle), "ckpp_batch_destroy")
+
+
+def ckpp_batch_insert(handle: int, keys: torch.Tensor, table_ids: torch.Tensor, vals: torch.Tensor,
+                      status: torch.Tensor, workspace: torch.Tensor, now: int = 0, ttl: int = 0, stream=None):
+    n = keys.shape[0]
+    _dev(keys, "keys", torch.uint8)
+    _dev(table_ids, "table_ids", (torch.int32, torch.uint32))
+    _dev(vals, "vals", (torch.int64, torch.uint64))
+    _dev(status, "status", torch.uint8)
+    _dev(workspace, "workspace", torch.uint8)
+    _check(_lib.ckpp_batch_insert(handle, _ptr(keys), _ptr(table_ids), _ptr(vals), n, now, ttl, _ptr(status),
+                                  _ptr(workspace), workspace.numel(), _stream(stream)), "ckpp_batch_insert")
+
+
+def ckpp_batch_delete(handle: int, keys: torch.Tensor, table_ids: torch.Tensor, status: torch.Tensor,
+                      workspace: torch.Tensor, now: int = 0, stream=None):
+    n = keys.shape[0]
+    _dev(keys, "keys", torch.uint8)
+    _dev(table_ids, "table_ids", (torch.int32, torch.uint32))
+    _dev(status, "status", torch.uint8)
+    _dev(workspace, "workspace", torch.uint8)
+    _check(_lib.ckpp_batch_delete(handle, _ptr(keys), _ptr(table_ids), n, now, _ptr(status), _ptr(workspace),
+                                  workspace.numel(), _stream(stream)), "ckpp_batch_delete")
 
 
 def ckpp_batch_lookup(handle: int, d_jobs: torch.Tensor, max_jobs: int, d_n_jobs: torch.Tensor | None = None,

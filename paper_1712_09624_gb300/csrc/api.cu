@@ -87,7 +87,7 @@ int ckpp_bulk_insert(ckpp_table* t, const ckpp_key* keys, const uint64_t* vals, 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Workspace ws;
   if (int rc = prepare_workspace(n, workspace, workspace_bytes, s, ws)) return rc;
-  return cuda_rc(launch_insert(t->view, reinterpret_cast<const uint8_t*>(keys), vals, n, now,
+  return cuda_rc(launch_insert(one_table(t), reinterpret_cast<const uint8_t*>(keys), vals, n, now,
                                (now + ttl) & 0xFFFFu, status, ws, s));
 }
 
@@ -100,7 +100,7 @@ int ckpp_bulk_delete(ckpp_table* t, const ckpp_key* keys, uint64_t n, uint32_t n
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Workspace ws;
   if (int rc = prepare_workspace(n, workspace, workspace_bytes, s, ws)) return rc;
-  return cuda_rc(launch_delete(t->view, reinterpret_cast<const uint8_t*>(keys), n, now, status, ws, s));
+  return cuda_rc(launch_delete(one_table(t), reinterpret_cast<const uint8_t*>(keys), n, now, status, ws, s));
 }
 
 int ckpp_expire(ckpp_table* t, uint32_t now, uint64_t* d_n_expired, ckpp_stream_t stream) {
@@ -190,6 +190,36 @@ int ckpp_batch_destroy(ckpp_batch* b) {
   if (!b) return CKPP_EINVAL;
   delete b;
   return CKPP_OK;
+}
+
+int ckpp_batch_insert(ckpp_batch* b, const ckpp_key* keys, const uint32_t* table_ids, const uint64_t* vals, uint64_t n,
+                      uint32_t now, uint16_t ttl, uint8_t* status, void* workspace, size_t workspace_bytes,
+                      ckpp_stream_t stream) {
+  if (!b || check_keys(keys, n) || ttl >= kAliveWindow) return CKPP_EINVAL;
+  if (n && (!table_ids || !vals || !status || !aligned(vals, 8) || !aligned(table_ids, 4))) return CKPP_EINVAL;
+  for (ckpp_table* t : b->tables)
+    if (int rc = time_check(t, now)) return rc;
+  if (!n) return CKPP_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Workspace ws;
+  if (int rc = prepare_workspace(n, workspace, workspace_bytes, s, ws)) return rc;
+  const TableSet ts{b->host_views[0], b->dev_views, table_ids, (uint32_t)b->tables.size()};
+  return cuda_rc(launch_insert(ts, reinterpret_cast<const uint8_t*>(keys), vals, n, now, (now + ttl) & 0xFFFFu, status,
+                               ws, s));
+}
+
+int ckpp_batch_delete(ckpp_batch* b, const ckpp_key* keys, const uint32_t* table_ids, uint64_t n, uint32_t now,
+                      uint8_t* status, void* workspace, size_t workspace_bytes, ckpp_stream_t stream) {
+  if (!b || check_keys(keys, n)) return CKPP_EINVAL;
+  if (n && (!table_ids || !status || !aligned(table_ids, 4))) return CKPP_EINVAL;
+  for (ckpp_table* t : b->tables)
+    if (int rc = time_check(t, now)) return rc;
+  if (!n) return CKPP_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Workspace ws;
+  if (int rc = prepare_workspace(n, workspace, workspace_bytes, s, ws)) return rc;
+  const TableSet ts{b->host_views[0], b->dev_views, table_ids, (uint32_t)b->tables.size()};
+  return cuda_rc(launch_delete(ts, reinterpret_cast<const uint8_t*>(keys), n, now, status, ws, s));
 }
 
 int ckpp_batch_lookup(ckpp_batch* b, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,

@@ -39,8 +39,8 @@ inline size_t table_bytes(const ckpp_geometry* g) {
 }
 
 // Workspace of an n-key batch: counters | set_first[m] | set_last[m] |
-// slot_of[n] | pending[n] | retry[n] | fixup[fix_cap], each part 256-byte
-// aligned.
+// slot_of[n] | pending[n] | retry[n] | fixup[fix_cap] (8 bytes each), each
+// part 256-byte aligned.
 struct WsLayout {
   uint64_t m = 0;
   uint32_t fix_cap = 0;
@@ -65,7 +65,7 @@ constexpr WsLayout ws_layout(uint64_t n) {
   L.off_retry = off;
   off = align_up(off + 4 * n, kAlign);
   L.off_fixup = off;
-  off = align_up(off + 4 * (size_t)L.fix_cap, kAlign);
+  off = align_up(off + 8 * (size_t)L.fix_cap, kAlign);
   L.total = off;
   return L;
 }
@@ -80,7 +80,7 @@ inline int prepare_workspace(uint64_t n, void* workspace, size_t bytes, cudaStre
   ws.slot_of = reinterpret_cast<uint32_t*>(w + L.off_slot);
   ws.pending = reinterpret_cast<uint32_t*>(w + L.off_pending);
   ws.retry = reinterpret_cast<uint32_t*>(w + L.off_retry);
-  ws.fixup = reinterpret_cast<uint32_t*>(w + L.off_fixup);
+  ws.fixup = reinterpret_cast<unsigned long long*>(w + L.off_fixup);
   ws.m_mask = (uint32_t)(L.m - 1);
   ws.fix_cap = L.fix_cap;
   if (cudaMemsetAsync(w, 0, kAlign, s) != cudaSuccess) return CKPP_ECUDA;
@@ -114,6 +114,9 @@ inline int residency(const void* p) {
   if (a.type == cudaMemoryTypeHost && a.devicePointer == p) return 1;
   return -1;
 }
+
+// One table as a TableSet.
+inline TableSet one_table(const ckpp_table* t) { return TableSet{t->view, nullptr, nullptr, 1u}; }
 
 inline int check_keys(const ckpp_key* keys, uint64_t n) {
   if (n > kMaxBatch) return CKPP_EINVAL;

@@ -45,7 +45,8 @@ constexpr uint32_t kHdrMagic = 0, kHdrAbi = 4, kHdrBuckets = 8, kHdrSlots = 16, 
 constexpr uint32_t kErrLockTimeout = 1u;
 
 // per-key status codes (the public contract's values)
-constexpr uint8_t kStInserted = 1, kStUpdated = 2, kStFull = 3, kStDeleted = 4, kStNotFound = 5, kStBusy = 6;
+constexpr uint8_t kStInserted = 1, kStUpdated = 2, kStFull = 3, kStDeleted = 4, kStNotFound = 5, kStBusy = 6,
+                  kStNoTable = 7;
 
 // bounded waits
 constexpr int kLockSpins = 1 << 20;

@@ -18,9 +18,23 @@ struct Workspace {
   uint32_t* slot_of;    // [n] set position of each batch key
   uint32_t* pending;    // [n] leaders left for the displacement pass
   uint32_t* retry;      // [n] leaders the first displacement pass could not place
-  uint32_t* fixup;      // [fix_cap] buckets whose moved counter fell to 0 off-lock
+  unsigned long long* fixup;  // [fix_cap] (table << 32 | bucket) whose moved counter fell to 0 off-lock
   uint32_t m_mask;      // m - 1 (m a power of two >= 2n)
   uint32_t fix_cap;
+};
+
+// The table(s) a mutation batch works on: one table, or many (key i goes to
+// views[tab[i]]; keys naming no table are reported CKPP_ST_NO_TABLE).
+struct TableSet {
+  TableView single;
+  const TableView* views;  // nullptr: every key goes to `single`
+  const uint32_t* tab;     // per-key table index when views != nullptr
+  uint32_t n_tables;
+
+  __device__ __forceinline__ bool valid(uint64_t i) const { return !views || tab[i] < n_tables; }
+  __device__ __forceinline__ uint32_t id(uint64_t i) const { return views ? tab[i] : 0u; }
+  __device__ __forceinline__ TableView of(uint64_t i) const { return views ? views[tab[i]] : single; }
+  __device__ __forceinline__ TableView table(uint32_t id) const { return views ? views[id] : single; }
 };
 
 cudaError_t launch_init_header(uint8_t* base, uint64_t nb, uint32_t slots, uint32_t flags, uint64_t seed,
@@ -43,13 +57,13 @@ cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, co
                                   uint32_t max_jobs, uint32_t now, int threads_per_key, int group_depth,
                                   uint32_t blocks, cudaStream_t s);
 
-cudaError_t launch_dedup(const TableView& t, const uint8_t* keys, uint64_t n, const Workspace& ws,
+cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws,
                          cudaStream_t s);
 
-cudaError_t launch_insert(const TableView& t, const uint8_t* keys, const uint64_t* vals, uint64_t n,
+cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_t* vals, uint64_t n,
                           uint32_t now, uint32_t expiry, uint8_t* status, const Workspace& ws, cudaStream_t s);
 
-cudaError_t launch_delete(const TableView& t, const uint8_t* keys, uint64_t n, uint32_t now, uint8_t* status,
+cudaError_t launch_delete(const TableSet& ts, const uint8_t* keys, uint64_t n, uint32_t now, uint8_t* status,
                           const Workspace& ws, cudaStream_t s);
 
 cudaError_t launch_expire(const TableView& t, uint32_t now, unsigned long long* n_expired, cudaStream_t s);

@@ -38,12 +38,14 @@ __device__ __forceinline__ Key load_key(const uint8_t* keys, uint64_t i) {
 }
 
 // ---------------------------------------------------------------- dedup
-__global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restrict__ keys, uint64_t n, uint64_t seed,
+// Equal keys bound for different tables are different keys.
+__global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restrict__ keys, uint64_t n, TableSet ts,
                                                          Workspace ws) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Key k = load_key(keys, i);
-  uint32_t pos = (uint32_t)(hash_key(k, seed) >> 16) & ws.m_mask;
+  const uint32_t tid = ts.id(i);
+  uint32_t pos = (uint32_t)(hash_key(k, 0x51ED270B27A2B5E3ull ^ tid) >> 16) & ws.m_mask;
   for (uint32_t probe = 0; probe <= ws.m_mask; ++probe) {
     uint32_t cur = ld32_cg(ws.set_first + pos);
     if (cur == kEmpty) {
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restri
     // set_first only ever holds batch indices of one key group, so the key at
     // index cur is that group's key even while atomicMin lowers cur.
     const Key o = load_key(keys, cur);
-    if (o.k0 == k.k0 && o.k1 == k.k1) {
+    if (o.k0 == k.k0 && o.k1 == k.k1 && ts.id(cur) == tid) {
       atomicMin(ws.set_first + pos, (uint32_t)i);
       atomicMax(ws.set_last + pos, (uint32_t)i);
       ws.slot_of[i] = pos;
@@ -75,7 +77,7 @@ __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint3
 }
 
 // --------------------------------------------------------------- phase 1
-__global__ void __launch_bounds__(kThreads) insert_phase1(TableView t, const uint8_t* __restrict__ keys,
+__global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
                                                           const uint64_t* __restrict__ vals, uint64_t n,
                                                           uint32_t now, uint32_t expiry, uint8_t* __restrict__ status,
                                                           Workspace ws) {
@@ -83,6 +85,12 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableView t, const uin
   if (i >= n) return;
   uint32_t last;
   if (!is_leader(ws, i, last)) return;
+  if (!ts.valid(i)) {
+    status[i] = kStNoTable;
+    return;
+  }
+  const TableView t = ts.of(i);
+  const uint32_t tid = ts.id(i);
   const uint64_t v = vals[last];
   const Key k = load_key(keys, i);
   const Addr a = address_of(k, t.nb, t.seed);
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableView t, const uin
       b = f1 ? a.b1 : a.b2;
       uint32_t& cb = f1 ? c1 : c2;
       slot = __ffs(f1 ? f1 : f2) - 1;
-      if ((cb >> slot) & 1u) evict_entry(t, b, slot, cb, ws);
+      if ((cb >> slot) & 1u) evict_entry(t, tid, b, slot, cb, ws);
       place_entry(t, b, slot, k, v, a, expiry, cb);
       st = kStInserted;
     } else {
@@ -133,8 +141,12 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableView t, const uin
 // at most 48 KB per block): the contended first pass searches 96 buckets up
 // to 4 moves deep per thread; the single-block second pass 192 buckets, 5
 // moves; the single-thread last pass 2048 buckets, 6 moves (the sequential
-// CPU reference searches 1024 buckets, 5 moves).
+// CPU reference searches 1024 buckets, 5 moves). The later passes take on at
+// most kSecondPassKeys / kLastPassKeys keys: more failures than that mean the
+// table is full, not contended, and the rest are FULL without a search.
 constexpr int kP2Threads = 64;
+constexpr uint32_t kSecondPassKeys = 4096;  // keys the single-block pass takes on
+constexpr uint32_t kLastPassKeys = 128;     // keys the single-thread pass takes on
 constexpr int kMaxDepth = 6;
 constexpr int kPathBuckets = kMaxDepth + 1;
 constexpr int kMaxLocks = kPathBuckets + 1;   // the path plus the key's primary
@@ -148,8 +160,8 @@ struct Node {
 
 // Place k into the lowest free or dead slot of its primary, else secondary.
 // 1 placed, 0 no room, -1 lock timeout.
-__device__ int try_place(const TableView& t, const Key& k, uint64_t v, const Addr& a, uint32_t now, uint32_t expiry,
-                         const Workspace& ws) {
+__device__ int try_place(const TableView& t, uint32_t tid, const Key& k, uint64_t v, const Addr& a, uint32_t now,
+                         uint32_t expiry, const Workspace& ws) {
   uint32_t c1, c2;
   if (!lock_pair(t, a.b1, a.b2, c1, c2)) return -1;
   Snap s1, s2;
@@ -162,7 +174,7 @@ __device__ int try_place(const TableView& t, const Key& k, uint64_t v, const Add
     const uint32_t b = f1 ? a.b1 : a.b2;
     uint32_t& cb = f1 ? c1 : c2;
     const uint32_t slot = __ffs(f1 ? f1 : f2) - 1;
-    if ((cb >> slot) & 1u) evict_entry(t, b, slot, cb, ws);
+    if ((cb >> slot) & 1u) evict_entry(t, tid, b, slot, cb, ws);
     place_entry(t, b, slot, k, v, a, expiry, cb);
     placed = 1;
   }
@@ -234,7 +246,7 @@ __device__ void move_locked(const TableView& t, uint32_t x, uint32_t sx, uint32_
 // path[0] is the root (b1 or b2), path[len] the bucket with the hole; slot[j]
 // is the slot of path[j] whose entry moves to path[j + 1].
 // 1 placed, 0 stale path, -1 lock timeout.
-__device__ int execute_path(const TableView& t, const uint32_t (&path)[kPathBuckets],
+__device__ int execute_path(const TableView& t, uint32_t tid, const uint32_t (&path)[kPathBuckets],
                             const uint32_t (&slot)[kPathBuckets], int len, uint32_t hole, const Key& k, uint64_t v,
                             const Addr& a, uint32_t now, uint32_t expiry, const Workspace& ws) {
   uint32_t lk[kMaxLocks], cw[kMaxLocks];
@@ -279,7 +291,7 @@ __device__ int execute_path(const TableView& t, const uint32_t (&path)[kPathBuck
   if (ok && end_busy) ok = t.timers && !alive16(ld16_cg(expiry_ptr(t, path[len], hole)), now);
   int rc = 0;
   if (ok) {
-    if (end_busy) evict_entry(t, path[len], hole, cw[ie], ws);
+    if (end_busy) evict_entry(t, tid, path[len], hole, cw[ie], ws);
     uint32_t dst_s = hole;
     for (int j = len - 1; j >= 0; --j) {
       move_locked(t, path[j], slot[j], cw[idx(path[j])], path[j + 1], dst_s, cw[idx(path[j + 1])]);
@@ -296,25 +308,32 @@ __device__ int execute_path(const TableView& t, const uint32_t (&path)[kPathBuck
 // are appended to `retry` (when given) for a second, low-contention pass;
 // otherwise they are FULL.
 template <int kThreadsPerBlock, int kBfsNodes, int kBfsDepth>
-__global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableView t, const uint8_t* __restrict__ keys,
+__global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, const uint8_t* __restrict__ keys,
                                                                   const uint64_t* __restrict__ vals, uint32_t now,
                                                                   uint32_t expiry, uint8_t* __restrict__ status,
                                                                   Workspace ws, const uint32_t* list,
                                                                   const uint32_t* count_ptr, uint32_t* retry,
-                                                                  uint32_t* retry_count) {
+                                                                  uint32_t* retry_count, uint32_t max_keys) {
   static_assert(kThreadsPerBlock * kBfsNodes * sizeof(Node) <= 48 * 1024, "BFS queues exceed 48 KB");
   static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
   __shared__ Node queues[kThreadsPerBlock][kBfsNodes];
   Node* q = queues[threadIdx.x];
-  const uint32_t count = ld32_cg(count_ptr);
+  const uint32_t listed = ld32_cg(count_ptr);
+  const uint32_t count = min(listed, max_keys);
+  // A later pass searches wider but alone; when many keys reach it the table
+  // is full rather than contended, and those beyond max_keys are FULL at once.
+  for (uint32_t j = count + blockIdx.x * blockDim.x + threadIdx.x; j < listed; j += gridDim.x * blockDim.x)
+    status[list[j]] = kStFull;
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
     const uint32_t i = list[j];
+    const TableView t = ts.of(i);
+    const uint32_t tid = ts.id(i);
     const uint64_t v = vals[ws.set_last[ws.slot_of[i]]];
     const Key k = load_key(keys, i);
     const Addr a = address_of(k, t.nb, t.seed);
     uint8_t st = kStFull;
     for (int attempt = 0; attempt < kPathAttempts; ++attempt) {
-      const int placed = try_place(t, k, v, a, now, expiry, ws);
+      const int placed = try_place(t, tid, k, v, a, now, expiry, ws);
       if (placed != 0) {
         st = placed > 0 ? kStInserted : kStBusy;
         break;
@@ -328,7 +347,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableView t, c
         path[q[node].depth] = q[node].bucket;
         if (q[node].depth > 0) slot[q[node].depth - 1] = q[node].slot;
       }
-      const int r = execute_path(t, path, slot, len, hole, k, v, a, now, expiry, ws);
+      const int r = execute_path(t, tid, path, slot, len, hole, k, v, a, now, expiry, ws);
       if (r != 0) {
         st = r > 0 ? kStInserted : kStBusy;
         break;
@@ -344,16 +363,21 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableView t, c
 }
 
 // ----------------------------------------------------- fixup and finish
-__global__ void bloom_fixup(TableView t, Workspace ws) {
+__global__ void bloom_fixup(TableSet ts, Workspace ws) {
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ld32_cg(ws.counters + 2)) {
-    for (uint64_t b = tid; b < t.nb; b += stride)
-      if (ld32_cg(moved_ptr(t, (uint32_t)b)) == 0u) st64_cg(bloom_ptr(t, (uint32_t)b), 0ull);
+  if (ld32_cg(ws.counters + 2)) {  // the list overflowed: scan every bucket of every table
+    for (uint32_t tb = 0; tb < ts.n_tables; ++tb) {
+      const TableView t = ts.table(tb);
+      for (uint64_t b = tid; b < t.nb; b += stride)
+        if (ld32_cg(moved_ptr(t, (uint32_t)b)) == 0u) st64_cg(bloom_ptr(t, (uint32_t)b), 0ull);
+    }
   } else {
     const uint32_t count = min(ld32_cg(ws.counters + 1), ws.fix_cap);
     for (uint32_t j = tid; j < count; j += stride) {
-      const uint32_t b = ws.fixup[j];
+      const unsigned long long e = ws.fixup[j];
+      const TableView t = ts.table((uint32_t)(e >> 32));
+      const uint32_t b = (uint32_t)e;
       if (ld32_cg(moved_ptr(t, b)) == 0u) st64_cg(bloom_ptr(t, b), 0ull);
     }
   }
@@ -365,18 +389,23 @@ __global__ void __launch_bounds__(kThreads) insert_finish(uint64_t n, uint8_t* _
   const uint32_t leader = ws.set_first[ws.slot_of[i]];
   if (leader == (uint32_t)i) return;
   const uint8_t st = status[leader];
-  status[i] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;
+  status[i] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;  // FULL, BUSY, NO_TABLE copy through
 }
 
-__global__ void __launch_bounds__(kThreads) delete_kernel(TableView t, const uint8_t* __restrict__ keys, uint64_t n,
+__global__ void __launch_bounds__(kThreads) delete_kernel(TableSet ts, const uint8_t* __restrict__ keys, uint64_t n,
                                                           uint32_t now, uint8_t* __restrict__ status, Workspace ws) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (!ts.valid(i)) {
+    status[i] = kStNoTable;
+    return;
+  }
   uint32_t last;
   if (!is_leader(ws, i, last)) {
     status[i] = kStNotFound;
     return;
   }
+  const TableView t = ts.of(i);
   const Key k = load_key(keys, i);
   const Addr a = address_of(k, t.nb, t.seed);
   uint64_t h[4];
@@ -410,42 +439,42 @@ unsigned grid_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1)
 
 }  // namespace
 
-cudaError_t launch_dedup(const TableView& t, const uint8_t* keys, uint64_t n, const Workspace& ws, cudaStream_t s) {
-  dedup_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(keys, n, t.seed, ws);
+cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws, cudaStream_t s) {
+  dedup_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(keys, n, ts, ws);
   return cudaGetLastError();
 }
 
-cudaError_t launch_insert(const TableView& t, const uint8_t* keys, const uint64_t* vals, uint64_t n, uint32_t now,
+cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_t* vals, uint64_t n, uint32_t now,
                           uint32_t expiry, uint8_t* status, const Workspace& ws, cudaStream_t s) {
-  cudaError_t e = launch_dedup(t, keys, n, ws, s);
+  cudaError_t e = launch_dedup(ts, keys, n, ws, s);
   if (e != cudaSuccess) return e;
-  insert_phase1<<<grid_for(n, kThreads), kThreads, 0, s>>>(t, keys, vals, n, now, expiry, status, ws);
+  insert_phase1<<<grid_for(n, kThreads), kThreads, 0, s>>>(ts, keys, vals, n, now, expiry, status, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const unsigned p2_blocks = (unsigned)std::min<uint64_t>(grid_for(n, kP2Threads), 152 * 4);
-  insert_phase2<kP2Threads, 96, 4><<<p2_blocks, kP2Threads, 0, s>>>(t, keys, vals, now, expiry, status, ws,
+  insert_phase2<kP2Threads, 96, 4><<<p2_blocks, kP2Threads, 0, s>>>(ts, keys, vals, now, expiry, status, ws,
                                                                     ws.pending, ws.counters + 0, ws.retry,
-                                                                    ws.counters + 3);
+                                                                    ws.counters + 3, 0xFFFFFFFFu);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // second pass, one block: the keys the contended pass could not place
-  insert_phase2<32, 192, 5><<<1, 32, 0, s>>>(t, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 3,
-                                             ws.pending, ws.counters + 4);
+  insert_phase2<32, 192, 5><<<1, 32, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 3,
+                                             ws.pending, ws.counters + 4, kSecondPassKeys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // last pass, one thread: no contention left and the widest search; a key
   // is FULL only if it finds no path
-  insert_phase2<1, 2048, 6><<<1, 1, 0, s>>>(t, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 4,
-                                            nullptr, nullptr);
+  insert_phase2<1, 2048, 6><<<1, 1, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 4,
+                                            nullptr, nullptr, kLastPassKeys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bloom_fixup<<<152 * 2, 256, 0, s>>>(t, ws);
+  bloom_fixup<<<152 * 2, 256, 0, s>>>(ts, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   insert_finish<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, status, ws);
   return cudaGetLastError();
 }
 
-cudaError_t launch_delete(const TableView& t, const uint8_t* keys, uint64_t n, uint32_t now, uint8_t* status,
+cudaError_t launch_delete(const TableSet& ts, const uint8_t* keys, uint64_t n, uint32_t now, uint8_t* status,
                           const Workspace& ws, cudaStream_t s) {
-  cudaError_t e = launch_dedup(t, keys, n, ws, s);
+  cudaError_t e = launch_dedup(ts, keys, n, ws, s);
   if (e != cudaSuccess) return e;
-  delete_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(t, keys, n, now, status, ws);
+  delete_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(ts, keys, n, now, status, ws);
   return cudaGetLastError();
 }
 

@@ -105,18 +105,18 @@ __device__ __forceinline__ int find_key(const TableView& t, uint32_t b, uint32_t
   return -1;
 }
 
-__device__ __forceinline__ void push_fixup(const Workspace& ws, uint32_t b) {
+__device__ __forceinline__ void push_fixup(const Workspace& ws, uint32_t table, uint32_t b) {
   const uint32_t idx = atomicAdd(ws.counters + 1, 1u);
   if (idx < ws.fix_cap) {
-    ws.fixup[idx] = b;
+    ws.fixup[idx] = ((unsigned long long)table << 32) | b;
   } else {
     atomicExch(ws.counters + 2, 1u);
   }
 }
 
-// Remove the (dead) entry in slot s of locked bucket b: if it sits in its
+// Remove the (dead) entry in slot s of locked bucket b of table tid: if it sits in its
 // secondary bucket its primary's moved counter is decremented (Sec. 4.1).
-__device__ __forceinline__ void evict_entry(const TableView& t, uint32_t b, uint32_t s, uint32_t& ctrl,
+__device__ __forceinline__ void evict_entry(const TableView& t, uint32_t tid, uint32_t b, uint32_t s, uint32_t& ctrl,
                                             const Workspace& ws) {
   if ((ctrl >> (kInsecShift + s)) & 1u) {
     uint64_t r[4];
@@ -124,7 +124,7 @@ __device__ __forceinline__ void evict_entry(const TableView& t, uint32_t b, uint
     const Key k{r[0], r[1]};
     const Addr a = address_of(k, t.nb, t.seed);
     const uint32_t old = atomicSub(moved_ptr(t, a.b1), 1u);
-    if (old == 1u) push_fixup(ws, a.b1);
+    if (old == 1u) push_fixup(ws, tid, a.b1);
   }
   ctrl &= ~((1u << s) | (1u << (kInsecShift + s)));
 }

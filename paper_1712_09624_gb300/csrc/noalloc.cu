@@ -62,6 +62,6 @@ extern "C" int ckpp_bulk_insert_noalloc(ckpp_table* t, const ckpp_key* keys, con
   // prepare_workspace clears the counters and the duplicate-key set, the parts
   // that must start at zero (the array keeps the previous call's contents).
   if (int rc = prepare_workspace(n, scratch, kNoallocBytes, s, ws)) return rc;
-  return cuda_rc(launch_insert(t->view, reinterpret_cast<const uint8_t*>(keys), vals, n, now, (now + ttl) & 0xFFFFu,
-                               status, ws, s));
+  return cuda_rc(launch_insert(one_table(t), reinterpret_cast<const uint8_t*>(keys), vals, n, now,
+                               (now + ttl) & 0xFFFFu, status, ws, s));
 }

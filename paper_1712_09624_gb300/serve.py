@@ -1,0 +1,293 @@
+"""Served form: a continuous-batching request loop over device-resident tables.
+
+Packet bursts arrive from many ports (Poisson arrivals, uniform burst sizes);
+each burst targets one table and is either a lookup of flows or an insert of
+new flows. The loop runs in real time on the host:
+
+* it retires finished launches (CUDA event queries) and frees their staging
+  footprint;
+* it admits every burst that has arrived, in arrival order, while the
+  staging footprint (keys in, results out) of work in flight stays within an
+  HBM budget; a burst that does not fit waits for the next turn;
+* it launches the admitted work without waiting for the previous launch: the
+  admitted inserts as one multi-table ``ckpp_batch_insert`` and the admitted
+  lookups as one persistent ``ckpp_batch_lookup`` (one job per burst), both
+  on one stream, so the next launch is queued while the current one runs.
+
+Lookups read flows of the warm fill (and unknown flows); inserts add new
+flows. Lookup results therefore do not depend on how bursts are grouped, and
+every burst's result equals what it gets when run alone; the tests check
+this. Per-burst latency is completion time (the launch's CUDA event, mapped
+to host time) minus arrival time.
+
+The comparison arm serves the same arrival stream with one plain launch per
+burst (``ckpp_bulk_lookup`` / ``ckpp_bulk_insert``) as bursts arrive.
+"""
+
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _ckpp as K
+from . import workload_gpu as WG
+from .batched import BatchedLookup
+from .table import FlowTable
+
+KEY_BYTES_IO = 16 + 8 + 1  # key in, value and flag out
+
+
+@dataclass
+class ServeConfig:
+    n_tables: int = 256
+    total_slots: int = 500_000_000
+    warm_lf: float = 0.8
+    ports: int = 64
+    min_burst: int = 32
+    max_burst: int = 4096
+    offered_lookups_per_s: float = 2e9
+    insert_fraction: float = 0.10
+    neg_rate: float = 0.2
+    duration_s: float = 0.2
+    footprint_bytes: int = 256 << 20
+    seed: int = 7
+
+
+@dataclass
+class Stream:
+    """Pre-drawn request stream (arrival order)."""
+    arrival: np.ndarray    # seconds since start
+    table: np.ndarray      # target table
+    size: np.ndarray       # keys in the burst
+    insert: np.ndarray     # True: insert of new flows
+    offset: np.ndarray     # lookups: offset in the table's lookup pool; inserts: offset in the insert pool
+
+
+def draw_stream(cfg: ServeConfig) -> Stream:
+    rng = np.random.default_rng(cfg.seed)
+    mean_burst = (cfg.min_burst + cfg.max_burst) / 2
+    rate_per_port = cfg.offered_lookups_per_s / (cfg.ports * mean_burst)
+    per_port = []
+    for _ in range(cfg.ports):
+        n = int(rate_per_port * cfg.duration_s * 1.2) + 16
+        t = np.cumsum(rng.exponential(1.0 / rate_per_port, n))
+        per_port.append(t[t < cfg.duration_s])
+    arrival = np.sort(np.concatenate(per_port))
+    nb = arrival.shape[0]
+    table = rng.integers(0, cfg.n_tables, nb)
+    size = rng.integers(cfg.min_burst, cfg.max_burst + 1, nb)
+    insert = rng.random(nb) < cfg.insert_fraction
+    offset = np.zeros(nb, np.int64)
+    ins_sizes = np.where(insert, size, 0)
+    offset[insert] = (np.cumsum(ins_sizes) - ins_sizes)[insert]
+    look = ~insert
+    for t in range(cfg.n_tables):
+        sel = look & (table == t)
+        s = size[sel]
+        offset[sel] = np.cumsum(s) - s
+    return Stream(arrival, table, size, insert, offset)
+
+
+class Service:
+    """Tables, request pools and output buffers of one served run."""
+
+    def __init__(self, cfg: ServeConfig, device=None):
+        self.cfg = cfg
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        dev = self.device
+        self.stream = draw_stream(cfg)
+        st = self.stream
+        nb_table = max(2, cfg.total_slots // (8 * cfg.n_tables))
+        self.warm = int(cfg.warm_lf * nb_table * 8)
+        ws = torch.empty(K.ckpp_workspace_bytes(self.warm), dtype=torch.uint8, device=dev)
+        cuda = torch.cuda.current_stream(dev)
+        self.tables = []
+        for t in range(cfg.n_tables):
+            tb = FlowTable(nb_table, seed=cfg.seed * 1000 + t, device=dev)
+            k, v = WG.fill_keys(cfg.seed * 1000 + t, 0, self.warm, dev)
+            s = torch.empty(self.warm, dtype=torch.uint8, device=dev)
+            K.ckpp_bulk_insert(tb.handle, k, v, s, ws, 0, 0, cuda)
+            self.tables.append(tb)
+        del ws
+        # per-table lookup pools (keys, expected answers, outputs), arrival order
+        look = ~st.insert
+        self.pools = []
+        for t in range(cfg.n_tables):
+            n = int(st.size[look & (st.table == t)].sum())
+            keys, ef, ev = WG.lookup_batch(cfg.seed * 1000 + t, n, self.warm, cfg.neg_rate, 1, device=dev)
+            self.pools.append(dict(keys=keys, expect_found=ef, expect_value=ev,
+                                   vals=torch.zeros(n, dtype=torch.int64, device=dev),
+                                   found=torch.zeros(n, dtype=torch.uint8, device=dev)))
+        # one insert pool for all tables, arrival order: new flows never in any table
+        n_ins = int(st.size[st.insert].sum())
+        self.ins_keys, self.ins_vals = WG.fill_keys(cfg.seed * 1000 + 999_999, 0, n_ins, dev)
+        tids = np.repeat(st.table[st.insert], st.size[st.insert]).astype(np.int32)
+        self.ins_tables = torch.from_numpy(tids).to(dev)
+        self.ins_status = torch.zeros(n_ins, dtype=torch.uint8, device=dev)
+        self.ins_ws = torch.empty(K.ckpp_workspace_bytes(max(1, n_ins)), dtype=torch.uint8, device=dev)
+        self.batch = BatchedLookup(self.tables, max_jobs=K.BATCH_MAX_JOBS, device=dev)
+        torch.cuda.synchronize(dev)
+
+    def reset_outputs(self):
+        for p in self.pools:
+            p["vals"].zero_()
+            p["found"].zero_()
+        self.ins_status.zero_()
+
+    # ------------------------------------------------------------------ runs
+    def run(self, mode: str = "batched", warmup_fraction: float = 0.1) -> dict:
+        """Serve the whole stream in real time; mode 'batched' (continuous
+        batching) or 'plain' (one launch per burst)."""
+        cfg, st, dev = self.cfg, self.stream, self.device
+        cuda = torch.cuda.current_stream(dev)
+        n_bursts = st.arrival.shape[0]
+        done_at = np.full(n_bursts, np.nan)
+        foot = st.size.astype(np.int64) * KEY_BYTES_IO
+        in_flight = deque()  # (event, first, last, bytes)
+        flight_bytes = 0
+        nxt = 0
+        lib = K.library()
+        job_dtype = np.dtype([("keys", "<u8"), ("out_vals", "<u8"), ("out_found", "<u8"), ("n", "<u4"),
+                              ("table", "<u4")])
+        # a ring of pinned job buffers: the host fills one while earlier copies are still queued
+        ring = [torch.zeros(K.BATCH_MAX_JOBS * K.JOB_BYTES, dtype=torch.uint8).pin_memory() for _ in range(8)]
+        ring_views = [r.numpy().view(job_dtype) for r in ring]
+        ring_event = [None] * len(ring)
+        slot = 0
+        pool_keys = np.array([p["keys"].data_ptr() for p in self.pools], np.uint64)
+        pool_vals = np.array([p["vals"].data_ptr() for p in self.pools], np.uint64)
+        pool_found = np.array([p["found"].data_ptr() for p in self.pools], np.uint64)
+        handles = [t.handle for t in self.tables]
+        ws_small = torch.empty(K.ckpp_workspace_bytes(cfg.max_burst), dtype=torch.uint8, device=dev)
+        launches = 0
+        starts, groups, gpu_busy = [], [], []
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(cuda)
+
+        def retire(block: bool):
+            nonlocal flight_bytes
+            while in_flight and (block or in_flight[0][0].query()):
+                ev, a, b, nbytes = in_flight.popleft()
+                ev.synchronize()
+                done_at[a:b] = ev_time(ev)
+                flight_bytes -= nbytes
+                if starts:
+                    gpu_busy.append(starts.pop(0).elapsed_time(ev) / 1e3)
+                block = False
+
+        def ev_time(ev):
+            return e0.elapsed_time(ev) / 1e3
+
+        sh = cuda.cuda_stream
+        while nxt < n_bursts or in_flight:
+            retire(False)
+            now = time.perf_counter() - t0
+            if nxt < n_bursts and st.arrival[nxt] <= now:
+                hi = int(np.searchsorted(st.arrival, now, side="right"))
+                if mode == "batched":
+                    hi = min(hi, nxt + K.BATCH_MAX_JOBS)
+                    room = cfg.footprint_bytes - flight_bytes
+                    cum = np.cumsum(foot[nxt:hi])
+                    fit = int(np.searchsorted(cum, room, side="right"))
+                    if fit == 0:
+                        if in_flight:
+                            retire(True)
+                            continue
+                        fit = 1  # a burst larger than the budget goes alone
+                    hi = nxt + fit
+                    sel = slice(nxt, hi)
+                    ev_start = torch.cuda.Event(enable_timing=True)
+                    ev_start.record(cuda)
+                    ins = st.insert[sel]
+                    if ins.any():  # the admitted inserts form one contiguous range of the insert pool
+                        first = int(st.offset[sel][ins][0])
+                        n_ins = int(st.size[sel][ins].sum())
+                        lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
+                                              self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
+                                              n_ins, 0, 0, self.ins_status[first:].data_ptr(),
+                                              self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
+                        launches += 1
+                    look = ~ins
+                    nj = int(look.sum())
+                    if nj:
+                        if ring_event[slot] is not None:
+                            ring_event[slot].synchronize()  # the copy that last read this buffer is done
+                        view = ring_views[slot]
+                        tb = st.table[sel][look]
+                        off = st.offset[sel][look].astype(np.uint64)
+                        view["keys"][:nj] = pool_keys[tb] + off * np.uint64(16)
+                        view["out_vals"][:nj] = pool_vals[tb] + off * np.uint64(8)
+                        view["out_found"][:nj] = pool_found[tb] + off
+                        view["n"][:nj] = st.size[sel][look]
+                        view["table"][:nj] = tb
+                        nbytes_jobs = nj * K.JOB_BYTES
+                        self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
+                        # the job count is known here: the prefix scan is sized to it (no device count)
+                        K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs, nj, None, 0, self.batch.tuning, cuda)
+                        launches += 1
+                    ev = torch.cuda.Event(enable_timing=True)
+                    ev.record(cuda)
+                    if nj:
+                        ring_event[slot] = ev
+                        slot = (slot + 1) % len(ring)
+                    nbytes = int(cum[fit - 1])
+                    in_flight.append((ev, nxt, hi, nbytes))
+                    starts.append(ev_start)
+                    groups.append(hi - nxt)
+                    flight_bytes += nbytes
+                    nxt = hi
+                else:  # plain: one launch per burst, as it arrives
+                    for b in range(nxt, hi):
+                        t = int(st.table[b])
+                        n = int(st.size[b])
+                        off = int(st.offset[b])
+                        if st.insert[b]:
+                            lib.ckpp_bulk_insert(handles[t], self.ins_keys[off:].data_ptr(),
+                                                 self.ins_vals[off:].data_ptr(), n, 0, 0,
+                                                 self.ins_status[off:].data_ptr(), ws_small.data_ptr(),
+                                                 ws_small.numel(), sh)
+                        else:
+                            p = self.pools[t]
+                            lib.ckpp_bulk_lookup(handles[t], p["keys"][off:].data_ptr(), n, p["vals"][off:].data_ptr(),
+                                                 p["found"][off:].data_ptr(), 0, 0, sh)
+                        launches += 1
+                    ev = torch.cuda.Event(enable_timing=True)
+                    ev.record(cuda)
+                    in_flight.append((ev, nxt, hi, 0))
+                    nxt = hi
+            elif not in_flight and nxt < n_bursts:
+                time.sleep(max(0.0, min(50e-6, st.arrival[nxt] - now)))
+        retire(True)
+        wall = time.perf_counter() - t0
+        lat = (done_at - st.arrival) * 1e6
+        keep = st.arrival >= warmup_fraction * cfg.duration_s
+        lk = ~st.insert
+        served = int(st.size[lk].sum())
+        return {
+            "mode": mode, "bursts": int(n_bursts), "lookups": served, "inserts": int(st.size[st.insert].sum()),
+            "offered_glookups": round(served / cfg.duration_s / 1e9, 3),
+            "achieved_glookups": round(served / wall / 1e9, 3), "wall_s": round(wall, 4),
+            "launches": launches,
+            "groups": len(groups) if groups else None,
+            "bursts_per_group": round(float(np.mean(groups)), 1) if groups else None,
+            "gpu_busy_fraction": round(float(np.sum(gpu_busy)) / wall, 3) if gpu_busy else None,
+            "gpu_ms_per_group": round(float(np.mean(gpu_busy)) * 1e3, 4) if gpu_busy else None,
+            "latency_us": {"p50": round(float(np.percentile(lat[keep], 50)), 1),
+                           "p99": round(float(np.percentile(lat[keep], 99)), 1),
+                           "p99_9": round(float(np.percentile(lat[keep], 99.9)), 1),
+                           "max": round(float(lat[keep].max()), 1)},
+        }
+
+    def check(self) -> dict:
+        """Every lookup output equals the workload's map; every insert status is
+        INSERTED and the inserted flows are found afterwards."""
+        ok_lookups = all(bool(torch.equal(p["found"], p["expect_found"])) and
+                         bool(torch.equal(p["vals"], p["expect_value"])) for p in self.pools)
+        ok_inserts = bool((self.ins_status == K.ST_INSERTED).all())
+        return {"lookups_match_map": ok_lookups, "inserts_all_inserted": ok_inserts}

@@ -142,3 +142,60 @@ def test_batched_matches_oracle_small():
         ov, of = ors[i].lookup(qs[i].keys)
         assert (outs[i][1].cpu().numpy() == of).all()
         assert (outs[i][0].cpu().numpy().view(np.uint64) == ov).all()
+
+
+def test_batch_insert_and_delete_across_tables_match_per_table_calls():
+    """ckpp_batch_insert / ckpp_batch_delete (one call, keys bound for many
+    tables) give the statuses and tables of one ckpp_bulk_insert /
+    ckpp_bulk_delete per table, and the oracle's."""
+    from paper_1712_09624_gb300 import _ckpp as K
+    from paper_1712_09624_gb300.batched import BatchedLookup
+    from gpu_layout import download, oracle_live
+    rng = np.random.default_rng(80)
+    sizes = [3, 64, 500, 2000]
+    multi = [FT(nb, timers=(i % 2 == 1), seed=80 + i) for i, nb in enumerate(sizes)]
+    single = [FT(nb, timers=(i % 2 == 1), seed=80 + i) for i, nb in enumerate(sizes)]
+    ors = [oracle.Table(nb, 8, i % 2 == 1, 80 + i) for i, nb in enumerate(sizes)]
+    batch = BatchedLookup(multi)
+    pools = [W.make_keys(80 + i, 81, int(1.1 * nb * 8)) for i, nb in enumerate(sizes)]
+    now = 10
+    for step in range(6):
+        tids, keys, vals = [], [], []
+        for i, nb in enumerate(sizes):
+            cap = int(0.85 * nb * 8) - ors[i].size()
+            n = int(rng.integers(0, max(1, min(cap, 400)) + 1))
+            pick = pools[i][rng.integers(0, pools[i].shape[0], n)]
+            tids.append(np.full(n, i, np.int32)), keys.append(pick)
+            vals.append(rng.integers(0, 2**62, n, dtype=np.int64).astype(np.uint64))
+        order = rng.permutation(sum(len(t) for t in tids))  # keys of all tables interleaved
+        T = np.concatenate(tids)[order]
+        Kk = np.concatenate(keys)[order]
+        V = np.concatenate(vals)[order]
+        bad = np.array([len(sizes) + 5], np.int32)  # one key naming no table
+        T = np.concatenate([T, bad]); Kk = np.concatenate([Kk, pools[0][:1]]); V = np.concatenate([V, [7]]).astype(np.uint64)
+        kd = torch.from_numpy(Kk).cuda(); td = torch.from_numpy(T).cuda()
+        vd = torch.from_numpy(V.view(np.int64)).cuda(); st = torch.empty(len(T), dtype=torch.uint8, device="cuda")
+        ws = torch.empty(K.ckpp_workspace_bytes(len(T)), dtype=torch.uint8, device="cuda")
+        K.ckpp_batch_insert(batch.handle, kd, td, vd, st, ws, now, 500)
+        st = st.cpu().numpy()
+        assert st[-1] == K.ST_NO_TABLE
+        for i in range(len(sizes)):
+            sel = np.nonzero(T[:-1] == i)[0]
+            ref = single[i].insert(Kk[sel], V[sel], now, 500).cpu().numpy()
+            assert (st[sel] == ref).all()
+            assert (st[sel] == ors[i].insert(Kk[sel], V[sel], now, 500)).all()
+        # delete a few keys of every table in one call
+        dsel = rng.choice(len(T) - 1, size=min(200, len(T) - 1), replace=False)
+        dst = torch.empty(len(dsel), dtype=torch.uint8, device="cuda")
+        K.ckpp_batch_delete(batch.handle, torch.from_numpy(Kk[dsel]).cuda(), torch.from_numpy(T[dsel]).cuda(),
+                            dst, ws, now)
+        dst = dst.cpu().numpy()
+        for i in range(len(sizes)):
+            sel = np.nonzero(T[dsel] == i)[0]
+            assert (dst[sel] == ors[i].delete(Kk[dsel][sel], now)).all()
+            single[i].delete(Kk[dsel][sel], now)
+        now += 7
+    for i in range(len(sizes)):
+        d = download(multi[i])
+        assert d.check() == []
+        assert d.live(now) == oracle_live(ors[i], now)
