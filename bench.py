@@ -70,6 +70,7 @@ def parse():
                         "random-read: the GPU's random 32/64-byte read ceiling; served: continuous-batching "
                         "request loop vs one launch per burst")
     p.add_argument("--serve-seconds", type=float, default=0.2, help="served: seconds of offered traffic")
+    p.add_argument("--serve-modes", default="batched,plain", help="served: arms to run")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
     return p.parse_args()
 
@@ -674,7 +675,7 @@ def run_served(args):
     torch.cuda.set_device(0)
     cfg = ServeConfig(duration_s=args.serve_seconds, seed=args.seed)
     out = {}
-    for mode in ("batched", "plain"):
+    for mode in args.serve_modes.split(","):
         svc = Service(cfg)
         r = svc.run(mode)
         r.update(svc.check())
@@ -687,7 +688,7 @@ def run_served(args):
             "config": {"workload": "served form: 64 ports, Poisson bursts of 32..4096 keys, 2 G lookups/s offered, "
                                    "256 tables / 500M slots, 10% inserts", "duration_s": cfg.duration_s,
                        "footprint_budget_bytes": cfg.footprint_bytes},
-            "batched": b, "plain_per_burst": out["plain"]}
+            "batched": b, "plain_per_burst": out.get("plain")}
 
 
 def main():

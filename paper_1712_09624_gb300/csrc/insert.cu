@@ -183,31 +183,62 @@ __device__ int try_place(const TableView& t, uint32_t tid, const Key& k, uint64_
 }
 
 // Breadth-first search over buckets from b1 and b2 (lock-free reads; the path
-// is re-validated under its locks). Returns the index of a node whose bucket
-// has a free or dead slot (in hole), or -1.
+// is re-validated under its locks). Expanding a bucket issues the key reads of
+// its 8 slots together, then the control-word (and expiry) reads of the 8
+// buckets those entries can move to, so one level of the search costs two
+// memory round trips; a child with a free or dead slot ends the search (the
+// first such child in queue order, i.e. a shortest path). Returns the node
+// index of the bucket with the hole (in hole), or -1.
 template <int kBfsNodes, int kBfsDepth>
 __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, Node* q, uint32_t& hole) {
   int nq = 0;
   q[nq++] = Node{a.b1, -1, 0, 0};
   q[nq++] = Node{a.b2, -1, 0, 0};
-  for (int qi = 0; qi < nq; ++qi) {
-    const Node cur = q[qi];
+  for (int r = 0; r < 2; ++r) {  // the roots themselves (a slot may have freed up)
     Snap s;
-    snap_bucket(t, cur.bucket, s);
+    snap_bucket(t, q[r].bucket, s);
     const uint32_t f = free_mask(t, (uint32_t)s.w[3], s, now);
     if (f) {
       hole = __ffs(f) - 1;
-      return qi;
+      return r;
     }
+  }
+  for (int qi = 0; qi < nq; ++qi) {
+    const Node cur = q[qi];
     if (cur.depth >= kBfsDepth) continue;
+    uint64_t k0[kSlots], k1[kSlots];
+#pragma unroll
+    for (uint32_t sl = 0; sl < kSlots; ++sl) ld128_cg(record_ptr(t, cur.bucket, sl), k0[sl], k1[sl]);
+    uint32_t y[kSlots], cy[kSlots];
+    uint64_t e0[kSlots], e1[kSlots];
+#pragma unroll
+    for (uint32_t sl = 0; sl < kSlots; ++sl) {
+      const Addr e = address_of(Key{k0[sl], k1[sl]}, t.nb, t.seed);
+      y[sl] = (e.b1 == cur.bucket) ? e.b2 : e.b1;
+    }
+#pragma unroll
+    for (uint32_t sl = 0; sl < kSlots; ++sl) {
+      cy[sl] = ld32_cg(ctrl_ptr(t, y[sl]));
+      if (t.timers) {
+        ld128_cg(expiry_ptr(t, y[sl], 0), e0[sl], e1[sl]);
+      } else {
+        e0[sl] = e1[sl] = 0;
+      }
+    }
     for (uint32_t sl = 0; sl < kSlots && nq < kBfsNodes; ++sl) {
-      uint64_t r[4];
-      ld256_cg(record_ptr(t, cur.bucket, sl), r);
-      const Addr e = address_of(Key{r[0], r[1]}, t.nb, t.seed);
-      const uint32_t y = (e.b1 == cur.bucket) ? e.b2 : e.b1;
       bool seen = false;
-      for (int j = 0; j < nq; ++j) seen |= (q[j].bucket == y);
-      if (!seen) q[nq++] = Node{y, (int16_t)qi, (uint8_t)sl, (uint8_t)(cur.depth + 1)};
+      for (int j = 0; j < nq; ++j) seen |= (q[j].bucket == y[sl]);
+      if (seen) continue;
+      q[nq] = Node{y[sl], (int16_t)qi, (uint8_t)sl, (uint8_t)(cur.depth + 1)};
+      Snap s;
+      s.e0 = e0[sl];
+      s.e1 = e1[sl];
+      const uint32_t f = free_mask(t, cy[sl], s, now);
+      ++nq;
+      if (f) {
+        hole = __ffs(f) - 1;
+        return nq - 1;
+      }
     }
   }
   return -1;
