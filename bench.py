@@ -64,11 +64,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side", action="store_true", help="skip pos/neg/e2e/mutation side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle timing budget")
-    p.add_argument("--workload", default="scale", choices=["scale", "batched", "sweep", "random-read", "served"],
+    p.add_argument("--workload", default="scale",
+                   choices=["scale", "batched", "sweep", "random-read", "served", "mixed"],
                    help="scale: the headline at-scale lookup (default); batched: many tables in one launch vs "
                         "one launch per table; sweep: load factor x negative rate x lookup strategy grid; "
                         "random-read: the GPU's random 32/64-byte read ceiling; served: continuous-batching "
-                        "request loop vs one launch per burst")
+                        "request loop vs one launch per burst; mixed: insert/lookup/delete/expire mix on a "
+                        "200M-slot table with timers")
+    p.add_argument("--mixed-batches", type=int, default=400, help="mixed: batches (time units) to run")
     p.add_argument("--serve-seconds", type=float, default=0.2, help="served: seconds of offered traffic")
     p.add_argument("--serve-modes", default="batched,plain", help="served: arms to run")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
@@ -181,6 +184,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
 
     from paper_1712_09624_gb300 import _ckpp as K
+    from paper_1712_09624_gb300 import dist as D
     from paper_1712_09624_gb300 import workload as W
     from paper_1712_09624_gb300.table import FlowTable
 
@@ -189,7 +193,7 @@ def run_ours(args, rank, world, local_rank):
     nb = 1 << args.log2_buckets
     n_fill = int(args.load_factor * nb * 8)
     n = 1 << args.log2_batch
-    seed = args.seed + 1000 * rank  # independent tables per rank
+    seed = D.rank_seed(args.seed, rank)  # independent tables per rank
     stream = torch.cuda.current_stream()
 
     fill = W.fill(seed, n_fill)
@@ -256,12 +260,9 @@ def run_ours(args, rank, world, local_rank):
     time.sleep(0.15 if sampler else 0)
     if sampler:
         sampler.stop()
-    if world > 1:
-        t = torch.tensor([secs], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = D.max_over_ranks(secs, dev)
     per_launch = secs / args.steps
-    value = world * n * args.steps / secs / 1e9
+    value = D.job_throughput(n, args.steps, secs, world) / 1e9
 
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / per_launch / 1e9
@@ -691,11 +692,126 @@ def run_served(args):
             "batched": b, "plain_per_burst": out.get("plain")}
 
 
+def run_mixed(args):
+    """Mixed mutation workload on one 200M-slot table with timers (25M buckets
+    x 8). The warm fill reaches LF 0.9 with expiries spread over the next 1000
+    time units. Then batches run, time +1 per batch, drawn 20:70:5:5 as:
+    - insert 900K new flows (ttl 1000);
+    - look up 4M keys, Zipf(0.99) over the live flows;
+    - delete 250K live flows (uniform);
+    - expire (full scan).
+    A flow is named by its index in one global sequence of keys (the device
+    generator), so the live window is known without host bookkeeping."""
+    import torch
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    from paper_1712_09624_gb300.table import FlowTable
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(args.seed)
+    nb = 25_000_000
+    warm = int(0.9 * nb * 8)
+    sub = 50  # warm sub-batches, expiries 20, 40, ..., 1000
+    t = FlowTable(nb, timers=True, seed=args.seed, device=dev)
+    ws = torch.empty(K.ckpp_workspace_bytes(1 << 22), dtype=torch.uint8, device=dev)
+    per = (warm + sub - 1) // sub
+    t_fill = time.time()
+    for j in range(sub):
+        lo = j * per
+        n = min(per, warm - lo)
+        for c in range(0, n, 1 << 22):
+            m = min(1 << 22, n - c)
+            k, v = WG.fill_keys(args.seed, lo + c, m, dev)
+            st = torch.empty(m, dtype=torch.uint8, device=dev)
+            K.ckpp_bulk_insert(t.handle, k, v, st, ws, 0, 20 * (j + 1), stream)
+    torch.cuda.synchronize()
+    fill_s = time.time() - t_fill
+    # Zipf(0.99) ranks over [1, N] by the inverse of the continuous CDF approximation
+    n_look, n_ins, n_del = 4_000_000, 900_000, 250_000
+    s_exp = 0.99
+    u = rng.random(n_look)
+    big_n = float(warm)
+    ranks = np.floor((1 + u * (big_n ** (1 - s_exp) - 1)) ** (1 / (1 - s_exp))).astype(np.int64) - 1
+    ranks_d = torch.from_numpy(ranks).to(dev)
+    mult = 0x9E3779B97F4A7C15 & ((1 << 63) - 1)
+    ops = rng.choice(4, size=args.mixed_batches, p=[0.20, 0.70, 0.05, 0.05])
+    next_flow = warm
+    now = 0
+    time_by = {0: 0.0, 1: 0.0, 2: 0.0, 3: 0.0}
+    count_by = {0: 0, 1: 0, 2: 0, 3: 0}
+    keys_by = {0: 0, 1: 0, 2: 0, 3: 0}
+    hits = torch.zeros(1, dtype=torch.int64, device=dev)
+    deleted = torch.zeros(1, dtype=torch.int64, device=dev)
+    out_v = torch.empty(n_look, dtype=torch.int64, device=dev)
+    out_f = torch.empty(n_look, dtype=torch.uint8, device=dev)
+    st_ins = torch.empty(n_ins, dtype=torch.uint8, device=dev)
+    st_del = torch.empty(n_del, dtype=torch.uint8, device=dev)
+    n_expired = torch.zeros(1, dtype=torch.int64, device=dev)
+    for b, op in enumerate(ops):
+        now += 1
+        lo_live = min(warm, per * (now // 20))  # warm sub-batches whose expiry passed are dead
+        window = next_flow - lo_live
+        # inputs of this batch are prepared before its timed region
+        if op == 0:
+            k, v = WG.fill_keys(args.seed, next_flow, n_ins, dev)
+            next_flow += n_ins
+        elif op == 1:
+            salt = int(rng.integers(0, 2**31))
+            idx = lo_live + torch.remainder(ranks_d * mult + salt, window)
+            k = WG.keys_at(args.seed, idx)
+        elif op == 2:
+            idx = torch.from_numpy(rng.integers(lo_live, next_flow, n_del)).to(dev)
+            k = WG.keys_at(args.seed, idx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if op == 0:
+            K.ckpp_bulk_insert(t.handle, k, v, st_ins, ws, now, 1000, stream)
+        elif op == 1:
+            K.ckpp_bulk_lookup(t.handle, k, out_v, out_f, now, 0, stream)
+        elif op == 2:
+            K.ckpp_bulk_delete(t.handle, k, st_del, ws, now, stream)
+        else:
+            K.ckpp_expire(t.handle, now, n_expired, stream)
+        e1.record(stream)
+        if op == 1:
+            hits += out_f.sum()
+        elif op == 2:
+            deleted += (st_del == K.ST_DELETED).sum()
+        e1.synchronize()
+        time_by[op] += e0.elapsed_time(e1) / 1e3
+        count_by[op] += 1
+        keys_by[op] += {0: n_ins, 1: n_look, 2: n_del, 3: nb}[op]
+    torch.cuda.synchronize()
+    st = t.stats(now)
+    names = {0: "insert", 1: "lookup", 2: "delete", 3: "expire"}
+    per_op = {names[o]: {"batches": count_by[o], "keys_or_buckets": keys_by[o],
+                         "ms_per_batch": round(time_by[o] / max(1, count_by[o]) * 1e3, 4),
+                         "per_s": round(keys_by[o] / max(time_by[o], 1e-12) / 1e6, 1)} for o in names}
+    total_keys = keys_by[0] + keys_by[1] + keys_by[2]
+    total_time = sum(time_by.values())
+    return {"metric": "mixed insert/lookup/delete/expire: keys per second (GPU time)",
+            "value": round(total_keys / total_time / 1e9, 4), "unit": "Gkeys/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "mixed mutation workload: 200M-slot table with timers, 20:70:5:5 "
+                                   "insert/lookup/delete/expire batches, Zipf(0.99) lookups, ttl 1000",
+                       "n_buckets": nb, "warm_entries": warm, "batches": int(args.mixed_batches),
+                       "warm_fill_s": round(fill_s, 1)},
+            "per_op": per_op, "lookup_hit_rate": round(float(hits.item()) / max(1, keys_by[1]), 4),
+            "deleted_live": int(deleted.item()), "expired": int(n_expired.item()),
+            "table_after": {"live": st["n_live"], "occupied": st["n_occupied"],
+                            "load_factor_live": round(st["n_live"] / (nb * 8), 4),
+                            "in_secondary": round(st["n_in_secondary"] / max(1, st["n_occupied"]), 4)},
+            "device_errors": t.sync_status()}
+
+
 def main():
     args = parse()
     if args.workload != "scale" and args.impl == "ours":
         run = {"batched": run_batched, "sweep": run_sweep, "random-read": run_random_read,
-               "served": run_served}[args.workload]
+               "served": run_served, "mixed": run_mixed}[args.workload]
         print(json.dumps(run(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

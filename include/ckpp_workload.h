@@ -30,6 +30,10 @@ typedef struct CUstream_st* ckpp_wl_stream_t;
 int ckpp_wl_fill_keys(uint64_t seed, uint64_t first, uint64_t n, uint8_t* out_keys, uint64_t* out_vals,
                       ckpp_wl_stream_t stream);
 
+/* Fill keys at arbitrary indices: out_keys[i] = key idx[i] of the fill of `seed`
+ * (idx: device uint64 [n]). */
+int ckpp_wl_keys_at(uint64_t seed, const uint64_t* idx, uint64_t n, uint8_t* out_keys, ckpp_wl_stream_t stream);
+
 /* workload.lookup_batch(seed, n, workload.fill(seed, n_inserted), neg_rate,
  * batch_id): keys [n][16], expected found flags [n] and values [n] (either
  * expectation pointer may be NULL). */

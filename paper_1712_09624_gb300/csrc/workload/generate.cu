@@ -65,6 +65,14 @@ __global__ void fill_kernel(uint64_t seed, uint64_t first, uint64_t n, uint8_t* 
   if (vals) vals[i] = first + i;
 }
 
+__global__ void keys_at_kernel(uint64_t seed, const uint64_t* __restrict__ idx, uint64_t n, uint8_t* keys) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t k0, k1;
+  make_key(seed, kStreamInsert, idx[i], k0, k1);
+  reinterpret_cast<ulonglong2*>(keys)[i] = make_ulonglong2(k0, k1);
+}
+
 __global__ void lookup_batch_kernel(uint64_t seed, uint64_t batch_id, uint64_t n, uint64_t m, double neg_rate,
                                     uint8_t* keys, uint8_t* found, uint64_t* value) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -93,6 +101,16 @@ extern "C" int ckpp_wl_fill_keys(uint64_t seed, uint64_t first, uint64_t n, uint
     return -1;
   fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(seed, first, n, out_keys,
                                                                                                  out_vals);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+extern "C" int ckpp_wl_keys_at(uint64_t seed, const uint64_t* idx, uint64_t n, uint8_t* out_keys,
+                               ckpp_wl_stream_t stream) {
+  if (n == 0) return 0;
+  if (!idx || !out_keys || reinterpret_cast<uintptr_t>(out_keys) % 16 || reinterpret_cast<uintptr_t>(idx) % 8)
+    return -1;
+  keys_at_kernel<<<(unsigned)((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(seed, idx, n,
+                                                                                                   out_keys);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

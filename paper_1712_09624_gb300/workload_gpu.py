@@ -23,6 +23,8 @@ def _load():
     L.ckpp_wl_fill_keys.argtypes = [u64, u64, u64, vp, vp, vp]
     L.ckpp_wl_lookup_batch.restype = C.c_int
     L.ckpp_wl_lookup_batch.argtypes = [u64, u64, u64, u64, C.c_double, vp, vp, vp, vp]
+    L.ckpp_wl_keys_at.restype = C.c_int
+    L.ckpp_wl_keys_at.argtypes = [u64, vp, u64, vp, vp]
     L.ckpp_wl_random_read.restype = C.c_int
     L.ckpp_wl_random_read.argtypes = [vp, u64, C.c_uint32, u64, u64, vp, vp]
     return L
@@ -45,6 +47,17 @@ def fill_keys(seed: int, first: int, n: int, device, stream=None, with_values: b
     if rc:
         raise RuntimeError(f"ckpp_wl_fill_keys failed ({rc})")
     return keys, vals
+
+
+def keys_at(seed: int, idx: torch.Tensor, stream=None) -> torch.Tensor:
+    """Keys idx[i] of workload.fill(seed, .) for a device int64 index tensor."""
+    n = idx.shape[0]
+    keys = torch.empty((n, 16), dtype=torch.uint8, device=idx.device)
+    rc = _lib.ckpp_wl_keys_at(seed & (2**64 - 1), idx.data_ptr() if n else None, n,
+                              keys.data_ptr() if n else None, _stream(stream))
+    if rc:
+        raise RuntimeError(f"ckpp_wl_keys_at failed ({rc})")
+    return keys
 
 
 def lookup_batch(seed: int, n: int, n_inserted: int, neg_rate: float, batch_id: int = 0, device=None, stream=None):

@@ -26,3 +26,12 @@ def test_lookup_batch_matches_host(seed, n, m, neg, bid):
     assert (k.cpu().numpy() == ref.keys).all()
     assert (f.cpu().numpy() == ref.expect_found).all()
     assert (v.cpu().numpy().view(np.uint64) == ref.expect_value).all()
+
+
+def test_keys_at_match_host():
+    import torch
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    idx = np.array([0, 5, 3, 1000, 77, 77, 2], np.int64)
+    k = WG.keys_at(9, torch.from_numpy(idx).cuda())
+    ref = W.fill(9, 1001).keys[idx]
+    assert (k.cpu().numpy() == ref).all()
