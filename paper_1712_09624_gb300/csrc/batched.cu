@@ -147,7 +147,7 @@ __device__ void lookup_g(const TableView* __restrict__ tables, uint32_t n_tables
                        : confirm<false, false>(tv[g], b, candidates(h2, a[g].tag), k[g], stream, rec[g], expiry, nrec);
     }
     bool found = s >= 0;
-    if (found && tv[g].timers) found = alive16(ld16_cg(expiry_ptr(tv[g], b, s)), now);
+    if (found && tv[g].timers) found = alive16((uint32_t)(rec[g][3] & 0xFFFFu), now);
     jb.out_vals[local[g]] = found ? rec[g][2] : 0ull;
     jb.out_found[local[g]] = found ? 1 : 0;
   }

@@ -15,7 +15,10 @@
 //   bytes 28..31  moved    moved counter (Sec. 4.1)
 // With timers, the second sector holds expiry[8] (16-bit, Sec. 4.2) in bytes
 // 32..47; bytes 48..63 are reserved (zero).
-// Record (32 B, one sector): key (16 B), value (u64), reserved (u64, zero).
+// Record (32 B, one sector): key (16 B), value (u64), then a u64 whose low 16
+// bits copy the slot's expiry in tables with timers (zero otherwise); the
+// rest is zero. The bucket's expiry[] is the copy inserts and scans use; the
+// record's copy lets a lookup test liveness with the sector it reads anyway.
 #pragma once
 
 #include <cstdint>
@@ -213,7 +216,15 @@ __device__ __forceinline__ void st16_cg(void* p, uint32_t v) {
   asm volatile("st.global.relaxed.gpu.u16 [%0], %1;" ::"l"(p), "h"((uint16_t)v) : "memory");
 }
 
-// Records are read as 4 x u64: k0, k1, value, reserved.
+// Set a slot's expiry: the bucket's copy and the record's copy.
+__device__ __forceinline__ void set_expiry(const TableView& t, uint32_t b, uint32_t s, uint32_t expiry) {
+  asm volatile("st.global.relaxed.gpu.u16 [%0], %1;" ::"l"(reinterpret_cast<uint16_t*>(t.buckets + ((uint64_t)b << t.bucket_shift) + 32) + s),
+               "h"((uint16_t)expiry) : "memory");
+  asm volatile("st.global.relaxed.gpu.u16 [%0], %1;" ::"l"(t.records + ((uint64_t)b * kSlots + s) * kRecordBytes + 24),
+               "h"((uint16_t)expiry) : "memory");
+}
+
+// Records are read as 4 x u64: k0, k1, value, expiry copy (timers) / zero.
 __device__ __forceinline__ bool same_key(const uint64_t (&r)[4], const Key& k) { return r[0] == k.k0 && r[1] == k.k1; }
 
 __device__ __forceinline__ void latch_error(const TableView& t, uint32_t bit) { atomicOr(t.err, bit); }

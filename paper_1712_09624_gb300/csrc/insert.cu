@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
   if (slot >= 0) {
     const bool was_alive = !t.timers || alive16(snap_expiry(*sb, slot), now);
     st64_cg(record_ptr(t, b, slot) + 16, v);
-    if (t.timers) st16_cg(expiry_ptr(t, b, slot), expiry);
+    if (t.timers) set_expiry(t, b, slot, expiry);
     st = was_alive ? kStUpdated : kStInserted;
   } else {
     const uint32_t f1 = free_mask(t, c1, s1, now);

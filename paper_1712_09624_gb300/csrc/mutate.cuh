@@ -134,7 +134,7 @@ __device__ __forceinline__ void evict_entry(const TableView& t, uint32_t tid, ui
 // primary's moved counter (Sec. 4.1). The caller holds the primary's lock too.
 __device__ __forceinline__ void place_entry(const TableView& t, uint32_t b, uint32_t s, const Key& k, uint64_t v,
                                             const Addr& a, uint32_t expiry, uint32_t& ctrl) {
-  st256_cg(record_ptr(t, b, s), k.k0, k.k1, v, 0ull);
+  st256_cg(record_ptr(t, b, s), k.k0, k.k1, v, t.timers ? (uint64_t)(expiry & 0xFFFFu) : 0ull);
   st16_cg(tag_ptr(t, b, s), a.tag);
   if (t.timers) st16_cg(expiry_ptr(t, b, s), expiry);
   ctrl |= 1u << s;

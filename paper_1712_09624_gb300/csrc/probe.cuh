@@ -23,15 +23,16 @@ enum LookupVariant : int { kBloom = 0, kOptimistic = 1, kPessimistic = 2 };
 
 // Confirm the candidate slots of bucket b (tag matches among busy slots) by
 // reading their records. Returns the matching slot or -1; rec holds its record.
-// With timers the candidate's expiry is fetched alongside its record.
+// With timers the record carries a copy of the slot's 16-bit expiry (its low
+// bytes 24..25), so the alive test costs no read beyond the record itself.
 template <bool kTimers, bool kCount>
 __device__ __forceinline__ int confirm(const TableView& t, uint32_t b, uint32_t cand, const Key& k, uint64_t pol,
                                        uint64_t (&rec)[4], uint32_t& expiry, uint32_t& nrec) {
   while (cand) {
     const int s = __ffs(cand) - 1;
     cand &= cand - 1;
-    if (kTimers) expiry = ld16_cg(expiry_ptr(t, b, s));
     ld256_ro(record_ptr(t, b, s), pol, rec);
+    if (kTimers) expiry = (uint32_t)(rec[3] & 0xFFFFu);
     if (kCount) ++nrec;
     if (same_key(rec, k)) return s;
   }
@@ -75,7 +76,7 @@ __device__ __forceinline__ bool probe_key(const TableView& t, const Key& k, uint
   // Sec. 4.2: a dead entry is ignored; a hit may refresh the expiry.
   if (kTimers && found) {
     found = alive16(expiry, now);
-    if (!kCount && found && refresh_ttl) st16_cg(expiry_ptr(t, b, s), now + refresh_ttl);
+    if (!kCount && found && refresh_ttl) set_expiry(t, b, s, now + refresh_ttl);
   }
   value = found ? rec[2] : 0ull;
   return found;

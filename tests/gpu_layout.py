@@ -83,8 +83,14 @@ class Decoded:
             bad.append("in_secondary flag disagrees with the bucket")
         if not (self.tags[b, s] == a["tag"]).all():
             bad.append("stored tag differs from the key's tag")
-        if (self.rec_reserved[occ] != 0).any():
+        mirror = self.rec_reserved[occ] & np.uint64(0xFFFF)
+        if (self.rec_reserved[occ] >> np.uint64(16) != 0).any():
             bad.append("record reserved bytes not zero")
+        if self.timers:
+            if not (mirror == self.expiry[b, s].astype(np.uint64)).all():
+                bad.append("record expiry copy differs from the bucket's expiry")
+        elif (mirror != 0).any():
+            bad.append("record expiry copy set in a table without timers")
         bits = (np.uint64(1) << a["bit1"].astype(np.uint64)) | (np.uint64(1) << a["bit2"].astype(np.uint64))
         p = a["b1"][insec]
         if not ((self.bloom[p] & bits[insec]) == bits[insec]).all():
