@@ -56,6 +56,47 @@ __global__ void __launch_bounds__(256) lookup_kernel(TableView t, const uint8_t*
 
 constexpr int kLookupThreads = 256;
 
+// Host-buffer lookup: keys read and results written in place in pinned host
+// memory over NVLink-C2C. Small scattered stores are what the link does worst,
+// so a block stages its 256 values and 256 flags in shared memory and writes
+// them out as 16-byte vectors (2 KB + 256 B per block); keys come in as one
+// coalesced 16-byte load per thread.
+template <bool kTimers>
+__global__ void __launch_bounds__(kLookupThreads) lookup_host_kernel(TableView t, const uint8_t* __restrict__ keys,
+                                                                     uint64_t n, uint64_t* __restrict__ out_vals,
+                                                                     uint8_t* __restrict__ out_found, uint32_t now,
+                                                                     uint32_t refresh_ttl) {
+  __shared__ __align__(16) uint64_t vals[kLookupThreads];
+  __shared__ __align__(16) uint8_t flags[kLookupThreads];
+  const uint64_t base = (uint64_t)blockIdx.x * kLookupThreads;
+  const uint64_t i = base + threadIdx.x;
+  uint64_t value = 0;
+  bool found = false;
+  if (i < n) {
+    const uint64_t keep = policy_evict_last();
+    const uint64_t stream = policy_evict_first();
+    const ulonglong2 kk = *reinterpret_cast<const ulonglong2*>(keys + 16 * i);
+    uint32_t nsec = 0, nrec = 0;
+    found = probe_key<kTimers, false, kBloom>(t, Key{kk.x, kk.y}, now, refresh_ttl, keep, stream, value, nsec, nrec);
+  }
+  vals[threadIdx.x] = value;
+  flags[threadIdx.x] = found ? 1 : 0;
+  __syncthreads();
+  if (base + kLookupThreads <= n) {
+    // full block: 128 threads store the values, 16 the flags, 16 bytes each
+    if (threadIdx.x < kLookupThreads / 2) {
+      reinterpret_cast<ulonglong2*>(out_vals + base)[threadIdx.x] =
+          reinterpret_cast<const ulonglong2*>(vals)[threadIdx.x];
+    } else if (threadIdx.x < kLookupThreads / 2 + kLookupThreads / 16) {
+      const int j = threadIdx.x - kLookupThreads / 2;
+      reinterpret_cast<uint4*>(out_found + base)[j] = reinterpret_cast<const uint4*>(flags)[j];
+    }
+  } else if (i < n) {
+    out_vals[i] = vals[threadIdx.x];
+    out_found[i] = flags[threadIdx.x];
+  }
+}
+
 template <bool kTimers, bool kCount, bool kHostIO, int kVariant>
 cudaError_t launch(const TableView& t, const uint8_t* keys, uint64_t n, uint64_t* out_vals, uint8_t* out_found,
                    uint32_t now, uint32_t refresh_ttl, unsigned long long* counts, cudaStream_t s) {
@@ -80,6 +121,16 @@ cudaError_t launch_lookup(const TableView& t, const uint8_t* keys, uint64_t n, u
                           cudaStream_t s) {
   if (host_io) {
     if (variant != kBloom) return cudaErrorInvalidValue;
+    const bool vec = (reinterpret_cast<uintptr_t>(out_vals) % 16 == 0) && (reinterpret_cast<uintptr_t>(out_found) % 16 == 0);
+    if (vec) {
+      const unsigned blocks = (unsigned)((n + kLookupThreads - 1) / kLookupThreads);
+      if (t.timers) {
+        lookup_host_kernel<true><<<blocks, kLookupThreads, 0, s>>>(t, keys, n, out_vals, out_found, now, refresh_ttl);
+      } else {
+        lookup_host_kernel<false><<<blocks, kLookupThreads, 0, s>>>(t, keys, n, out_vals, out_found, now, 0);
+      }
+      return cudaGetLastError();
+    }
     if (t.timers) return launch<true, false, true, kBloom>(t, keys, n, out_vals, out_found, now, refresh_ttl, nullptr, s);
     return launch<false, false, true, kBloom>(t, keys, n, out_vals, out_found, now, 0, nullptr, s);
   }

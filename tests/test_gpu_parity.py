@@ -367,3 +367,24 @@ def test_full_size_config_properties():
     idx = np.random.default_rng(2).choice(q.keys.shape[0], 1 << 17, replace=False)
     ov, of = o.lookup(q.keys[idx])
     assert (fd.cpu().numpy()[idx] == of).all() and (np_vals(v)[idx] == ov).all()
+
+
+@pytest.mark.parametrize("n", [1, 300, 70001])
+def test_host_buffer_lookup_paths(K, n):
+    """ckpp_bulk_lookup on pinned host buffers (read and written in place by the
+    kernel) equals the device-buffer lookup: 16-byte-aligned outputs (staged
+    vector stores, ragged last block) and misaligned outputs (scalar stores)."""
+    nb = 1 << 12
+    f = W.fill(90, int(0.9 * nb * 8))
+    g = FT(nb, timers=True, seed=90)
+    g.insert(f.keys, f.values, 5, 600)
+    q = W.lookup_batch(90, n, f, 0.4)
+    dv, dfd = g.lookup(q.keys, 7)
+    hk = torch.from_numpy(q.keys).pin_memory()
+    for off in (0, 1):
+        hv_raw = torch.zeros(n + 2, dtype=torch.int64).pin_memory()
+        hf_raw = torch.zeros(n + 16, dtype=torch.uint8).pin_memory()
+        hv, hf = hv_raw[:n], hf_raw[off:off + n]
+        K.ckpp_bulk_lookup(g.handle, hk, hv, hf, 7, 0)
+        torch.cuda.synchronize()
+        assert torch.equal(hv, dv.cpu()) and torch.equal(hf.bool(), dfd.cpu())
