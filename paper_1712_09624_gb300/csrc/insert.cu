@@ -77,28 +77,19 @@ __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint3
 }
 
 // --------------------------------------------------------------- phase 1
-__global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
-                                                          const uint64_t* __restrict__ vals, uint64_t n,
-                                                          uint32_t now, uint32_t expiry, uint8_t* __restrict__ status,
-                                                          Workspace ws) {
-  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t last;
-  if (!is_leader(ws, i, last)) return;
-  if (!ts.valid(i)) {
-    status[i] = kStNoTable;
-    return;
-  }
-  const TableView t = ts.of(i);
-  const uint32_t tid = ts.id(i);
-  const uint64_t v = vals[last];
-  const Key k = load_key(keys, i);
-  const Addr a = address_of(k, t.nb, t.seed);
+// Per leader. Fast path: lock the primary bucket only. With its lock held, its
+// filter is exact about this key (Sec. 4.1: a key stored in its secondary has
+// both bits set in its primary's filter, set under the primary's lock; phase 1
+// moves no entry and the batch holds each key once). If the key is in the
+// primary it is updated there; if the filter rules out the secondary and the
+// primary has a free or dead slot, the key is placed there. Everything else
+// takes the two-bucket path: both buckets locked in index order and searched.
+__device__ uint8_t phase1_two_buckets(const TableView& t, uint32_t tid, const Key& k, uint64_t v, const Addr& a,
+                                      uint32_t now, uint32_t expiry, const Workspace& ws, uint64_t i) {
   uint32_t c1, c2;
   if (!lock_pair(t, a.b1, a.b2, c1, c2)) {
-    status[i] = kStBusy;
     latch_error(t, kErrLockTimeout);
-    return;
+    return kStBusy;
   }
   Snap s1, s2;
   snap_bucket(t, a.b1, s1);
@@ -133,6 +124,55 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
     }
   }
   unlock_pair(t, a.b1, a.b2, c1, c2);
+  return st;
+}
+
+__global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
+                                                          const uint64_t* __restrict__ vals, uint64_t n,
+                                                          uint32_t now, uint32_t expiry, uint8_t* __restrict__ status,
+                                                          Workspace ws) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t last;
+  if (!is_leader(ws, i, last)) return;
+  if (!ts.valid(i)) {
+    status[i] = kStNoTable;
+    return;
+  }
+  const TableView t = ts.of(i);
+  const uint32_t tid = ts.id(i);
+  const uint64_t v = vals[last];
+  const Key k = load_key(keys, i);
+  const Addr a = address_of(k, t.nb, t.seed);
+  uint32_t c1;
+  if (!lock_bucket(t, a.b1, c1)) {
+    status[i] = kStBusy;
+    latch_error(t, kErrLockTimeout);
+    return;
+  }
+  Snap s1;
+  snap_bucket(t, a.b1, s1);
+  uint8_t st = 0;
+  bool done = false;
+  const int slot = find_key(t, a.b1, c1, s1, k, a.tag);
+  if (slot >= 0) {
+    const bool was_alive = !t.timers || alive16(snap_expiry(s1, slot), now);
+    st64_cg(record_ptr(t, a.b1, slot) + 16, v);
+    if (t.timers) set_expiry(t, a.b1, slot, expiry);
+    st = was_alive ? kStUpdated : kStInserted;
+    done = true;
+  } else if ((s1.w[2] & a.bits) != a.bits) {  // the filter rules the secondary out
+    const uint32_t f1 = free_mask(t, c1, s1, now);
+    if (f1) {
+      const uint32_t sl = __ffs(f1) - 1;
+      if ((c1 >> sl) & 1u) evict_entry(t, tid, a.b1, sl, c1, ws);
+      place_entry(t, a.b1, sl, k, v, a, expiry, c1);
+      st = kStInserted;
+      done = true;
+    }
+  }
+  unlock_bucket(t, a.b1, c1);
+  if (!done) st = phase1_two_buckets(t, tid, k, v, a, now, expiry, ws, i);
   if (st) status[i] = st;
 }
 

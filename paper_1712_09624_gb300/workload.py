@@ -3,7 +3,7 @@
 This module only draws inputs; it holds none of the table's arithmetic, so the
 CUDA path and the CPU oracle can both be fed from it.
 
-Random numbers come from the Philox4x32-10 counter-based generator (Salmon et
+Random numbers come from the Philox4x64-10 counter-based generator (Salmon et
 al., SC'11) through numpy's ``Philox`` bit generator, whose raw 64-bit output
 stream for a given 128-bit key is fixed by that algorithm. Every draw uses a
 distinct key ``(seed, stream)``, so each quantity is reproducible on its own.
@@ -33,7 +33,7 @@ STREAM_MISC = 6
 
 
 def raw64(seed: int, stream: int, n: int) -> np.ndarray:
-    """The first n raw 64-bit outputs of Philox4x32-10 keyed by (seed, stream)."""
+    """The first n raw 64-bit outputs of Philox4x64-10 keyed by (seed, stream)."""
     bg = np.random.Philox(key=np.array([seed & (2**64 - 1), stream & (2**64 - 1)], dtype=np.uint64))
     return np.asarray(bg.random_raw(n), dtype=np.uint64)
 

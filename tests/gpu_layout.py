@@ -121,3 +121,70 @@ def oracle_live(t: "oracle.Table", now: int) -> dict:
         if (not t.timers) or ((e - now) & 0xFFFF) < 1024:
             out[d["key"][i].tobytes()] = (int(d["value"][i]), e if t.timers else 0)
     return out
+
+
+def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int) -> tuple[int, int, int]:
+    """(keys, secondary-bucket reads, record reads) that a lookup of ``keys``
+    with strategy ``variant`` (0 Bloom, 1 optimistic, 2 pessimistic) makes on
+    the decoded table: candidates are busy slots whose tag matches, confirmed in
+    slot order until the key is met (Sec. 2); the secondary is read after a
+    primary miss when both filter bits are set (Bloom, Sec. 4.1), after every
+    primary miss (optimistic) or always (pessimistic, Sec. 3)."""
+    a = oracle.address(keys, d.nb, d.seed)
+    kv = np.ascontiguousarray(keys).view(np.dtype((np.void, 16))).reshape(-1)
+    rk = np.ascontiguousarray(d.rec_key).view(np.dtype((np.void, 16))).reshape(-1)
+    slots = np.arange(SLOTS)
+
+    def bucket_reads(b):
+        cand = (d.tags[b] == a["tag"][:, None]) & d.busy[b]
+        hit = cand & (rk[(b[:, None] * SLOTS + slots).reshape(-1)].reshape(-1, SLOTS) == kv[:, None])
+        found = hit.any(axis=1)
+        first = np.where(found, hit.argmax(axis=1), SLOTS)
+        upto = cand & (slots[None, :] <= first[:, None])
+        return found, upto.sum(axis=1)
+
+    f1, r1 = bucket_reads(a["b1"].astype(np.int64))
+    _, r2 = bucket_reads(a["b2"].astype(np.int64))
+    bits = (np.uint64(1) << a["bit1"].astype(np.uint64)) | (np.uint64(1) << a["bit2"].astype(np.uint64))
+    if variant == 0:
+        read2 = ~f1 & ((d.bloom[a["b1"]] & bits) == bits)
+        sec = int(read2.sum())
+    elif variant == 1:
+        read2 = ~f1
+        sec = int(read2.sum())
+    else:
+        read2 = ~f1
+        sec = keys.shape[0]
+    rec = int(r1.sum() + r2[read2].sum())
+    return keys.shape[0], sec, rec
+
+
+def encode_oracle(t: "oracle.Table") -> np.ndarray:
+    """The oracle table's entries written out in the GPU byte layout (header,
+    bucket array, record array), so the decoder and the helpers above can be
+    checked on the CPU against the oracle's own answers."""
+    nb, timers = t.n_buckets, t.timers
+    bb = 64 if timers else 32
+    buf = np.zeros(HEADER + nb * bb + nb * SLOTS * 32, np.uint8)
+    buf[0:4] = np.frombuffer(np.uint32(0x50504B43).tobytes(), np.uint8)
+    d = t.dump()
+    bloom, moved = t.meta()
+    bk = buf[HEADER:HEADER + nb * bb].reshape(nb, bb)
+    bk[:, 16:24] = bloom.view(np.uint8).reshape(nb, 8)
+    bk[:, 28:32] = moved.view(np.uint8).reshape(nb, 4)
+    ctrl = np.zeros(nb, np.uint32)
+    rec = buf[HEADER + nb * bb:].reshape(nb * SLOTS, 32)
+    a = oracle.address(d["key"], nb, t.seed)
+    for i in range(d["value"].shape[0]):
+        b, s = int(d["bucket"][i]), int(d["slot"][i])
+        ctrl[b] |= np.uint32(1 << s) | np.uint32(int(d["in_secondary"][i]) << (8 + s))
+        bk[b, 2 * s:2 * s + 2] = np.frombuffer(np.uint16(a["tag"][i]).tobytes(), np.uint8)
+        r = b * SLOTS + s
+        rec[r, 0:16] = d["key"][i]
+        rec[r, 16:24] = np.frombuffer(np.uint64(d["value"][i]).tobytes(), np.uint8)
+        if timers:
+            e = np.uint16(d["expiry"][i]).tobytes()
+            bk[b, 32 + 2 * s:34 + 2 * s] = np.frombuffer(e, np.uint8)
+            rec[r, 24:26] = np.frombuffer(e, np.uint8)
+    bk[:, 24:28] = ctrl.view(np.uint8).reshape(nb, 4)
+    return buf
