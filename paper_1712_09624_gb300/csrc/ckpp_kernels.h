@@ -11,13 +11,14 @@ namespace ckpp {
 // Device scratch for one insert or delete batch (carved out of the caller's
 // workspace buffer, see workspace_layout in api.cu).
 struct Workspace {
-  uint32_t* counters;   // [0] pending count, [1] fixup count, [2] fixup overflow flag, [3] retry count,
-                        // [4] count of the last displacement pass (its list reuses `pending`)
+  uint32_t* counters;   // [0] pending count, [1] fixup count, [2] fixup overflow flag; list counts of the
+                        // displacement passes: [3] after move1 (in `retry`), [5] after the grid search
+                        // (in `pending`), [6] after the block search (in `retry`)
   uint32_t* set_first;  // [m] open-addressing set of batch keys: lowest batch index of the key
   uint32_t* set_last;   // [m] highest batch index of the key
   uint32_t* slot_of;    // [n] set position of each batch key
   uint32_t* pending;    // [n] leaders left for the displacement pass
-  uint32_t* retry;      // [n] leaders the first displacement pass could not place
+  uint32_t* retry;      // [n] leaders a displacement pass passes on to the next
   unsigned long long* fixup;  // [fix_cap] (table << 32 | bucket) whose moved counter fell to 0 off-lock
   uint32_t m_mask;      // m - 1 (m a power of two >= 2n)
   uint32_t fix_cap;

@@ -10,13 +10,19 @@
 //             stored (alive or dead), else take the lowest free or dead slot of
 //             the primary, else of the secondary; leaders with two full buckets
 //             are queued for phase 2.
-//   phase2  - per queued leader: breadth-first search for a cuckoo path without
-//             locks (queue in shared memory), then lock every bucket of the path
-//             plus the key's primary, re-validate the path, and move the entries
-//             backwards and store the key, all under those locks; retry a
-//             bounded number of times. Keys still unplaced get a second pass by
-//             a single block, then a last pass by a single thread (no
-//             contention); only then FULL.
+//   move1   - per queued leader: the cuckoo paths of length one. Read the
+//             entries of b1, then of b2, and the buckets they can move to; the
+//             first entry whose other bucket has a free or dead slot moves
+//             there under the locks of the path, and the key takes its slot.
+//             No shared memory, so the pass runs at full occupancy; at load
+//             factor 0.9 it places nearly every queued key.
+//   phase2  - per key move1 left: breadth-first search for a longer cuckoo
+//             path without locks (queue in shared memory), then lock every
+//             bucket of the path plus the key's primary, re-validate the path,
+//             and move the entries backwards and store the key, all under
+//             those locks; retry a bounded number of times. Keys still
+//             unplaced get a wider search by 8 single-warp blocks, then the
+//             widest by 16 single-thread blocks; only then FULL.
 //   fixup   - reset the filter of buckets whose moved counter reached zero off
 //             their lock (the reset of Sec. 4.1, deferred so that it never races
 //             a concurrent setter).
@@ -177,16 +183,25 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
 }
 
 // --------------------------------------------------------------- phase 2
-// Search budgets of the three displacement passes (queue in shared memory,
-// at most 48 KB per block): the contended first pass searches 96 buckets up
-// to 4 moves deep per thread; the single-block second pass 192 buckets, 5
-// moves; the single-thread last pass 2048 buckets, 6 moves (the sequential
-// CPU reference searches 1024 buckets, 5 moves). The later passes take on at
+// Search budgets of the displacement passes after move1 (queue in shared
+// memory, at most 48 KB per block): the grid pass searches 96 buckets up to 4
+// moves deep per thread; the second pass (8 blocks of one warp) 192 buckets, 5
+// moves; the last pass (16 blocks of one thread) 2048 buckets, 6 moves (the
+// sequential CPU reference searches 1024 buckets, 5 moves). Each later pass
+// runs far fewer searches at once, so paths rarely collide, and takes on at
 // most kSecondPassKeys / kLastPassKeys keys: more failures than that mean the
 // table is full, not contended, and the rest are FULL without a search.
+//
+// Within one insert call no bucket gains a free or dead slot: phase 1 fills
+// them, a path ends by filling one, every move along it vacates a slot that
+// the next move (or the key) refills, and `now` is fixed. A key queued by
+// phase 1 found both its buckets without a free or dead slot, so the passes
+// search from them without re-checking the roots.
 constexpr int kP2Threads = 64;
-constexpr uint32_t kSecondPassKeys = 4096;  // keys the single-block pass takes on
-constexpr uint32_t kLastPassKeys = 128;     // keys the single-thread pass takes on
+constexpr uint32_t kSecondPassKeys = 4096;  // keys the second pass takes on
+constexpr uint32_t kLastPassKeys = 128;     // keys the last pass takes on
+constexpr unsigned kSecondPassBlocks = 8;
+constexpr unsigned kLastPassBlocks = 16;
 constexpr int kMaxDepth = 6;
 constexpr int kPathBuckets = kMaxDepth + 1;
 constexpr int kMaxLocks = kPathBuckets + 1;   // the path plus the key's primary
@@ -198,52 +213,75 @@ struct Node {
   uint8_t depth;
 };
 
-// Place k into the lowest free or dead slot of its primary, else secondary.
-// 1 placed, 0 no room, -1 lock timeout.
-__device__ int try_place(const TableView& t, uint32_t tid, const Key& k, uint64_t v, const Addr& a, uint32_t now,
-                         uint32_t expiry, const Workspace& ws) {
-  uint32_t c1, c2;
-  if (!lock_pair(t, a.b1, a.b2, c1, c2)) return -1;
-  Snap s1, s2;
-  snap_bucket(t, a.b1, s1);
-  snap_bucket(t, a.b2, s2);
-  const uint32_t f1 = free_mask(t, c1, s1, now);
-  const uint32_t f2 = f1 ? 0u : free_mask(t, c2, s2, now);
-  int placed = 0;
-  if (f1 || f2) {
-    const uint32_t b = f1 ? a.b1 : a.b2;
-    uint32_t& cb = f1 ? c1 : c2;
-    const uint32_t slot = __ffs(f1 ? f1 : f2) - 1;
-    if ((cb >> slot) & 1u) evict_entry(t, tid, b, slot, cb, ws);
-    place_entry(t, b, slot, k, v, a, expiry, cb);
-    placed = 1;
-  }
-  unlock_pair(t, a.b1, a.b2, c1, c2);
-  return placed;
-}
+// One thread's search queue inside a block's shared array stored node-major
+// (node j of every thread side by side), so that the threads of a warp touch
+// consecutive words and never the same bank.
+struct Queue {
+  Node* base;
+  int stride;
+  __device__ __forceinline__ Node& operator[](int i) const { return base[i * stride]; }
+};
 
 // Breadth-first search over buckets from b1 and b2 (lock-free reads; the path
 // is re-validated under its locks). Expanding a bucket issues the key reads of
 // its 8 slots together, then the control-word (and expiry) reads of the 8
 // buckets those entries can move to, so one level of the search costs two
 // memory round trips; a child with a free or dead slot ends the search (the
-// first such child in queue order, i.e. a shortest path). Returns the node
-// index of the bucket with the hole (in hole), or -1.
+// first such child in queue order, i.e. a shortest path). A bucket enters the
+// queue once: small searches test the queue itself, large ones an
+// open-addressing set of 2 x kBfsNodes bucket numbers (`seen`, shared memory).
+// Returns the node index of the bucket with the hole (in hole), or -1.
+template <int kBfsNodes>
+struct SeenSet {
+  static constexpr bool kHashed = kBfsNodes >= 512;
+  static constexpr uint32_t kSize = kHashed ? 2 * kBfsNodes : 1;
+  static_assert(!kHashed || (kSize & (kSize - 1)) == 0, "set size must be a power of two");
+};
+
+// Per-thread storage of the set, in shared memory; none for small searches.
+template <bool kHashed, int kThreadsPerBlock, uint32_t kSize>
+struct SeenStorage {
+  __device__ static uint32_t* get() {
+    __shared__ uint32_t sets[kThreadsPerBlock][kSize];
+    return sets[threadIdx.x];
+  }
+};
+template <int kThreadsPerBlock, uint32_t kSize>
+struct SeenStorage<false, kThreadsPerBlock, kSize> {
+  __device__ static uint32_t* get() { return nullptr; }
+};
+
+// Adds bucket b to the set; false if it was there already.
+template <int kBfsNodes>
+__device__ __forceinline__ bool seen_insert(uint32_t* seen, uint32_t b) {
+  constexpr uint32_t mask = SeenSet<kBfsNodes>::kSize - 1;
+  uint32_t h = (b * 0x9E3779B1u) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    if (seen[h] == b) return false;
+    if (seen[h] == 0xFFFFFFFFu) {
+      seen[h] = b;
+      return true;
+    }
+    h = (h + 1) & mask;
+  }
+  return false;  // not reached: the set holds at most kBfsNodes of its 2 x kBfsNodes entries
+}
+
 template <int kBfsNodes, int kBfsDepth>
-__device__ int bfs(const TableView& t, const Addr& a, uint32_t now, Node* q, uint32_t& hole) {
+__device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue& q, uint32_t* seen,
+                    uint32_t& hole) {
+  constexpr bool kHashed = SeenSet<kBfsNodes>::kHashed;
   int nq = 0;
   q[nq++] = Node{a.b1, -1, 0, 0};
   q[nq++] = Node{a.b2, -1, 0, 0};
-  for (int r = 0; r < 2; ++r) {  // the roots themselves (a slot may have freed up)
-    Snap s;
-    snap_bucket(t, q[r].bucket, s);
-    const uint32_t f = free_mask(t, (uint32_t)s.w[3], s, now);
-    if (f) {
-      hole = __ffs(f) - 1;
-      return r;
-    }
+  if (kHashed) {
+    for (uint32_t j = 0; j < SeenSet<kBfsNodes>::kSize; ++j) seen[j] = 0xFFFFFFFFu;
+    seen_insert<kBfsNodes>(seen, a.b1);
+    seen_insert<kBfsNodes>(seen, a.b2);
   }
-  for (int qi = 0; qi < nq; ++qi) {
+  // A hole is only ever found on a newly queued bucket, so the search ends
+  // when the queue is full.
+  for (int qi = 0; qi < nq && nq < kBfsNodes; ++qi) {
     const Node cur = q[qi];
     if (cur.depth >= kBfsDepth) continue;
     uint64_t k0[kSlots], k1[kSlots];
@@ -266,9 +304,14 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, Node* q, uin
       }
     }
     for (uint32_t sl = 0; sl < kSlots && nq < kBfsNodes; ++sl) {
-      bool seen = false;
-      for (int j = 0; j < nq; ++j) seen |= (q[j].bucket == y[sl]);
-      if (seen) continue;
+      bool fresh;
+      if (kHashed) {
+        fresh = seen_insert<kBfsNodes>(seen, y[sl]);
+      } else {
+        fresh = true;
+        for (int j = 0; j < nq; ++j) fresh &= (q[j].bucket != y[sl]);
+      }
+      if (!fresh) continue;
       q[nq] = Node{y[sl], (int16_t)qi, (uint8_t)sl, (uint8_t)(cur.depth + 1)};
       Snap s;
       s.e0 = e0[sl];
@@ -375,6 +418,75 @@ __device__ int execute_path(const TableView& t, uint32_t tid, const uint32_t (&p
   return rc;
 }
 
+// One-move pass over `list` (count in *count_ptr): for each key, the entries
+// of b1 and then of b2 are read with the buckets they can move to (two memory
+// round trips per root); the first entry whose other bucket has a free or dead
+// slot gives a cuckoo path of length one, executed under locks. Keys without
+// one, or whose path went stale, are appended to `next`.
+__global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint8_t* __restrict__ keys,
+                                                         const uint64_t* __restrict__ vals, uint32_t now,
+                                                         uint32_t expiry, uint8_t* __restrict__ status, Workspace ws,
+                                                         const uint32_t* list, const uint32_t* count_ptr,
+                                                         uint32_t* next, uint32_t* next_count) {
+  const uint32_t count = ld32_cg(count_ptr);
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+    const uint32_t i = list[j];
+    const TableView t = ts.of(i);
+    const Key k = load_key(keys, i);
+    const Addr a = address_of(k, t.nb, t.seed);
+    uint32_t path[kPathBuckets], slot[kPathBuckets], hole = 0;
+    bool found = false;
+    for (int r = 0; r < 2 && !found; ++r) {
+      const uint32_t x = r ? a.b2 : a.b1;
+      uint32_t y[kSlots];
+#pragma unroll
+      for (uint32_t sl = 0; sl < kSlots; ++sl) {
+        uint64_t k0, k1;
+        ld128_cg(record_ptr(t, x, sl), k0, k1);
+        const Addr e = address_of(Key{k0, k1}, t.nb, t.seed);
+        y[sl] = (e.b1 == x) ? e.b2 : e.b1;
+      }
+      uint32_t cy[kSlots];
+      uint64_t e0[kSlots], e1[kSlots];
+#pragma unroll
+      for (uint32_t sl = 0; sl < kSlots; ++sl) {
+        cy[sl] = ld32_cg(ctrl_ptr(t, y[sl]));
+        if (t.timers) {
+          ld128_cg(expiry_ptr(t, y[sl], 0), e0[sl], e1[sl]);
+        } else {
+          e0[sl] = e1[sl] = 0;
+        }
+      }
+#pragma unroll
+      for (uint32_t sl = 0; sl < kSlots; ++sl) {
+        if (found || y[sl] == a.b1 || y[sl] == a.b2) continue;  // the roots have no room
+        Snap s;
+        s.e0 = e0[sl];
+        s.e1 = e1[sl];
+        const uint32_t f = free_mask(t, cy[sl], s, now);
+        if (f) {
+          path[0] = x;
+          path[1] = y[sl];
+          slot[0] = sl;
+          hole = __ffs(f) - 1;
+          found = true;
+        }
+      }
+    }
+    int rc = 0;
+    if (found) {
+      const uint64_t v = vals[ws.set_last[ws.slot_of[i]]];
+      rc = execute_path(t, ts.id(i), path, slot, 1, hole, k, v, a, now, expiry, ws);
+    }
+    if (rc == 0) {
+      next[atomicAdd(next_count, 1u)] = i;
+    } else {
+      if (rc < 0) latch_error(t, kErrLockTimeout);
+      status[i] = rc > 0 ? kStInserted : kStBusy;
+    }
+  }
+}
+
 // Displacement pass over `list` (count in *count). Keys that find no path
 // are appended to `retry` (when given) for a second, low-contention pass;
 // otherwise they are FULL.
@@ -385,10 +497,14 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
                                                                   Workspace ws, const uint32_t* list,
                                                                   const uint32_t* count_ptr, uint32_t* retry,
                                                                   uint32_t* retry_count, uint32_t max_keys) {
-  static_assert(kThreadsPerBlock * kBfsNodes * sizeof(Node) <= 48 * 1024, "BFS queues exceed 48 KB");
+  constexpr bool kHashed = SeenSet<kBfsNodes>::kHashed;
+  static_assert(kThreadsPerBlock * (kBfsNodes * sizeof(Node) + (kHashed ? SeenSet<kBfsNodes>::kSize * 4 : 0)) <=
+                    48 * 1024,
+                "BFS state exceeds 48 KB");
   static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
-  __shared__ Node queues[kThreadsPerBlock][kBfsNodes];
-  Node* q = queues[threadIdx.x];
+  __shared__ Node queues[kBfsNodes][kThreadsPerBlock];
+  const Queue q{&queues[0][threadIdx.x], kThreadsPerBlock};
+  uint32_t* seen = SeenStorage<kHashed, kThreadsPerBlock, SeenSet<kBfsNodes>::kSize>::get();
   const uint32_t listed = ld32_cg(count_ptr);
   const uint32_t count = min(listed, max_keys);
   // A later pass searches wider but alone; when many keys reach it the table
@@ -404,13 +520,8 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
     const Addr a = address_of(k, t.nb, t.seed);
     uint8_t st = kStFull;
     for (int attempt = 0; attempt < kPathAttempts; ++attempt) {
-      const int placed = try_place(t, tid, k, v, a, now, expiry, ws);
-      if (placed != 0) {
-        st = placed > 0 ? kStInserted : kStBusy;
-        break;
-      }
       uint32_t hole = 0;
-      const int end = bfs<kBfsNodes, kBfsDepth>(t, a, now, q, hole);
+      const int end = bfs<kBfsNodes, kBfsDepth>(t, a, now, q, seen, hole);
       if (end < 0) break;  // no cuckoo path within the search bound: FULL
       uint32_t path[kPathBuckets], slot[kPathBuckets];
       const int len = q[end].depth;
@@ -521,19 +632,24 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
   if (e != cudaSuccess) return e;
   insert_phase1<<<grid_for(n, kThreads), kThreads, 0, s>>>(ts, keys, vals, n, now, expiry, status, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const unsigned p2_blocks = (unsigned)std::min<uint64_t>(grid_for(n, kP2Threads), 152 * 4);
-  insert_phase2<kP2Threads, 96, 4><<<p2_blocks, kP2Threads, 0, s>>>(ts, keys, vals, now, expiry, status, ws,
-                                                                    ws.pending, ws.counters + 0, ws.retry,
-                                                                    ws.counters + 3, 0xFFFFFFFFu);
+  // lists: phase 1 -> pending [0] -> move1 -> retry [3] -> grid search ->
+  // pending [5] -> block search -> retry [6] -> last search
+  insert_move1<<<152 * 8, kThreads, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 0,
+                                            ws.retry, ws.counters + 3);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // second pass, one block: the keys the contended pass could not place
-  insert_phase2<32, 192, 5><<<1, 32, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 3,
-                                             ws.pending, ws.counters + 4, kSecondPassKeys);
+  insert_phase2<kP2Threads, 96, 4><<<152 * 4, kP2Threads, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.retry,
+                                                                  ws.counters + 3, ws.pending, ws.counters + 5,
+                                                                  0xFFFFFFFFu);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // last pass, one thread: no contention left and the widest search; a key
-  // is FULL only if it finds no path
-  insert_phase2<1, 2048, 6><<<1, 1, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 4,
-                                            nullptr, nullptr, kLastPassKeys);
+  // second pass, 8 single-warp blocks: the keys the grid pass could not place
+  insert_phase2<32, 192, 5><<<kSecondPassBlocks, 32, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.pending,
+                                                             ws.counters + 5, ws.retry, ws.counters + 6,
+                                                             kSecondPassKeys);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // last pass, 16 single-thread blocks: the widest search, a few searches at
+  // a time; a key is FULL only if it finds no path
+  insert_phase2<1, 2048, 6><<<kLastPassBlocks, 1, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.retry,
+                                                          ws.counters + 6, nullptr, nullptr, kLastPassKeys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bloom_fixup<<<152 * 2, 256, 0, s>>>(ts, ws);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
