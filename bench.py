@@ -65,12 +65,13 @@ def parse():
     p.add_argument("--no-side", action="store_true", help="skip pos/neg/e2e/mutation side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle timing budget")
     p.add_argument("--workload", default="scale",
-                   choices=["scale", "batched", "sweep", "random-read", "served", "mixed"],
+                   choices=["scale", "batched", "sweep", "random-read", "served", "mixed", "insert"],
                    help="scale: the headline at-scale lookup (default); batched: many tables in one launch vs "
                         "one launch per table; sweep: load factor x negative rate x lookup strategy grid; "
                         "random-read: the GPU's random 32/64-byte read ceiling; served: continuous-batching "
                         "request loop vs one launch per burst; mixed: insert/lookup/delete/expire mix on a "
-                        "200M-slot table with timers")
+                        "200M-slot table with timers; insert: bulk insert rate as a table fills from LF 0.85 "
+                        "to 0.99")
     p.add_argument("--mixed-batches", type=int, default=400, help="mixed: batches (time units) to run")
     p.add_argument("--serve-seconds", type=float, default=0.2, help="served: seconds of offered traffic")
     p.add_argument("--serve-modes", default="batched,plain", help="served: arms to run")
@@ -807,11 +808,77 @@ def run_mixed(args):
             "device_errors": t.sync_status()}
 
 
+def run_insert_load(args):
+    """Bulk insert rate as the table fills: a 2^24-bucket table (134M slots,
+    no timers) is filled to LF 0.85 untimed, then batches of 2^20 new keys are
+    inserted until LF 0.99, each timed with CUDA events. Per batch: the load
+    factor before it, the time, the statuses, and how many keys each
+    displacement pass was left with (the workspace's diagnostic words)."""
+    import torch
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    from paper_1712_09624_gb300.table import FlowTable
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    nb = 1 << 24
+    slots = nb * 8
+    batch = 1 << 20
+    t = FlowTable(nb, seed=args.seed, device=dev)
+    ws = torch.empty(K.ckpp_workspace_bytes(1 << 22), dtype=torch.uint8, device=dev)
+    done = 0
+    warm = int(0.85 * slots)
+    while done < warm:
+        c = min(1 << 22, warm - done)
+        k, v = WG.fill_keys(args.seed, done, c, dev)
+        st = torch.empty(c, dtype=torch.uint8, device=dev)
+        K.ckpp_bulk_insert(t.handle, k, v, st, ws, 0, 0, stream)
+        done += c
+    torch.cuda.synchronize()
+    stored = warm
+    rows = []
+    st = torch.empty(batch, dtype=torch.uint8, device=dev)
+    while stored < 0.99 * slots:
+        k, v = WG.fill_keys(args.seed, done, batch, dev)
+        done += batch
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        K.ckpp_bulk_insert(t.handle, k, v, st, ws, 0, 0, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        diag = ws[:32].cpu().numpy().view(np.uint32)
+        counts = np.bincount(st.cpu().numpy(), minlength=8)
+        inserted = int(counts[K.ST_INSERTED])
+        rows.append({"lf_before": round(stored / slots, 4), "ms": round(ms, 4),
+                     "mkeys_per_s": round(batch / ms / 1e3, 1), "inserted": inserted,
+                     "full": int(counts[K.ST_FULL]), "queued_by_phase1": int(diag[0]),
+                     "left_after_one_move": int(diag[3]), "left_after_grid_search": int(diag[5]),
+                     "left_after_second_pass": int(diag[6])})
+        stored += inserted
+    if t.sync_status() != 0:
+        raise RuntimeError("a device wait gave up during the insert run")
+
+    def rate(lo, hi):
+        sel = [r for r in rows if lo <= r["lf_before"] < hi]
+        return round(sum(batch for _ in sel) / max(1e-9, sum(r["ms"] for r in sel)) / 1e3, 1) if sel else None
+
+    bands = {"0.85-0.90": rate(0.85, 0.90), "0.90-0.95": rate(0.90, 0.95), "0.95-0.99": rate(0.95, 0.99)}
+    return {"metric": "bulk insert keys per second by load factor (GPU time)", "value": bands["0.85-0.90"],
+            "unit": "Mkeys/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "bulk insert of 2^20-key batches of new keys into a 2^24-bucket x 8 table "
+                                   "from LF 0.85 to 0.99, no timers", "n_buckets": nb, "batch": batch},
+            "bands_mkeys_per_s": bands, "rows": rows}
+
+
 def main():
     args = parse()
     if args.workload != "scale" and args.impl == "ours":
         run = {"batched": run_batched, "sweep": run_sweep, "random-read": run_random_read,
-               "served": run_served, "mixed": run_mixed}[args.workload]
+               "served": run_served, "mixed": run_mixed, "insert": run_insert_load}[args.workload]
         print(json.dumps(run(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -107,7 +107,12 @@ typedef struct ckpp_stats {
 size_t ckpp_required_bytes(const ckpp_geometry* geometry);
 
 /* Device workspace bytes an insert or delete batch of n keys needs (scratch for
- * resolving in-batch duplicate keys and for the displacement pass). */
+ * resolving in-batch duplicate keys and for the displacement passes). Once an
+ * insert call has completed on its stream, the first 32 bytes of its workspace
+ * hold diagnostics as uint32 words: [0] keys that found no free or dead slot in
+ * either bucket, [3] of those, keys the one-move pass left, [5] keys the grid
+ * search left, [6] keys the second search pass left (the last pass reports the
+ * ones it cannot place FULL). The other words are scratch. */
 size_t ckpp_workspace_bytes(uint64_t n);
 
 /* Create a table in the caller's device buffer dev_buf (at least
