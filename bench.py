@@ -810,10 +810,11 @@ def run_mixed(args):
 
 def run_insert_load(args):
     """Bulk insert rate as the table fills: a 2^24-bucket table (134M slots,
-    no timers) is filled to LF 0.85 untimed, then batches of 2^20 new keys are
-    inserted until LF 0.99, each timed with CUDA events. Per batch: the load
-    factor before it, the time, the statuses, and how many keys each
-    displacement pass was left with (the workspace's diagnostic words)."""
+    no timers; --log2-buckets changes it) is filled to LF 0.85 untimed, then
+    batches of 2^20 new keys are inserted until LF 0.99, each timed with CUDA
+    events. Per batch: the load factor before it, the time, the statuses, and
+    how many keys each displacement pass was left with (the workspace's
+    diagnostic words)."""
     import torch
 
     from paper_1712_09624_gb300 import _ckpp as K
@@ -823,7 +824,7 @@ def run_insert_load(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    nb = 1 << 24
+    nb = 1 << args.log2_buckets
     slots = nb * 8
     batch = 1 << 20
     t = FlowTable(nb, seed=args.seed, device=dev)
@@ -869,8 +870,9 @@ def run_insert_load(args):
     bands = {"0.85-0.90": rate(0.85, 0.90), "0.90-0.95": rate(0.90, 0.95), "0.95-0.99": rate(0.95, 0.99)}
     return {"metric": "bulk insert keys per second by load factor (GPU time)", "value": bands["0.85-0.90"],
             "unit": "Mkeys/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": "bulk insert of 2^20-key batches of new keys into a 2^24-bucket x 8 table "
-                                   "from LF 0.85 to 0.99, no timers", "n_buckets": nb, "batch": batch},
+            "config": {"workload": f"bulk insert of 2^20-key batches of new keys into a 2^{args.log2_buckets}"
+                                   "-bucket x 8 table from LF 0.85 to 0.99, no timers", "n_buckets": nb,
+                                   "batch": batch},
             "bands_mkeys_per_s": bands, "rows": rows}
 
 

@@ -83,25 +83,23 @@ __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint3
 }
 
 // --------------------------------------------------------------- phase 1
-// Per leader. Fast path: lock the primary bucket only. With its lock held, its
-// filter is exact about this key (Sec. 4.1: a key stored in its secondary has
-// both bits set in its primary's filter, set under the primary's lock; phase 1
-// moves no entry and the batch holds each key once). If the key is in the
-// primary it is updated there; if the filter rules out the secondary and the
-// primary has a free or dead slot, the key is placed there. Everything else
-// takes the two-bucket path: both buckets locked in index order and searched.
-__device__ uint8_t phase1_two_buckets(const TableView& t, uint32_t tid, const Key& k, uint64_t v, const Addr& a,
-                                      uint32_t now, uint32_t expiry, const Workspace& ws, uint64_t i) {
-  uint32_t c1, c2;
-  if (!lock_pair(t, a.b1, a.b2, c1, c2)) {
-    latch_error(t, kErrLockTimeout);
-    return kStBusy;
-  }
-  Snap s1, s2;
-  snap_bucket(t, a.b1, s1);
-  snap_bucket(t, a.b2, s2);
-  uint8_t st = 0;
-  // Upsert: a stored copy of the key (alive or dead) is updated in place.
+// Per leader. Lock the primary bucket first. With its lock held, its filter is
+// exact about this key (Sec. 4.1: a key stored in its secondary has both bits
+// set in its primary's filter, set under the primary's lock; phase 1 moves no
+// entry and the batch holds each key once). If the key is in the primary it is
+// updated there; if the filter rules out the secondary and the primary has a
+// free or dead slot, the key is placed there. Otherwise the secondary is
+// locked too -- directly when its index is higher (locks are taken in index
+// order), else by a single non-waiting attempt, and failing that both are
+// released and taken again in order -- and both buckets are searched.
+
+// Both buckets locked (c1/s1, c2/s2 their ctrl words and snapshots): update
+// the key where it is stored, else place it in the lowest free or dead slot of
+// the primary, else of the secondary, else queue it for the displacement
+// passes. Returns the status, or 0 if queued.
+__device__ uint8_t phase1_both(const TableView& t, uint32_t tid, const Key& k, uint64_t v, const Addr& a,
+                               uint32_t now, uint32_t expiry, const Workspace& ws, uint64_t i, uint32_t& c1,
+                               const Snap& s1, uint32_t& c2, const Snap& s2) {
   uint32_t b = a.b1;
   const Snap* sb = &s1;
   int slot = find_key(t, a.b1, c1, s1, k, a.tag);
@@ -114,23 +112,20 @@ __device__ uint8_t phase1_two_buckets(const TableView& t, uint32_t tid, const Ke
     const bool was_alive = !t.timers || alive16(snap_expiry(*sb, slot), now);
     st64_cg(record_ptr(t, b, slot) + 16, v);
     if (t.timers) set_expiry(t, b, slot, expiry);
-    st = was_alive ? kStUpdated : kStInserted;
-  } else {
-    const uint32_t f1 = free_mask(t, c1, s1, now);
-    const uint32_t f2 = f1 ? 0u : free_mask(t, c2, s2, now);
-    if (f1 || f2) {
-      b = f1 ? a.b1 : a.b2;
-      uint32_t& cb = f1 ? c1 : c2;
-      slot = __ffs(f1 ? f1 : f2) - 1;
-      if ((cb >> slot) & 1u) evict_entry(t, tid, b, slot, cb, ws);
-      place_entry(t, b, slot, k, v, a, expiry, cb);
-      st = kStInserted;
-    } else {
-      ws.pending[atomicAdd(ws.counters + 0, 1u)] = (uint32_t)i;
-    }
+    return was_alive ? kStUpdated : kStInserted;
   }
-  unlock_pair(t, a.b1, a.b2, c1, c2);
-  return st;
+  const uint32_t f1 = free_mask(t, c1, s1, now);
+  const uint32_t f2 = f1 ? 0u : free_mask(t, c2, s2, now);
+  if (f1 || f2) {
+    b = f1 ? a.b1 : a.b2;
+    uint32_t& cb = f1 ? c1 : c2;
+    slot = __ffs(f1 ? f1 : f2) - 1;
+    if ((cb >> slot) & 1u) evict_entry(t, tid, b, slot, cb, ws);
+    place_entry(t, b, slot, k, v, a, expiry, cb);
+    return kStInserted;
+  }
+  ws.pending[atomicAdd(ws.counters + 0, 1u)] = (uint32_t)i;
+  return 0;
 }
 
 __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
@@ -150,35 +145,55 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
   const uint64_t v = vals[last];
   const Key k = load_key(keys, i);
   const Addr a = address_of(k, t.nb, t.seed);
-  uint32_t c1;
+  uint32_t c1, c2;
   if (!lock_bucket(t, a.b1, c1)) {
     status[i] = kStBusy;
     latch_error(t, kErrLockTimeout);
     return;
   }
-  Snap s1;
+  Snap s1, s2;
   snap_bucket(t, a.b1, s1);
-  uint8_t st = 0;
-  bool done = false;
   const int slot = find_key(t, a.b1, c1, s1, k, a.tag);
   if (slot >= 0) {
     const bool was_alive = !t.timers || alive16(snap_expiry(s1, slot), now);
     st64_cg(record_ptr(t, a.b1, slot) + 16, v);
     if (t.timers) set_expiry(t, a.b1, slot, expiry);
-    st = was_alive ? kStUpdated : kStInserted;
-    done = true;
-  } else if ((s1.w[2] & a.bits) != a.bits) {  // the filter rules the secondary out
+    unlock_bucket(t, a.b1, c1);
+    status[i] = was_alive ? kStUpdated : kStInserted;
+    return;
+  }
+  if ((s1.w[2] & a.bits) != a.bits) {  // the filter rules the secondary out
     const uint32_t f1 = free_mask(t, c1, s1, now);
     if (f1) {
       const uint32_t sl = __ffs(f1) - 1;
       if ((c1 >> sl) & 1u) evict_entry(t, tid, a.b1, sl, c1, ws);
       place_entry(t, a.b1, sl, k, v, a, expiry, c1);
-      st = kStInserted;
-      done = true;
+      unlock_bucket(t, a.b1, c1);
+      status[i] = kStInserted;
+      return;
     }
   }
-  unlock_bucket(t, a.b1, c1);
-  if (!done) st = phase1_two_buckets(t, tid, k, v, a, now, expiry, ws, i);
+  // The secondary is needed as well.
+  bool held;
+  if (a.b2 > a.b1) {
+    held = lock_bucket(t, a.b2, c2);
+    if (!held) unlock_bucket(t, a.b1, c1);
+  } else {
+    held = try_lock_bucket(t, a.b2, c2);
+    if (!held) {
+      unlock_bucket(t, a.b1, c1);
+      held = lock_pair(t, a.b1, a.b2, c1, c2);
+      if (held) snap_bucket(t, a.b1, s1);
+    }
+  }
+  if (!held) {
+    status[i] = kStBusy;
+    latch_error(t, kErrLockTimeout);
+    return;
+  }
+  snap_bucket(t, a.b2, s2);
+  const uint8_t st = phase1_both(t, tid, k, v, a, now, expiry, ws, i, c1, s1, c2, s2);
+  unlock_pair(t, a.b1, a.b2, c1, c2);
   if (st) status[i] = st;
 }
 

@@ -19,12 +19,25 @@
 
 namespace ckpp {
 
+// Lock word access: taking a lock is an acquire (later reads see what the
+// previous holder wrote), releasing it a release (everything written under the
+// lock is visible before the word clears). No full fence is needed.
+__device__ __forceinline__ uint32_t or_acquire(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acquire.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void exch_release(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint32_t& ctrl) {
   uint32_t* c = ctrl_ptr(t, b);
   for (int i = 0; i < kLockSpins; ++i) {
-    const uint32_t old = atomicOr(c, kLockBit);
+    const uint32_t old = or_acquire(c, kLockBit);
     if (!(old & kLockBit)) {
-      __threadfence();
       ctrl = old;
       return true;
     }
@@ -33,9 +46,16 @@ __device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint
   return false;
 }
 
+// One attempt, no wait: safe to call while holding locks in any order.
+__device__ __forceinline__ bool try_lock_bucket(const TableView& t, uint32_t b, uint32_t& ctrl) {
+  const uint32_t old = or_acquire(ctrl_ptr(t, b), kLockBit);
+  if (old & kLockBit) return false;
+  ctrl = old;
+  return true;
+}
+
 __device__ __forceinline__ void unlock_bucket(const TableView& t, uint32_t b, uint32_t ctrl) {
-  __threadfence();
-  atomicExch(ctrl_ptr(t, b), ctrl & ~kLockBit);
+  exch_release(ctrl_ptr(t, b), ctrl & ~kLockBit);
 }
 
 // Lock two distinct buckets in index order (no lock cycles). cx/cy receive the
