@@ -5,7 +5,7 @@ slots) filled to load factor 0.9 with 120,795,955 random 5-tuple keys (value =
 insertion index), then bulk_lookup batches of 2^24 keys with each key negative
 with probability 0.5 (Bernoulli), positives drawn uniformly from the inserted
 keys. A step is one bulk_lookup of one such batch, inputs resident in HBM.
-The table (4.8 GB) and the key batch (256 MB) are both larger than L2, so no
+The table (4.3 GB) and the key batch (256 MB) are both larger than L2, so no
 L2 flush is needed between steps.
 
 One JSON line on rank 0. Beside the headline `value` it reports:
@@ -101,6 +101,22 @@ def sources_sha256(paths=LOOKUP_SOURCES) -> str:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+def alg_bytes_of(counts, n: int) -> float:
+    """Algorithmic bytes of a lookup batch from its read counts (primary
+    bucket reads, secondary bucket reads, record reads, second-line reads):
+    32 bytes per bucket read (tags, filter, busy mask) and per record read
+    (key and value), plus 16 bytes of key in and 9 of result out per lookup.
+    The count is the method's, independent of how the layout groups fields
+    into lines."""
+    return 32.0 * float(counts[0] + counts[1] + counts[2]) + 25.0 * n
+
+
+def lines_of(counts) -> float:
+    """128-byte line requests a lookup batch makes: one per bucket read, plus
+    one per second-line read."""
+    return float(counts[0] + counts[1] + counts[3])
 
 
 def profiled_traffic(summary: str):
@@ -235,7 +251,7 @@ def run_ours(args, rank, world, local_rank):
             not (out_v.cpu().numpy().view(np.uint64) == q.expect_value).all():
         raise RuntimeError("lookup results differ from the workload's key -> value map")
     counts = table.probe_counts(keys).cpu().numpy()
-    alg_bytes = 32.0 * float(counts.sum()) + 25.0 * n
+    alg_bytes = alg_bytes_of(counts, n)
 
     def timed(kk, ov, of, steps, warmup):
         for _ in range(warmup):
@@ -275,13 +291,14 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": "plain Cuckoo++ at scale: 2^24 buckets x 8 slots, LF 0.9, 16M-key bulk_lookup",
                    "n_buckets": nb, "slots": 8, "entries": n_fill, "load_factor": args.load_factor,
                    "batch": n, "neg_rate": args.neg_rate, "timers": False,
-                   "l2": "inputs larger than L2 (table 4.8 GB, keys 256 MB); no flush"},
+                   "l2": "inputs larger than L2 (table 4.3 GB, keys 256 MB); no flush"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "alg_bytes_per_lookup": round(alg_bytes / n, 3),
                      "reads_per_lookup": {"primary": float(counts[0] / n), "secondary": float(counts[1] / n),
-                                          "record": float(counts[2] / n)}},
+                                          "record": float(counts[2] / n)},
+                     "line_requests_per_lookup": round(lines_of(counts) / n, 5)},
         "gpu_launches": args.steps,
     }
     if sampler:
@@ -293,9 +310,10 @@ def run_ours(args, rank, world, local_rank):
             qq, kk = batch(neg, 1 + int(neg))
             s, _, _ = timed(kk, out_v, out_f, max(10, args.steps // 4), 3)
             c = table.probe_counts(kk).cpu().numpy()
-            b = 32.0 * float(c.sum()) + 25.0 * n
+            b = alg_bytes_of(c, n)
             side[name] = {"value": round(n * max(10, args.steps // 4) / s / 1e9, 4), "unit": UNIT,
                           "alg_bytes_per_lookup": round(b / n, 3),
+                          "line_requests_per_lookup": round(lines_of(c) / n, 5),
                           "frac": round(b / (s / max(10, args.steps // 4)) / 1e9 / peak, 4)}
         out.update(side)
         out["e2e"] = e2e_lookup(args, table, q, dev, stream)
@@ -553,7 +571,8 @@ def run_batched(args):
                    "tables": nt, "total_slots": slots, "total_lookups_per_launch": total,
                    "table_bytes": int(sum(t.buf.numel() for t in tables)), "build_s": round(build_s, 1)},
         "tuning": {"threads_per_key": best[0], "group_depth": best[1], "blocks_per_sm": best[2],
-                   "candidates_ms": {f"T{t}_G{gd}_B{b}": round(v * 1e3, 4) for (t, gd, b), v in tune.items()}},
+                   "keys_per_warp": best[3],
+                   "candidates_ms": {f"G{gd}_K{kp}_B{b}": round(v * 1e3, 4) for (t, gd, b, kp), v in tune.items()}},
         "plain_per_table_eager": {"value": round(total / t_eager / 1e9, 4), "ms_per_step": round(t_eager * 1e3, 3)},
         "plain_per_table_graph": ({"value": round(total / t_graph / 1e9, 4), "ms_per_step": round(t_graph * 1e3, 3)}
                                   if t_graph else {"error": graph_error}),
@@ -603,7 +622,7 @@ def run_sweep(args):
         for neg in (0.0, 0.25, 0.5, 0.75, 1.0):
             kq, ef, ev = WG.lookup_batch(args.seed, n, m, neg, int(lf * 100 + neg * 10), device=dev)
             for variant, name in names.items():
-                cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+                cnt = torch.zeros(4, dtype=torch.int64, device=dev)
                 K.ckpp_lookup_probe_counts(t.handle, kq, cnt, 0, variant, stream)
                 reads = cnt.cpu().numpy()
                 steps = max(5, args.steps // 10)
@@ -617,9 +636,10 @@ def run_sweep(args):
                 e1.synchronize()
                 sec = e0.elapsed_time(e1) / 1e3 / steps
                 exact = bool(torch.equal(of, ef)) and bool(torch.equal(ov, ev))
-                b = 32.0 * float(reads.sum()) + 25.0 * n
+                b = alg_bytes_of(reads, n)
                 cells.append({"lf": lf, "neg": neg, "strategy": name, "glookups": round(n / sec / 1e9, 3),
                               "alg_bytes_per_lookup": round(b / n, 2), "frac": round(b / sec / 1e9 / peak, 4),
+                              "line_requests_per_lookup": round(lines_of(reads) / n, 4),
                               "secondary_reads_per_lookup": round(float(reads[1]) / n, 5), "exact": exact})
         cells[-1]["table"] = {"in_secondary": st["n_in_secondary"] / max(1, st["n_occupied"]),
                               "moved_zero": st["n_moved_zero"] / nb,

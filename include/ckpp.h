@@ -42,7 +42,7 @@ extern "C" {
 /* cudaStream_t without including the CUDA runtime headers. */
 typedef struct CUstream_st* ckpp_stream_t;
 
-#define CKPP_ABI_VERSION 1
+#define CKPP_ABI_VERSION 2
 
 /* return codes */
 #define CKPP_OK 0
@@ -101,9 +101,15 @@ typedef struct ckpp_stats {
 } ckpp_stats;
 
 /* Bytes of device memory a table of this geometry needs (0 if the geometry is
- * invalid). Layout: a 256-byte header, n_buckets bucket records (32 bytes, or 64
- * with CKPP_TIMERS), then n_buckets * 8 key/value records of 32 bytes at the
- * implicit index bucket * 8 + slot (Sec. 4.3). */
+ * invalid): a 256-byte header, then n_buckets buckets of 256 bytes. A bucket
+ * is two 128-byte lines. Line 0 holds the fields a lookup reads first (8
+ * 16-bit tags, the 64-bit filter, the busy / in_secondary / lock word and the
+ * moved counter; Sec. 4.1, 4.3) with the keys of slots 0..3 and either their
+ * values or, with CKPP_TIMERS, the 8 16-bit expiries (Sec. 4.2). Line 1 holds
+ * the keys of slots 4..7 and the remaining values. The keys and values of a
+ * bucket's slots thus sit in the bucket itself rather than in a separate array
+ * at the implicit index of Sec. 4.3: a random access costs one 128-byte line
+ * on this GPU, whatever part of the line it uses. */
 size_t ckpp_required_bytes(const ckpp_geometry* geometry);
 
 /* Device workspace bytes an insert or delete batch of n keys needs (scratch for
@@ -174,14 +180,17 @@ typedef struct ckpp_lookup_job {
   uint32_t table;       /* index into the batch's table list; jobs naming no table are skipped */
 } ckpp_lookup_job;
 
-/* Kernel configuration: threads per key 1, 2, 4 or 8; group depth (keys in
- * flight per thread) 1, 2 or 4 with one thread per key, else 1; persistent
- * blocks per SM 1..16. */
+/* Kernel configuration. threads_per_key: 4 (the only value): a key's 128-byte
+ * bucket line is fetched by 8 lanes of 16 bytes, four lines per warp
+ * instruction, one line request each. group_depth: 1 or 2 keys owned per
+ * lane, i.e. up to 32 or 64 line requests a warp has in flight. blocks_per_sm:
+ * 1..16 persistent blocks per SM. keys_per_warp: 8, 16 or 32 lanes of a warp
+ * that own keys per iteration (0 means 32). A NULL tuning is {4, 1, 4, 32}. */
 typedef struct ckpp_batch_tuning {
   uint32_t threads_per_key;
   uint32_t group_depth;
   uint32_t blocks_per_sm;
-  uint32_t reserved;
+  uint32_t keys_per_warp;
 } ckpp_batch_tuning;
 
 typedef struct ckpp_batch ckpp_batch;
@@ -288,8 +297,12 @@ int ckpp_stats_get(ckpp_table* table, uint32_t now, ckpp_stats* host_out, ckpp_s
 /* For a lookup batch, count the memory reads a lookup strategy (variant, see
  * ckpp_bulk_lookup_variant) makes without performing the lookup (no refresh):
  * d_counts[0] += primary bucket reads (n), d_counts[1] += secondary bucket
- * reads, d_counts[2] += key/value record reads. d_counts is a device
- * uint64[3]. Used to state a batch's algorithmic bytes.
+ * reads, d_counts[2] += key/value record reads (tag-matching candidates,
+ * examined in slot order until the key is met, Sec. 2), d_counts[3] += second-
+ * line reads (a bucket's line 1, read when a candidate or, with timers, the
+ * value lies there). d_counts is a device uint64[4]. The first three state a
+ * batch's algorithmic bytes; d_counts[0] + d_counts[1] + d_counts[3] is the
+ * number of 128-byte line requests the lookup makes.
  * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
 int ckpp_lookup_probe_counts(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32_t now, int variant,
                              uint64_t* d_counts, ckpp_stream_t stream);

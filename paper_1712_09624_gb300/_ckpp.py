@@ -42,7 +42,7 @@ class ckpp_lookup_job(C.Structure):
 
 class ckpp_batch_tuning(C.Structure):
     _fields_ = [("threads_per_key", C.c_uint32), ("group_depth", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("keys_per_warp", C.c_uint32)]
 
 
 LOOKUP_BLOOM, LOOKUP_OPTIMISTIC, LOOKUP_PESSIMISTIC = 0, 1, 2
@@ -232,6 +232,8 @@ def ckpp_lookup_probe_counts(handle: int, keys: torch.Tensor, d_counts: torch.Te
                              variant: int = LOOKUP_BLOOM, stream=None):
     _dev(keys, "keys", torch.uint8)
     _dev(d_counts, "d_counts", (torch.int64, torch.uint64))
+    if d_counts.numel() < 4:
+        raise ValueError("d_counts needs 4 elements")
     _check(_lib.ckpp_lookup_probe_counts(handle, _ptr(keys), keys.shape[0], now, variant, _ptr(d_counts),
                                          _stream(stream)), "ckpp_lookup_probe_counts")
 
@@ -286,14 +288,16 @@ def ckpp_batch_delete(handle: int, keys: torch.Tensor, table_ids: torch.Tensor, 
 
 
 def ckpp_batch_lookup(handle: int, d_jobs: torch.Tensor, max_jobs: int, d_n_jobs: torch.Tensor | None = None,
-                      now: int = 0, tuning: tuple[int, int, int] | None = None, stream=None):
-    """d_jobs: device uint8 tensor holding max_jobs ckpp_lookup_job records."""
+                      now: int = 0, tuning: tuple | None = None, stream=None):
+    """d_jobs: device uint8 tensor holding max_jobs ckpp_lookup_job records.
+    tuning: (threads_per_key, group_depth, blocks_per_sm[, keys_per_warp])."""
     _dev(d_jobs, "d_jobs", torch.uint8)
     if d_jobs.numel() < max_jobs * JOB_BYTES:
         raise ValueError("d_jobs holds fewer than max_jobs jobs")
     if d_n_jobs is not None:
         _dev(d_n_jobs, "d_n_jobs", (torch.int32, torch.uint32))
-    tn = None if tuning is None else C.byref(ckpp_batch_tuning(tuning[0], tuning[1], tuning[2], 0))
+    tn = None if tuning is None else C.byref(
+        ckpp_batch_tuning(tuning[0], tuning[1], tuning[2], tuning[3] if len(tuning) > 3 else 32))
     _check(_lib.ckpp_batch_lookup(handle, _ptr(d_jobs), max_jobs, _ptr(d_n_jobs), now, tn, _stream(stream)),
            "ckpp_batch_lookup")
 

@@ -12,6 +12,8 @@
 using namespace ckpp;
 using namespace ckpp::api;
 
+static_assert(kAbiVersion == CKPP_ABI_VERSION, "device and C ABI versions differ");
+
 
 extern "C" {
 
@@ -32,11 +34,9 @@ int ckpp_create(ckpp_table** out, const ckpp_geometry* geometry, void* dev_buf, 
   t->base = static_cast<uint8_t*>(dev_buf);
   t->bytes = table_bytes(geometry);
   t->view.buckets = t->base + kHeaderBytes;
-  t->view.records = t->view.buckets + (size_t)geometry->n_buckets * ((size_t)1 << bucket_shift(geometry));
   t->view.err = reinterpret_cast<uint32_t*>(t->base + kHdrErr);
   t->view.nb = geometry->n_buckets;
   t->view.seed = geometry->seed;
-  t->view.bucket_shift = bucket_shift(geometry);
   t->view.timers = (geometry->flags & CKPP_TIMERS) ? 1u : 0u;
   if (cudaMemsetAsync(t->base, 0, t->bytes, s) != cudaSuccess ||
       launch_init_header(t->base, geometry->n_buckets, geometry->slots_per_bucket, geometry->flags, geometry->seed,
@@ -225,16 +225,16 @@ int ckpp_batch_delete(ckpp_batch* b, const ckpp_key* keys, const uint32_t* table
 int ckpp_batch_lookup(ckpp_batch* b, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,
                       uint32_t now, const ckpp_batch_tuning* tuning, ckpp_stream_t stream) {
   if (!b || max_jobs > kBatchMaxJobs || (max_jobs && !d_jobs)) return CKPP_EINVAL;
-  ckpp_batch_tuning tn = tuning ? *tuning : ckpp_batch_tuning{1, 1, 4, 0};
-  const uint32_t T = tn.threads_per_key, G = tn.group_depth;
-  if (!(T == 1 || T == 2 || T == 4 || T == 8) || !(G == 1 || G == 2 || G == 4) || (T > 1 && G > 1) ||
-      tn.blocks_per_sm < 1 || tn.blocks_per_sm > 16)
+  ckpp_batch_tuning tn = tuning ? *tuning : ckpp_batch_tuning{4, 1, 4, 32};
+  const uint32_t T = tn.threads_per_key, G = tn.group_depth, P = tn.keys_per_warp ? tn.keys_per_warp : 32;
+  if (T != 4 || !(G == 1 || G == 2) || !(P == 8 || P == 16 || P == 32) || tn.blocks_per_sm < 1 ||
+      tn.blocks_per_sm > 16)
     return CKPP_EINVAL;
   for (ckpp_table* t : b->tables)
     if (int rc = time_check(t, now)) return rc;
   if (!max_jobs) return CKPP_OK;
   return cuda_rc(launch_batched_lookup(b->dev_views, (uint32_t)b->tables.size(), d_jobs, d_n_jobs, max_jobs, now,
-                                       (int)T, (int)G, tn.blocks_per_sm * (uint32_t)b->sms,
+                                       (int)T, (int)G, (int)P, tn.blocks_per_sm * (uint32_t)b->sms,
                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 

@@ -31,12 +31,7 @@ inline bool geometry_ok(const ckpp_geometry* g) {
          (g->flags & ~CKPP_TIMERS) == 0;
 }
 
-inline uint32_t bucket_shift(const ckpp_geometry* g) { return (g->flags & CKPP_TIMERS) ? 6u : 5u; }
-
-inline size_t table_bytes(const ckpp_geometry* g) {
-  return kHeaderBytes + (size_t)g->n_buckets * ((size_t)1 << bucket_shift(g)) +
-         (size_t)g->n_buckets * kSlots * kRecordBytes;
-}
+inline size_t table_bytes(const ckpp_geometry* g) { return kHeaderBytes + (size_t)g->n_buckets * kBucketBytes; }
 
 // Workspace of an n-key batch: counters | set_first[m] | set_last[m] |
 // slot_of[n] | pending[n] | retry[n] | fixup[fix_cap] (8 bytes each), each

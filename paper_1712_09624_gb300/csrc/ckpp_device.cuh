@@ -1,24 +1,32 @@
 // Device-side layout, hashing and memory helpers of the GB300 Cuckoo++ table.
 //
-// HBM layout of one table (caller-owned buffer):
+// HBM layout of one table (caller-owned buffer, 256-byte aligned):
 //   [0, 256)             header: magic, geometry copy, latched device error word
-//   buckets              n_buckets records of 32 B (64 B with timers), 32 B aligned
-//   records              n_buckets * 8 key/value records of 32 B at the implicit
-//                        index bucket * 8 + slot (Sec. 4.3 of the paper)
+//   buckets              n_buckets buckets of 256 bytes: two 128-byte lines
 //
-// Bucket, first 32-byte sector (everything a lookup reads, Sec. 4.3 "all fields
-// accessed when looking up a bucket are in the same cacheline", here the same
-// DRAM sector):
-//   bytes  0..15  tag[8]   16-bit tags derived from the primary hash
-//   bytes 16..23  bloom    64-bit filter of this bucket's displaced keys (Sec. 4.1)
-//   bytes 24..27  ctrl     bits 0-7 busy, bits 8-15 in_secondary, bit 31 insert lock
-//   bytes 28..31  moved    moved counter (Sec. 4.1)
-// With timers, the second sector holds expiry[8] (16-bit, Sec. 4.2) in bytes
-// 32..47; bytes 48..63 are reserved (zero).
-// Record (32 B, one sector): key (16 B), value (u64), then a u64 whose low 16
-// bits copy the slot's expiry in tables with timers (zero otherwise); the
-// rest is zero. The bucket's expiry[] is the copy inserts and scans use; the
-// record's copy lets a lookup test liveness with the sector it reads anyway.
+// The paper keeps every field a bucket lookup reads in one cache line and the
+// keys and values in a separate array at the implicit index bucket * 8 + slot
+// (Sec. 4.3). On GB300 the unit a random access pays for is one 128-byte L2
+// line request: a warp instruction in which four lanes read the four 32-byte
+// sectors of one line costs the same as a single 32-byte read. So each bucket
+// puts its lookup fields and the entries of its first four slots in one line;
+// a key found in slots 0..3 costs one line request, and a negative lookup
+// that the filter stops costs one as well.
+//
+// Line 0, bytes [0, 128):
+//   0..15    tag[8]     16-bit tags derived from the primary hash (Sec. 4.3)
+//   16..23   bloom      64-bit filter of this bucket's displaced keys (Sec. 4.1)
+//   24..27   ctrl       bits 0-7 busy, bits 8-15 in_secondary, bit 31 insert lock
+//   28..31   moved      moved counter (Sec. 4.1)
+//   32..95   key[0..3]  16 bytes each
+//   96..127  value[0..3] (u64 each)          -- tables without timers
+//            expiry[8] (u16 each, 96..111), then 16 zero bytes -- with timers
+// Line 1, bytes [128, 256):
+//   128..191 key[4..7]
+//   192..223 value[4..7], then 32 zero bytes  -- tables without timers
+//   192..255 value[0..7]                      -- with timers (Sec. 4.2)
+// With timers the expiries sit beside the fields a scan or an insertion
+// decides on (line 0), and every value moves to line 1.
 #pragma once
 
 #include <cstdint>
@@ -28,8 +36,10 @@ namespace ckpp {
 
 constexpr uint32_t kSlots = 8;
 constexpr uint64_t kHeaderBytes = 256;
-constexpr uint32_t kRecordBytes = 32;
+constexpr uint32_t kBucketBytes = 256;
+constexpr uint32_t kLineBytes = 128;
 constexpr uint32_t kMagic = 0x50504B43u;  // "CKPP"
+constexpr uint32_t kAbiVersion = 2;       // written to the header; equals CKPP_ABI_VERSION
 constexpr uint64_t kSeed2Xor = 0x9E3779B97F4A7C15ull;
 constexpr uint32_t kAliveWindow = 1024;   // Sec. 4.2
 constexpr uint32_t kMaxStale = 64512;     // Sec. 4.2: 65536 - 1024
@@ -56,12 +66,11 @@ constexpr int kLockSpins = 1 << 20;
 
 struct TableView {
   uint8_t* buckets;
-  uint8_t* records;
   uint32_t* err;
   uint64_t nb;
   uint64_t seed;
-  uint32_t bucket_shift;  // log2 of the bucket stride: 5 (32 B) or 6 (64 B, timers)
   uint32_t timers;
+  uint32_t pad;
 };
 
 struct Key {
@@ -131,7 +140,7 @@ __device__ __forceinline__ uint32_t tag_mask(uint64_t t0, uint64_t t1, uint32_t 
 
 // ------------------------------------------------------------ addressing
 __device__ __forceinline__ uint8_t* bucket_ptr(const TableView& t, uint32_t b) {
-  return t.buckets + ((uint64_t)b << t.bucket_shift);
+  return t.buckets + (uint64_t)b * kBucketBytes;
 }
 __device__ __forceinline__ uint64_t* bloom_ptr(const TableView& t, uint32_t b) {
   return reinterpret_cast<uint64_t*>(bucket_ptr(t, b) + 16);
@@ -145,21 +154,24 @@ __device__ __forceinline__ uint32_t* moved_ptr(const TableView& t, uint32_t b) {
 __device__ __forceinline__ uint16_t* tag_ptr(const TableView& t, uint32_t b, uint32_t s) {
   return reinterpret_cast<uint16_t*>(bucket_ptr(t, b)) + s;
 }
-__device__ __forceinline__ uint16_t* expiry_ptr(const TableView& t, uint32_t b, uint32_t s) {
-  return reinterpret_cast<uint16_t*>(bucket_ptr(t, b) + 32) + s;
+// Byte offsets of a slot's key, value and expiry within its bucket.
+__device__ __forceinline__ uint32_t key_off(uint32_t s) { return 32u + 16u * s + (s >= 4 ? 32u : 0u); }
+__device__ __forceinline__ uint32_t value_off(uint32_t timers, uint32_t s) {
+  return timers ? 192u + 8u * s : 96u + 8u * s + (s >= 4 ? 64u : 0u);
 }
-__device__ __forceinline__ uint8_t* record_ptr(const TableView& t, uint32_t b, uint32_t s) {
-  return t.records + ((uint64_t)b * kSlots + s) * kRecordBytes;
+__device__ __forceinline__ uint8_t* key_ptr(const TableView& t, uint32_t b, uint32_t s) {
+  return bucket_ptr(t, b) + key_off(s);
+}
+__device__ __forceinline__ uint64_t* value_ptr(const TableView& t, uint32_t b, uint32_t s) {
+  return reinterpret_cast<uint64_t*>(bucket_ptr(t, b) + value_off(t.timers, s));
+}
+__device__ __forceinline__ uint16_t* expiry_ptr(const TableView& t, uint32_t b, uint32_t s) {
+  return reinterpret_cast<uint16_t*>(bucket_ptr(t, b) + 96) + s;
 }
 
 // ---------------------------------------------------------- memory access
-// Cache policies: bucket sectors are worth keeping in L2 (the bucket array is
-// the table's hot part), records and streamed keys are not.
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
+// Cache policies: L2 evict_first for data read once per lookup (bucket lines
+// of a table far larger than L2, streamed keys).
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -205,9 +217,8 @@ __device__ __forceinline__ uint32_t ld16_cg(const void* p) {
   asm volatile("ld.global.relaxed.gpu.u16 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st256_cg(void* p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
-  asm volatile("st.global.relaxed.gpu.v4.u64 [%0], {%1,%2,%3,%4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
-               : "memory");
+__device__ __forceinline__ void st128_cg(void* p, uint64_t a, uint64_t b) {
+  asm volatile("st.global.relaxed.gpu.v2.u64 [%0], {%1,%2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
 __device__ __forceinline__ void st64_cg(void* p, uint64_t v) {
   asm volatile("st.global.relaxed.gpu.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -216,16 +227,10 @@ __device__ __forceinline__ void st16_cg(void* p, uint32_t v) {
   asm volatile("st.global.relaxed.gpu.u16 [%0], %1;" ::"l"(p), "h"((uint16_t)v) : "memory");
 }
 
-// Set a slot's expiry: the bucket's copy and the record's copy.
+// Set a slot's expiry (timers tables only).
 __device__ __forceinline__ void set_expiry(const TableView& t, uint32_t b, uint32_t s, uint32_t expiry) {
-  asm volatile("st.global.relaxed.gpu.u16 [%0], %1;" ::"l"(reinterpret_cast<uint16_t*>(t.buckets + ((uint64_t)b << t.bucket_shift) + 32) + s),
-               "h"((uint16_t)expiry) : "memory");
-  asm volatile("st.global.relaxed.gpu.u16 [%0], %1;" ::"l"(t.records + ((uint64_t)b * kSlots + s) * kRecordBytes + 24),
-               "h"((uint16_t)expiry) : "memory");
+  asm volatile("st.global.relaxed.gpu.u16 [%0], %1;" ::"l"(expiry_ptr(t, b, s)), "h"((uint16_t)expiry) : "memory");
 }
-
-// Records are read as 4 x u64: k0, k1, value, expiry copy (timers) / zero.
-__device__ __forceinline__ bool same_key(const uint64_t (&r)[4], const Key& k) { return r[0] == k.k0 && r[1] == k.k1; }
 
 __device__ __forceinline__ void latch_error(const TableView& t, uint32_t bit) { atomicOr(t.err, bit); }
 

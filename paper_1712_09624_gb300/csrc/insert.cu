@@ -110,7 +110,7 @@ __device__ uint8_t phase1_both(const TableView& t, uint32_t tid, const Key& k, u
   }
   if (slot >= 0) {
     const bool was_alive = !t.timers || alive16(snap_expiry(*sb, slot), now);
-    st64_cg(record_ptr(t, b, slot) + 16, v);
+    st64_cg(value_ptr(t, b, slot), v);
     if (t.timers) set_expiry(t, b, slot, expiry);
     return was_alive ? kStUpdated : kStInserted;
   }
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
   const int slot = find_key(t, a.b1, c1, s1, k, a.tag);
   if (slot >= 0) {
     const bool was_alive = !t.timers || alive16(snap_expiry(s1, slot), now);
-    st64_cg(record_ptr(t, a.b1, slot) + 16, v);
+    st64_cg(value_ptr(t, a.b1, slot), v);
     if (t.timers) set_expiry(t, a.b1, slot, expiry);
     unlock_bucket(t, a.b1, c1);
     status[i] = was_alive ? kStUpdated : kStInserted;
@@ -301,7 +301,7 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue&
     if (cur.depth >= kBfsDepth) continue;
     uint64_t k0[kSlots], k1[kSlots];
 #pragma unroll
-    for (uint32_t sl = 0; sl < kSlots; ++sl) ld128_cg(record_ptr(t, cur.bucket, sl), k0[sl], k1[sl]);
+    for (uint32_t sl = 0; sl < kSlots; ++sl) ld128_cg(key_ptr(t, cur.bucket, sl), k0[sl], k1[sl]);
     uint32_t y[kSlots], cy[kSlots];
     uint64_t e0[kSlots], e1[kSlots];
 #pragma unroll
@@ -349,10 +349,12 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue&
 // zero (safe: filter bits of y are only ever set under y's lock, held here).
 __device__ void move_locked(const TableView& t, uint32_t x, uint32_t sx, uint32_t& cx, uint32_t y, uint32_t sy,
                             uint32_t& cy) {
-  uint64_t r[4];
-  ld256_cg(record_ptr(t, x, sx), r);
-  const Addr e = address_of(Key{r[0], r[1]}, t.nb, t.seed);
-  st256_cg(record_ptr(t, y, sy), r[0], r[1], r[2], r[3]);
+  uint64_t k0, k1;
+  ld128_cg(key_ptr(t, x, sx), k0, k1);
+  const uint64_t v = ld64_cg(value_ptr(t, x, sx));
+  const Addr e = address_of(Key{k0, k1}, t.nb, t.seed);
+  st128_cg(key_ptr(t, y, sy), k0, k1);
+  st64_cg(value_ptr(t, y, sy), v);
   st16_cg(tag_ptr(t, y, sy), e.tag);
   if (t.timers) st16_cg(expiry_ptr(t, y, sy), ld16_cg(expiry_ptr(t, x, sx)));
   cy |= 1u << sy;
@@ -409,9 +411,9 @@ __device__ int execute_path(const TableView& t, uint32_t tid, const uint32_t (&p
       ok = false;
       break;
     }
-    uint64_t r[4];
-    ld256_cg(record_ptr(t, path[j], slot[j]), r);
-    const Addr e = address_of(Key{r[0], r[1]}, t.nb, t.seed);
+    Key ek;
+    ld128_cg(key_ptr(t, path[j], slot[j]), ek.k0, ek.k1);
+    const Addr e = address_of(ek, t.nb, t.seed);
     const uint32_t other = (e.b1 == path[j]) ? e.b2 : (e.b2 == path[j] ? e.b1 : 0xFFFFFFFFu);
     ok = (other == path[j + 1]);
   }
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint
 #pragma unroll
       for (uint32_t sl = 0; sl < kSlots; ++sl) {
         uint64_t k0, k1;
-        ld128_cg(record_ptr(t, x, sl), k0, k1);
+        ld128_cg(key_ptr(t, x, sl), k0, k1);
         const Addr e = address_of(Key{k0, k1}, t.nb, t.seed);
         y[sl] = (e.b1 == x) ? e.b2 : e.b1;
       }

@@ -3,7 +3,7 @@
 // counter and Bloom filter upkeep of Sec. 4.1.
 //
 // Concurrency rules of the insert kernels (one table, one batch at a time):
-//  * a bucket's busy / in_secondary bits, tags, expiries and records change only
+//  * a bucket's busy / in_secondary bits, tags, expiries, keys and values change only
 //    while its lock bit (ctrl bit 31) is held; the new ctrl word is published
 //    by the unlocking exchange;
 //  * Bloom bits of bucket p are set only while p's lock is held, so a filter
@@ -31,6 +31,7 @@ __device__ __forceinline__ uint32_t or_acquire(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ void exch_release(uint32_t* p, uint32_t v) {
   uint32_t old;
   asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  (void)old;
 }
 
 __device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint32_t& ctrl) {
@@ -83,7 +84,7 @@ __device__ __forceinline__ void unlock_pair(const TableView& t, uint32_t x, uint
   }
 }
 
-// Coherent snapshot of a bucket: hot sector and (with timers) the 8 expiries.
+// Coherent snapshot of a bucket: its first sector and (with timers) the 8 expiries.
 struct Snap {
   uint64_t w[4];
   uint64_t e0, e1;
@@ -118,9 +119,9 @@ __device__ __forceinline__ int find_key(const TableView& t, uint32_t b, uint32_t
   while (cand) {
     const int slot = __ffs(cand) - 1;
     cand &= cand - 1;
-    uint64_t r[4];
-    ld256_cg(record_ptr(t, b, slot), r);
-    if (same_key(r, k)) return slot;
+    uint64_t k0, k1;
+    ld128_cg(key_ptr(t, b, slot), k0, k1);
+    if (k0 == k.k0 && k1 == k.k1) return slot;
   }
   return -1;
 }
@@ -139,9 +140,8 @@ __device__ __forceinline__ void push_fixup(const Workspace& ws, uint32_t table, 
 __device__ __forceinline__ void evict_entry(const TableView& t, uint32_t tid, uint32_t b, uint32_t s, uint32_t& ctrl,
                                             const Workspace& ws) {
   if ((ctrl >> (kInsecShift + s)) & 1u) {
-    uint64_t r[4];
-    ld256_cg(record_ptr(t, b, s), r);
-    const Key k{r[0], r[1]};
+    Key k;
+    ld128_cg(key_ptr(t, b, s), k.k0, k.k1);
     const Addr a = address_of(k, t.nb, t.seed);
     const uint32_t old = atomicSub(moved_ptr(t, a.b1), 1u);
     if (old == 1u) push_fixup(ws, tid, a.b1);
@@ -154,7 +154,8 @@ __device__ __forceinline__ void evict_entry(const TableView& t, uint32_t tid, ui
 // primary's moved counter (Sec. 4.1). The caller holds the primary's lock too.
 __device__ __forceinline__ void place_entry(const TableView& t, uint32_t b, uint32_t s, const Key& k, uint64_t v,
                                             const Addr& a, uint32_t expiry, uint32_t& ctrl) {
-  st256_cg(record_ptr(t, b, s), k.k0, k.k1, v, t.timers ? (uint64_t)(expiry & 0xFFFFu) : 0ull);
+  st128_cg(key_ptr(t, b, s), k.k0, k.k1);
+  st64_cg(value_ptr(t, b, s), v);
   st16_cg(tag_ptr(t, b, s), a.tag);
   if (t.timers) st16_cg(expiry_ptr(t, b, s), expiry);
   ctrl |= 1u << s;

@@ -10,7 +10,7 @@ namespace {
 
 __global__ void init_header_kernel(uint8_t* base, uint64_t nb, uint32_t slots, uint32_t flags, uint64_t seed) {
   *reinterpret_cast<uint32_t*>(base + kHdrMagic) = kMagic;
-  *reinterpret_cast<uint32_t*>(base + kHdrAbi) = 1u;
+  *reinterpret_cast<uint32_t*>(base + kHdrAbi) = kAbiVersion;
   *reinterpret_cast<uint64_t*>(base + kHdrBuckets) = nb;
   *reinterpret_cast<uint32_t*>(base + kHdrSlots) = slots;
   *reinterpret_cast<uint32_t*>(base + kHdrFlags) = flags;
@@ -37,9 +37,9 @@ __global__ void __launch_bounds__(256) expire_kernel(TableView t, uint32_t now, 
     while (displaced) {
       const int s = __ffs(displaced) - 1;
       displaced &= displaced - 1;
-      uint64_t r[4];
-      ld256_cg(record_ptr(t, b, s), r);
-      const Addr a = address_of(Key{r[0], r[1]}, t.nb, t.seed);
+      Key k;
+      ld128_cg(key_ptr(t, b, s), k.k0, k.k1);
+      const Addr a = address_of(k, t.nb, t.seed);
       if (atomicSub(moved_ptr(t, a.b1), 1u) == 1u)
         atomicExch(reinterpret_cast<unsigned long long*>(bloom_ptr(t, a.b1)), 0ull);
     }

@@ -82,10 +82,10 @@ class FlowTable:
         return K.ckpp_stats_get(self.handle, now, stream)
 
     def probe_counts(self, keys, now: int = 0, variant: int = K.LOOKUP_BLOOM, stream=None) -> torch.Tensor:
-        """[primary bucket reads, secondary bucket reads, record reads] a lookup
-        strategy makes on a batch."""
+        """[primary bucket reads, secondary bucket reads, record reads,
+        second-line reads] a lookup strategy makes on a batch."""
         k = as_device_keys(keys, self.device)
-        counts = torch.zeros(3, dtype=torch.int64, device=self.device)
+        counts = torch.zeros(4, dtype=torch.int64, device=self.device)
         K.ckpp_lookup_probe_counts(self.handle, k, counts, now, variant, stream)
         return counts
 

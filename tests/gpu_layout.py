@@ -14,31 +14,54 @@ import oracle
 
 HEADER = 256
 SLOTS = 8
+BUCKET = 256
+
+
+def key_offsets() -> np.ndarray:
+    """Byte offset of each slot's key in a bucket: slots 0-3 in line 0 after
+    the 32-byte header, slots 4-7 at the start of line 1."""
+    s = np.arange(SLOTS)
+    return 32 + 16 * s + np.where(s >= 4, 32, 0)
+
+
+def value_offsets(timers: bool) -> np.ndarray:
+    """Byte offset of each slot's value: without timers, values 0-3 end line 0
+    and values 4-7 follow keys 4-7; with timers all eight fill the end of
+    line 1."""
+    s = np.arange(SLOTS)
+    return 192 + 8 * s if timers else 96 + 8 * s + np.where(s >= 4, 64, 0)
+
+
+EXPIRY_OFF = 96  # timers: expiry[8] in line 0 after keys 0-3
+
+
+def reserved_ranges(timers: bool) -> list[tuple[int, int]]:
+    return [(112, 128)] if timers else [(224, 256)]
 
 
 class Decoded:
     def __init__(self, buf: np.ndarray, n_buckets: int, timers: bool, seed: int):
         self.nb, self.timers, self.seed = n_buckets, timers, seed
-        bb = 64 if timers else 32
         hdr = buf[:HEADER]
         self.magic = int(hdr[0:4].view(np.uint32)[0])
+        self.abi = int(hdr[4:8].view(np.uint32)[0])
         self.err = int(hdr[32:36].view(np.uint32)[0])
-        bk = buf[HEADER:HEADER + n_buckets * bb].reshape(n_buckets, bb)
+        bk = buf[HEADER:HEADER + n_buckets * BUCKET].reshape(n_buckets, BUCKET)
         self.tags = np.ascontiguousarray(bk[:, 0:16]).view(np.uint16).reshape(n_buckets, 8)
         self.bloom = np.ascontiguousarray(bk[:, 16:24]).view(np.uint64).reshape(n_buckets)
         self.ctrl = np.ascontiguousarray(bk[:, 24:28]).view(np.uint32).reshape(n_buckets)
         self.moved = np.ascontiguousarray(bk[:, 28:32]).view(np.uint32).reshape(n_buckets)
         if timers:
-            self.expiry = np.ascontiguousarray(bk[:, 32:48]).view(np.uint16).reshape(n_buckets, 8)
-            self.bucket_reserved = bk[:, 48:64]
+            self.expiry = np.ascontiguousarray(bk[:, EXPIRY_OFF:EXPIRY_OFF + 16]).view(np.uint16).reshape(n_buckets, 8)
         else:
             self.expiry = np.zeros((n_buckets, 8), np.uint16)
-            self.bucket_reserved = np.zeros((n_buckets, 0), np.uint8)
-        off = HEADER + n_buckets * bb
-        rec = buf[off:off + n_buckets * SLOTS * 32].reshape(n_buckets * SLOTS, 32)
-        self.rec_key = rec[:, 0:16]
-        self.rec_value = np.ascontiguousarray(rec[:, 16:24]).view(np.uint64).reshape(-1)
-        self.rec_reserved = np.ascontiguousarray(rec[:, 24:32]).view(np.uint64).reshape(-1)
+        self.bucket_reserved = np.concatenate([bk[:, a:b] for a, b in reserved_ranges(timers)], axis=1)
+        ko = key_offsets()
+        keys = np.stack([bk[:, o:o + 16] for o in ko], axis=1)  # [nb, 8, 16]
+        self.rec_key = np.ascontiguousarray(keys.reshape(n_buckets * SLOTS, 16))
+        vo = value_offsets(timers)
+        vals = np.stack([np.ascontiguousarray(bk[:, o:o + 8]).view(np.uint64).reshape(-1) for o in vo], axis=1)
+        self.rec_value = np.ascontiguousarray(vals.reshape(-1))
         bits = np.arange(8, dtype=np.uint32)
         self.busy = ((self.ctrl[:, None] >> bits) & 1).astype(bool)
         self.insec = ((self.ctrl[:, None] >> (bits + 8)) & 1).astype(bool)
@@ -83,14 +106,8 @@ class Decoded:
             bad.append("in_secondary flag disagrees with the bucket")
         if not (self.tags[b, s] == a["tag"]).all():
             bad.append("stored tag differs from the key's tag")
-        mirror = self.rec_reserved[occ] & np.uint64(0xFFFF)
-        if (self.rec_reserved[occ] >> np.uint64(16) != 0).any():
-            bad.append("record reserved bytes not zero")
-        if self.timers:
-            if not (mirror == self.expiry[b, s].astype(np.uint64)).all():
-                bad.append("record expiry copy differs from the bucket's expiry")
-        elif (mirror != 0).any():
-            bad.append("record expiry copy set in a table without timers")
+        if self.bucket_reserved.any():
+            bad.append("reserved bucket bytes not zero")
         bits = (np.uint64(1) << a["bit1"].astype(np.uint64)) | (np.uint64(1) << a["bit2"].astype(np.uint64))
         p = a["b1"][insec]
         if not ((self.bloom[p] & bits[insec]) == bits[insec]).all():
@@ -123,17 +140,23 @@ def oracle_live(t: "oracle.Table", now: int) -> dict:
     return out
 
 
-def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int) -> tuple[int, int, int]:
-    """(keys, secondary-bucket reads, record reads) that a lookup of ``keys``
-    with strategy ``variant`` (0 Bloom, 1 optimistic, 2 pessimistic) makes on
-    the decoded table: candidates are busy slots whose tag matches, confirmed in
-    slot order until the key is met (Sec. 2); the secondary is read after a
-    primary miss when both filter bits are set (Bloom, Sec. 4.1), after every
-    primary miss (optimistic) or always (pessimistic, Sec. 3)."""
+def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int,
+                          now: int = 0) -> tuple[int, int, int, int]:
+    """(keys, secondary-bucket reads, record reads, second-line reads) that a
+    lookup of ``keys`` with strategy ``variant`` (0 Bloom, 1 optimistic,
+    2 pessimistic) makes on the decoded table: candidates are busy slots whose
+    tag matches, confirmed in slot order until the key is met (Sec. 2); the
+    secondary is read after a primary miss when both filter bits are set
+    (Bloom, Sec. 4.1), after every primary miss (optimistic) or always
+    (pessimistic, Sec. 3). A bucket's second line is read when the key is not
+    among slots 0-3 and a tag of slots 4-7 matches, or, with timers, to fetch
+    the value of a live entry found in slots 0-3; a pessimistic read of the
+    secondary after a primary hit reads its first line only."""
     a = oracle.address(keys, d.nb, d.seed)
     kv = np.ascontiguousarray(keys).view(np.dtype((np.void, 16))).reshape(-1)
     rk = np.ascontiguousarray(d.rec_key).view(np.dtype((np.void, 16))).reshape(-1)
     slots = np.arange(SLOTS)
+    alive = d.alive(now)
 
     def bucket_reads(b):
         cand = (d.tags[b] == a["tag"][:, None]) & d.busy[b]
@@ -141,10 +164,13 @@ def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int) -> tuple[i
         found = hit.any(axis=1)
         first = np.where(found, hit.argmax(axis=1), SLOTS)
         upto = cand & (slots[None, :] <= first[:, None])
-        return found, upto.sum(axis=1)
+        low_hit = found & (first < 4)
+        hit_alive = alive[b, np.minimum(first, SLOTS - 1)]
+        line1 = np.where(low_hit, d.timers & hit_alive, cand[:, 4:].any(axis=1))
+        return found, upto.sum(axis=1), line1
 
-    f1, r1 = bucket_reads(a["b1"].astype(np.int64))
-    _, r2 = bucket_reads(a["b2"].astype(np.int64))
+    f1, r1, l1 = bucket_reads(a["b1"].astype(np.int64))
+    _, r2, l2 = bucket_reads(a["b2"].astype(np.int64))
     bits = (np.uint64(1) << a["bit1"].astype(np.uint64)) | (np.uint64(1) << a["bit2"].astype(np.uint64))
     if variant == 0:
         read2 = ~f1 & ((d.bloom[a["b1"]] & bits) == bits)
@@ -156,35 +182,34 @@ def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int) -> tuple[i
         read2 = ~f1
         sec = keys.shape[0]
     rec = int(r1.sum() + r2[read2].sum())
-    return keys.shape[0], sec, rec
+    line1 = int(l1.sum() + l2[read2].sum())
+    return keys.shape[0], sec, rec, line1
 
 
 def encode_oracle(t: "oracle.Table") -> np.ndarray:
     """The oracle table's entries written out in the GPU byte layout (header,
-    bucket array, record array), so the decoder and the helpers above can be
-    checked on the CPU against the oracle's own answers."""
+    then 256-byte buckets), so the decoder and the helpers above can be checked
+    on the CPU against the oracle's own answers."""
     nb, timers = t.n_buckets, t.timers
-    bb = 64 if timers else 32
-    buf = np.zeros(HEADER + nb * bb + nb * SLOTS * 32, np.uint8)
+    buf = np.zeros(HEADER + nb * BUCKET, np.uint8)
     buf[0:4] = np.frombuffer(np.uint32(0x50504B43).tobytes(), np.uint8)
+    buf[4:8] = np.frombuffer(np.uint32(2).tobytes(), np.uint8)
     d = t.dump()
     bloom, moved = t.meta()
-    bk = buf[HEADER:HEADER + nb * bb].reshape(nb, bb)
+    bk = buf[HEADER:].reshape(nb, BUCKET)
     bk[:, 16:24] = bloom.view(np.uint8).reshape(nb, 8)
     bk[:, 28:32] = moved.view(np.uint8).reshape(nb, 4)
     ctrl = np.zeros(nb, np.uint32)
-    rec = buf[HEADER + nb * bb:].reshape(nb * SLOTS, 32)
     a = oracle.address(d["key"], nb, t.seed)
+    ko, vo = key_offsets(), value_offsets(timers)
     for i in range(d["value"].shape[0]):
         b, s = int(d["bucket"][i]), int(d["slot"][i])
         ctrl[b] |= np.uint32(1 << s) | np.uint32(int(d["in_secondary"][i]) << (8 + s))
         bk[b, 2 * s:2 * s + 2] = np.frombuffer(np.uint16(a["tag"][i]).tobytes(), np.uint8)
-        r = b * SLOTS + s
-        rec[r, 0:16] = d["key"][i]
-        rec[r, 16:24] = np.frombuffer(np.uint64(d["value"][i]).tobytes(), np.uint8)
+        bk[b, ko[s]:ko[s] + 16] = d["key"][i]
+        bk[b, vo[s]:vo[s] + 8] = np.frombuffer(np.uint64(d["value"][i]).tobytes(), np.uint8)
         if timers:
             e = np.uint16(d["expiry"][i]).tobytes()
-            bk[b, 32 + 2 * s:34 + 2 * s] = np.frombuffer(e, np.uint8)
-            rec[r, 24:26] = np.frombuffer(e, np.uint8)
+            bk[b, EXPIRY_OFF + 2 * s:EXPIRY_OFF + 2 * s + 2] = np.frombuffer(e, np.uint8)
     bk[:, 24:28] = ctrl.view(np.uint8).reshape(nb, 4)
     return buf

@@ -46,11 +46,11 @@ def test_every_declared_symbol_is_exported(K):
 
 
 def test_host_only_calls(K):
-    assert K.ckpp_abi_version() == 1
+    assert K.ckpp_abi_version() == 2
     g = K.geometry(1 << 24)
-    assert K.ckpp_required_bytes(g) == 256 + (1 << 24) * 32 + (1 << 27) * 32
+    assert K.ckpp_required_bytes(g) == 256 + (1 << 24) * 256  # 256-byte buckets, entries inside
     gt = K.geometry(1 << 24, timers=True)
-    assert K.ckpp_required_bytes(gt) == 256 + (1 << 24) * 64 + (1 << 27) * 32
+    assert K.ckpp_required_bytes(gt) == 256 + (1 << 24) * 256
     for bad in (K.geometry(1), K.geometry(0), K.geometry(1 << 32)):
         assert K.ckpp_required_bytes(bad) == 0
     wrong_slots = K.ckpp_geometry(1024, 4, 0, 0)

@@ -84,7 +84,7 @@ def batch_setup():
     return BatchedLookup(tables, max_jobs=64), tables, qs
 
 
-@pytest.mark.parametrize("tuning", [(1, 1, 4), (1, 2, 4), (1, 4, 2), (2, 1, 4), (4, 1, 4), (8, 1, 2), (1, 1, 1)])
+@pytest.mark.parametrize("tuning", [(4, 1, 4, 32), (4, 2, 3, 32), (4, 2, 1, 8), (4, 1, 2, 16), (4, 1, 1, 8)])
 def test_batched_equals_plain_per_table(batch_setup, tuning):
     batch, tables, qs = batch_setup
     ref = plain_results(tables, qs)

@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_layout import download, oracle_live
+from gpu_layout import download, expected_probe_counts, oracle_live
 from paper_1712_09624_gb300 import workload as W
 
 pytestmark = pytest.mark.gpu
@@ -81,8 +81,10 @@ def test_lookup_ragged_batches(n):
 
 
 def test_probe_counts_match_method():
-    """Secondary-bucket and record reads reported by the counting kernel equal a
-    host replay of the method on the downloaded GPU table."""
+    """Secondary-bucket, record and second-line reads reported by the counting
+    kernel equal a host replay of the method on the downloaded GPU table. A
+    bucket's second line (slots 4-7) is read only when the key is not found
+    among slots 0-3 and a tag of slots 4-7 matches."""
     nb = 1 << 12
     f = W.fill(3, int(0.93 * nb * 8))
     g = FT(nb, seed=3)
@@ -91,7 +93,7 @@ def test_probe_counts_match_method():
     c = g.probe_counts(q.keys).cpu().numpy()
     d = download(g)
     a = oracle.address(q.keys, nb, 3)
-    sec = rec = 0
+    sec = rec = line1 = 0
     kv = q.keys.view(np.uint64).reshape(-1, 2)
     rk = d.rec_key.view(np.uint64).reshape(-1, 2)
     for i in range(q.keys.shape[0]):
@@ -104,13 +106,33 @@ def test_probe_counts_match_method():
                 sec += 1
             for s in range(8):
                 if d.busy[b, s] and d.tags[b, s] == a["tag"][i]:
+                    if s >= 4 and not any(d.busy[b, t] and d.tags[b, t] == a["tag"][i] for t in range(4, s)):
+                        line1 += 1  # the first candidate of slots 4-7 brings in line 1
                     rec += 1
                     if (rk[b * 8 + s] == kv[i]).all():
                         hit = True
                         break
             if hit:
                 break
-    assert c[0] == q.keys.shape[0] and c[1] == sec and c[2] == rec
+    assert c[0] == q.keys.shape[0] and c[1] == sec and c[2] == rec and c[3] == line1
+    assert tuple(int(x) for x in c) == expected_probe_counts(d, q.keys, 0)
+
+
+def test_probe_counts_with_timers():
+    """With timers every value sits in line 1, so a live entry found in slots
+    0-3 costs a second line read and a dead one does not; the counting kernel
+    agrees with the replay at a time when part of the table has expired."""
+    nb = 1 << 12
+    f = W.fill(4, int(0.9 * nb * 8))
+    g = FT(nb, timers=True, seed=4)
+    half = f.keys.shape[0] // 2
+    g.insert(f.keys[:half], f.values[:half], now=100, ttl=50)
+    g.insert(f.keys[half:], f.values[half:], now=100, ttl=900)
+    q = W.lookup_batch(4, 30000, f, 0.3)
+    d = download(g)
+    for now in (120, 400):
+        c = g.probe_counts(q.keys, now=now).cpu().numpy()
+        assert tuple(int(x) for x in c) == expected_probe_counts(d, q.keys, 0, now)
 
 
 # ----------------------------------------------------- mutation streams

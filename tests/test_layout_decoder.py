@@ -19,12 +19,15 @@ def test_decoder_round_trip_and_read_counts():
         assert d.check() == []
         assert d.live(20) == oracle_live(o, 20)
         q = W.lookup_batch(seed, 20000, f, 0.5)
-        n, sec, rec = expected_probe_counts(d, q.keys, 0)
+        n, sec, rec, l1 = expected_probe_counts(d, q.keys, 0, 20)
         assert n == q.keys.shape[0] and (sec, rec) == o.probe_counts(q.keys, 20)
-        _, sec_opt, rec_opt = expected_probe_counts(d, q.keys, 1)
-        _, sec_pes, rec_pes = expected_probe_counts(d, q.keys, 2)
+        _, sec_opt, rec_opt, l1_opt = expected_probe_counts(d, q.keys, 1, 20)
+        _, sec_pes, rec_pes, l1_pes = expected_probe_counts(d, q.keys, 2, 20)
         assert sec < sec_opt < sec_pes == n
         assert rec <= rec_opt == rec_pes
+        assert l1 <= l1_opt == l1_pes
+        # without timers a second line is read only for a tag match in slots 4-7
+        assert 0 < l1 < n
 
 
 def test_decoder_flags_a_broken_filter():
