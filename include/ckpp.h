@@ -184,8 +184,9 @@ typedef struct ckpp_lookup_job {
  * bucket line is fetched by 8 lanes of 16 bytes, four lines per warp
  * instruction, one line request each. group_depth: 1 or 2 keys owned per
  * lane, i.e. up to 32 or 64 line requests a warp has in flight. blocks_per_sm:
- * 1..16 persistent blocks per SM. keys_per_warp: 8, 16 or 32 lanes of a warp
- * that own keys per iteration (0 means 32). A NULL tuning is {4, 1, 4, 32}. */
+ * 1..4 persistent blocks of 512 threads per SM. keys_per_warp: 8, 16 or 32
+ * lanes of a warp that own keys per iteration (0 means 32). A NULL tuning is
+ * {4, 1, 2, 32}. */
 typedef struct ckpp_batch_tuning {
   uint32_t threads_per_key;
   uint32_t group_depth;
@@ -195,7 +196,9 @@ typedef struct ckpp_batch_tuning {
 
 typedef struct ckpp_batch ckpp_batch;
 
-/* Device bytes of a batch descriptor for n_tables tables. */
+/* Device bytes of a batch descriptor for n_tables tables (their views and a
+ * 256-byte control block the lookup kernel uses to hand out work; lookups that
+ * use one descriptor must therefore be ordered, e.g. on one stream). */
 size_t ckpp_batch_bytes(uint32_t n_tables);
 
 /* Describe tables[0..n_tables) (handles of tables on the current device) in
@@ -225,8 +228,8 @@ int ckpp_batch_delete(ckpp_batch* batch, const ckpp_key* keys, const uint32_t* t
 /* Look up every job's keys in its table (filter-pruned, as ckpp_bulk_lookup,
  * without refresh) in one launch. d_jobs: device array of at least max_jobs
  * jobs; d_n_jobs: NULL (use max_jobs) or a device uint32 job count, clamped to
- * max_jobs. tuning: NULL for the default (1 thread per key, depth 1, 4 blocks
- * per SM). The job data is not validated on the host: every job's pointers must
+ * max_jobs. tuning: NULL for the default (see ckpp_batch_tuning). Launches on
+ * one batch must not overlap on the GPU (they share its work counter). The job data is not validated on the host: every job's pointers must
  * be valid device memory. Errors: CKPP_EINVAL (max_jobs above
  * CKPP_BATCH_MAX_JOBS, bad tuning), CKPP_ESTALE (a timers table), CKPP_ECUDA. */
 int ckpp_batch_lookup(ckpp_batch* batch, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,

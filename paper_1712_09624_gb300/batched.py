@@ -25,7 +25,7 @@ assert JOB_DTYPE.itemsize == K.JOB_BYTES
 THREADS_PER_KEY = 4
 GROUP_DEPTHS = [1, 2]
 KEYS_PER_WARP = [8, 16, 32]
-BLOCKS_PER_SM = [1, 2, 3, 4]
+BLOCKS_PER_SM = [1, 2, 3, 4]  # blocks of 512 threads
 
 _tune_cache: dict[tuple, tuple[int, int, int, int]] = {}
 
@@ -41,7 +41,7 @@ class BatchedLookup:
         self.handle = K.ckpp_batch_create([t.handle for t in self.tables], self.desc, stream)
         self.jobs = torch.zeros(self.max_jobs * K.JOB_BYTES, dtype=torch.uint8, device=self.device)
         self.n_jobs = torch.zeros(1, dtype=torch.int32, device=self.device)
-        self.tuning: tuple[int, int, int, int] = (THREADS_PER_KEY, 1, 4, 32)
+        self.tuning: tuple[int, int, int, int] = (THREADS_PER_KEY, 1, 2, 32)
         self.graph = None
         self._keep = []
 

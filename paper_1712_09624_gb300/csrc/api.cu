@@ -153,10 +153,12 @@ struct ckpp_batch {
   std::vector<ckpp_table*> tables;
   std::vector<TableView> host_views;  // kept alive for the copy to the device
   TableView* dev_views;
+  unsigned long long* ctrl;           // the lookup kernel's chunk and finished-warp counters
   int sms;
 };
 
-size_t ckpp_batch_bytes(uint32_t n_tables) { return align_up((size_t)n_tables * sizeof(TableView), kAlign); }
+// Descriptor buffer: the table views, then a 256-byte control block.
+size_t ckpp_batch_bytes(uint32_t n_tables) { return align_up((size_t)n_tables * sizeof(TableView), kAlign) + kAlign; }
 
 int ckpp_batch_create(ckpp_batch** out, ckpp_table* const* tables, uint32_t n_tables, void* dev_buf, size_t bytes,
                       ckpp_stream_t stream) {
@@ -171,6 +173,8 @@ int ckpp_batch_create(ckpp_batch** out, ckpp_table* const* tables, uint32_t n_ta
   b->host_views.resize(n_tables);
   for (uint32_t i = 0; i < n_tables; ++i) b->host_views[i] = tables[i]->view;
   b->dev_views = static_cast<TableView*>(dev_buf);
+  b->ctrl = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(dev_buf) +
+                                                  align_up((size_t)n_tables * sizeof(TableView), kAlign));
   int dev = 0;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -178,6 +182,7 @@ int ckpp_batch_create(ckpp_batch** out, ckpp_table* const* tables, uint32_t n_ta
       prepare_batched_lookup() != cudaSuccess ||
       cudaMemcpyAsync(b->dev_views, b->host_views.data(), n_tables * sizeof(TableView), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
+      cudaMemsetAsync(b->ctrl, 0, kAlign, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     delete b;
     return CKPP_ECUDA;
@@ -225,16 +230,16 @@ int ckpp_batch_delete(ckpp_batch* b, const ckpp_key* keys, const uint32_t* table
 int ckpp_batch_lookup(ckpp_batch* b, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,
                       uint32_t now, const ckpp_batch_tuning* tuning, ckpp_stream_t stream) {
   if (!b || max_jobs > kBatchMaxJobs || (max_jobs && !d_jobs)) return CKPP_EINVAL;
-  ckpp_batch_tuning tn = tuning ? *tuning : ckpp_batch_tuning{4, 1, 4, 32};
+  ckpp_batch_tuning tn = tuning ? *tuning : ckpp_batch_tuning{4, 1, 2, 32};
   const uint32_t T = tn.threads_per_key, G = tn.group_depth, P = tn.keys_per_warp ? tn.keys_per_warp : 32;
   if (T != 4 || !(G == 1 || G == 2) || !(P == 8 || P == 16 || P == 32) || tn.blocks_per_sm < 1 ||
-      tn.blocks_per_sm > 16)
+      tn.blocks_per_sm > 4)
     return CKPP_EINVAL;
   for (ckpp_table* t : b->tables)
     if (int rc = time_check(t, now)) return rc;
   if (!max_jobs) return CKPP_OK;
   return cuda_rc(launch_batched_lookup(b->dev_views, (uint32_t)b->tables.size(), d_jobs, d_n_jobs, max_jobs, now,
-                                       (int)T, (int)G, (int)P, tn.blocks_per_sm * (uint32_t)b->sms,
+                                       (int)T, (int)G, (int)P, tn.blocks_per_sm * (uint32_t)b->sms, b->ctrl,
                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 

@@ -5,11 +5,14 @@
 // Work list: a device array of jobs {keys, out_vals, out_found, n, table}; the
 // job count may live in device memory, so one captured CUDA graph can be
 // replayed while the caller rewrites jobs between replays. Every block scans
-// the job sizes into a prefix array in shared memory and then walks the flat
-// key range [0, total) in warp-sized chunks with a grid-stride loop; a key finds
-// its job by binary search in the prefix array, and the warp runs the
-// cooperative lookup of probe.cuh over keys of possibly different tables.
-//
+// the job sizes into a prefix array in shared memory; warps then take chunks
+// of the flat key range [0, total) from a counter in the batch descriptor, in
+// order (eight chunks per draw, so one counter can serve the whole grid), so that (as with a plain launch's short-lived blocks) the resident
+// warps read keys and write results within one narrow window of the batch. A
+// key finds its job by binary search in the prefix array, and the warp runs
+// the cooperative lookup of probe.cuh over keys of possibly different tables.
+// The last warp to finish resets the counter for the next launch, so
+// launches that use one batch descriptor must not overlap on the GPU.
 // Tuning (picked by the autotuner):
 //   threads per key  4: a key's 128-byte bucket line is fetched by 8 lanes of
 //                    16 bytes, four lines per warp instruction; fixed by the
@@ -33,7 +36,8 @@ struct BatchJob {  // layout of ckpp_lookup_job
 
 namespace {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 512;  // 16 warps share one copy of the job prefix array
+constexpr unsigned long long kChunksPerDraw = 8;
 
 // Exclusive prefix sums of the first nj job sizes into prefix[0..nj].
 __device__ void scan_jobs(const BatchJob* __restrict__ jobs, uint32_t nj, unsigned long long* prefix) {
@@ -138,18 +142,37 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
                                                                        uint32_t n_tables,
                                                                        const BatchJob* __restrict__ jobs,
                                                                        const uint32_t* __restrict__ n_jobs_ptr,
-                                                                       uint32_t max_jobs, uint32_t now, uint32_t kpw) {
+                                                                       uint32_t max_jobs, uint32_t now, uint32_t kpw,
+                                                                       unsigned long long* __restrict__ ctrl) {
   extern __shared__ __align__(128) unsigned long long prefix[];
   WarpStage<G>* stages = reinterpret_cast<WarpStage<G>*>(reinterpret_cast<uint8_t*>(prefix) + stage_offset_dev(max_jobs));
   const uint32_t nj = n_jobs_ptr ? min(ld32_cg(n_jobs_ptr), max_jobs) : max_jobs;
   scan_jobs(jobs, nj, prefix);
   const unsigned long long total = prefix[nj];
   const uint64_t pol = policy_evict_first();
-  const unsigned long long per_warp = (unsigned long long)kpw * G;
-  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-  for (unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       w * per_warp < total; w += warps) {
-    lookup_chunk<G>(tables, n_tables, jobs, prefix, nj, total, w * per_warp, kpw, now, pol, stages[threadIdx.x >> 5]);
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned long long per_chunk = (unsigned long long)kpw * G;
+  const unsigned long long chunks = (total + per_chunk - 1) / per_chunk;
+  for (;;) {
+    // kChunksPerDraw chunks per atomic: one counter word serves every warp of the grid
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(ctrl, 1ull) * kChunksPerDraw;
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= chunks) break;
+    const unsigned long long c_end = c + kChunksPerDraw < chunks ? c + kChunksPerDraw : chunks;
+    for (; c < c_end; ++c)
+      lookup_chunk<G>(tables, n_tables, jobs, prefix, nj, total, c * per_chunk, kpw, now, pol,
+                      stages[threadIdx.x >> 5]);
+  }
+  // Every warp has drawn past the last chunk before it counts itself out, so
+  // the last one out can reset the counters for the next launch.
+  if (lane == 0) {
+    unsigned int* out = reinterpret_cast<unsigned int*>(ctrl + 1);
+    const unsigned int warps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(out, 1u) == warps - 1) {
+      atomicExch(ctrl, 0ull);
+      atomicExch(out, 0u);
+    }
   }
 }
 
@@ -161,9 +184,10 @@ cudaError_t set_smem_limit() {
 
 template <int G>
 cudaError_t launch_g(const TableView* tables, uint32_t n_tables, const BatchJob* jobs, const uint32_t* n_jobs,
-                     uint32_t max_jobs, uint32_t now, uint32_t kpw, uint32_t blocks, cudaStream_t s) {
+                     uint32_t max_jobs, uint32_t now, uint32_t kpw, uint32_t blocks, unsigned long long* ctrl,
+                     cudaStream_t s) {
   batched_lookup_kernel<G><<<blocks, kBatchThreads, batched_smem<G>(max_jobs), s>>>(tables, n_tables, jobs, n_jobs,
-                                                                                   max_jobs, now, kpw);
+                                                                                   max_jobs, now, kpw, ctrl);
   return cudaGetLastError();
 }
 
@@ -177,14 +201,14 @@ cudaError_t prepare_batched_lookup() {
 
 cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, const void* jobs, const uint32_t* n_jobs,
                                   uint32_t max_jobs, uint32_t now, int threads_per_key, int group_depth,
-                                  int keys_per_warp, uint32_t blocks, cudaStream_t s) {
+                                  int keys_per_warp, uint32_t blocks, unsigned long long* ctrl, cudaStream_t s) {
   const BatchJob* j = static_cast<const BatchJob*>(jobs);
   if (threads_per_key != 4 || (keys_per_warp != 8 && keys_per_warp != 16 && keys_per_warp != 32))
     return cudaErrorInvalidValue;
   const uint32_t kpw = (uint32_t)keys_per_warp;
   switch (group_depth) {
-    case 1: return launch_g<1>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, s);
-    case 2: return launch_g<2>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, s);
+    case 1: return launch_g<1>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
+    case 2: return launch_g<2>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
     default: return cudaErrorInvalidValue;
   }
 }

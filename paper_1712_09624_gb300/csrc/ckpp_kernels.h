@@ -52,11 +52,12 @@ cudaError_t launch_probe_counts(const TableView& t, const uint8_t* keys, uint64_
                                 unsigned long long* counts, cudaStream_t s);
 
 // Batched form (batched.cu): tables [n_tables] in device memory, jobs a device
-// array of ckpp_lookup_job, n_jobs NULL or a device count (clamped to max_jobs).
+// array of ckpp_lookup_job, n_jobs NULL or a device count (clamped to max_jobs),
+// ctrl the descriptor's two zeroed counter words (chunk counter, warps done).
 cudaError_t prepare_batched_lookup();
 cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, const void* jobs, const uint32_t* n_jobs,
                                   uint32_t max_jobs, uint32_t now, int threads_per_key, int group_depth,
-                                  int keys_per_warp, uint32_t blocks, cudaStream_t s);
+                                  int keys_per_warp, uint32_t blocks, unsigned long long* ctrl, cudaStream_t s);
 
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws,
                          cudaStream_t s);

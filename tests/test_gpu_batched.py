@@ -84,7 +84,7 @@ def batch_setup():
     return BatchedLookup(tables, max_jobs=64), tables, qs
 
 
-@pytest.mark.parametrize("tuning", [(4, 1, 4, 32), (4, 2, 3, 32), (4, 2, 1, 8), (4, 1, 2, 16), (4, 1, 1, 8)])
+@pytest.mark.parametrize("tuning", [(4, 1, 2, 32), (4, 2, 1, 32), (4, 2, 2, 8), (4, 1, 3, 16), (4, 1, 1, 8)])
 def test_batched_equals_plain_per_table(batch_setup, tuning):
     batch, tables, qs = batch_setup
     ref = plain_results(tables, qs)
