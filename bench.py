@@ -655,7 +655,8 @@ def run_sweep(args):
 def run_random_read(args):
     """Random-read ceiling of this GPU: 2^26 independent reads of 32 or 64
     bytes at random aligned offsets of buffers from 64 MiB (L2-resident) to
-    8 GiB, timed with CUDA events."""
+    8 GiB, timed with CUDA events; then 2^26 random accesses of each request
+    shape of the line-read probe on a 4 GiB buffer."""
     import torch
 
     from paper_1712_09624_gb300 import workload_gpu as WG
@@ -681,9 +682,28 @@ def run_random_read(args):
             rows.append({"buffer_MiB": size >> 20, "unit_B": unit, "greads_per_s": round(n / sec / 1e9, 2),
                          "useful_GBs": round(n * unit / sec / 1e9, 1)})
     big = [r for r in rows if r["buffer_MiB"] == 8192 and r["unit_B"] == 32][0]
+    # request shapes on a 4 GiB buffer: what one random access costs
+    shapes = {0: "1 lane x 32 B", 1: "1 lane, 2 loads of 32 B (64 B)", 2: "4 lanes x 32 B, one 128 B line",
+              3: "8 lanes x 32 B, two lines (256 B)", 4: "32 B, then a dependent 32 B in the same line",
+              5: "as above, first load with the L2::128B prefetch hint",
+              6: "cp.async, 8 lanes x 16 B per line, 32 lines per warp"}
+    view = buf[:4 << 30]
+    lines = []
+    for mode, what in shapes.items():
+        for w in range(3):
+            WG.line_read(view, mode, n, w + 1, sink, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(10):
+            WG.line_read(view, mode, n, 100 + r, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / 10
+        lines.append({"mode": mode, "shape": what, "g_accesses_per_s": round(n / sec / 1e9, 2)})
     return {"metric": "random 32-byte reads per second (8 GiB buffer)", "value": big["greads_per_s"],
             "unit": "Greads/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": "random-read probe, 2^26 reads per launch"}, "rows": rows}
+            "config": {"workload": "random-read probe, 2^26 reads per launch"}, "rows": rows,
+            "request_shapes_4GiB": lines}
 
 
 def run_served(args):

@@ -47,6 +47,21 @@ int ckpp_wl_lookup_batch(uint64_t seed, uint64_t batch_id, uint64_t n, uint64_t 
 int ckpp_wl_random_read(const uint8_t* buf, uint64_t bytes, uint32_t unit, uint64_t n, uint64_t seed,
                         uint64_t* sink, ckpp_wl_stream_t stream);
 
+/* Line-read probe (measurement): n random accesses to buf (`bytes` a power of
+ * two >= 256, 256-byte aligned device memory), each of one shape (mode):
+ *   0  one lane reads 32 bytes;
+ *   1  one lane reads two adjacent 32-byte sectors with two loads;
+ *   2  4 lanes read the 4 sectors of one 128-byte line in one instruction;
+ *   3  8 lanes read two adjacent lines (256 bytes) in one instruction;
+ *   4  one lane reads 32 bytes, then (dependent on it) another sector of the
+ *      same line;
+ *   5  as 4, with the .L2::128B prefetch-size hint on the first load;
+ *   6  each warp copies 32 lines into shared memory with cp.async (8 lanes x
+ *      16 bytes per line, four lines per instruction).
+ * sink as for ckpp_wl_random_read. Returns 0, -1 (bad argument) or -2. */
+int ckpp_wl_line_read(const uint8_t* buf, uint64_t bytes, int mode, uint64_t n, uint64_t seed, uint64_t* sink,
+                      ckpp_wl_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

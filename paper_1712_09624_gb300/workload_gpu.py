@@ -27,6 +27,8 @@ def _load():
     L.ckpp_wl_keys_at.argtypes = [u64, vp, u64, vp, vp]
     L.ckpp_wl_random_read.restype = C.c_int
     L.ckpp_wl_random_read.argtypes = [vp, u64, C.c_uint32, u64, u64, vp, vp]
+    L.ckpp_wl_line_read.restype = C.c_int
+    L.ckpp_wl_line_read.argtypes = [vp, u64, C.c_int, u64, u64, vp, vp]
     return L
 
 
@@ -79,3 +81,10 @@ def random_read(buf: torch.Tensor, unit: int, n: int, seed: int, sink: torch.Ten
     rc = _lib.ckpp_wl_random_read(buf.data_ptr(), buf.numel(), unit, n, seed, sink.data_ptr(), _stream(stream))
     if rc:
         raise RuntimeError(f"ckpp_wl_random_read failed ({rc})")
+
+
+def line_read(buf: torch.Tensor, mode: int, n: int, seed: int, sink: torch.Tensor, stream=None):
+    """n random accesses of one request shape (see ckpp_wl_line_read)."""
+    rc = _lib.ckpp_wl_line_read(buf.data_ptr(), buf.numel(), mode, n, seed, sink.data_ptr(), _stream(stream))
+    if rc != 0:
+        raise RuntimeError(f"ckpp_wl_line_read failed ({rc})")
