@@ -154,6 +154,7 @@ struct ckpp_batch {
   std::vector<TableView> host_views;  // kept alive for the copy to the device
   TableView* dev_views;
   unsigned long long* ctrl;           // the lookup kernel's chunk and finished-warp counters
+  bool any_timers;                    // some table has timers
   int sms;
 };
 
@@ -171,7 +172,11 @@ int ckpp_batch_create(ckpp_batch** out, ckpp_table* const* tables, uint32_t n_ta
   if (!b) return CKPP_EINVAL;
   b->tables.assign(tables, tables + n_tables);
   b->host_views.resize(n_tables);
-  for (uint32_t i = 0; i < n_tables; ++i) b->host_views[i] = tables[i]->view;
+  b->any_timers = false;
+  for (uint32_t i = 0; i < n_tables; ++i) {
+    b->host_views[i] = tables[i]->view;
+    b->any_timers = b->any_timers || tables[i]->view.timers;
+  }
   b->dev_views = static_cast<TableView*>(dev_buf);
   b->ctrl = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(dev_buf) +
                                                   align_up((size_t)n_tables * sizeof(TableView), kAlign));
@@ -239,7 +244,8 @@ int ckpp_batch_lookup(ckpp_batch* b, const ckpp_lookup_job* d_jobs, uint32_t max
     if (int rc = time_check(t, now)) return rc;
   if (!max_jobs) return CKPP_OK;
   return cuda_rc(launch_batched_lookup(b->dev_views, (uint32_t)b->tables.size(), d_jobs, d_n_jobs, max_jobs, now,
-                                       (int)T, (int)G, (int)P, tn.blocks_per_sm * (uint32_t)b->sms, b->ctrl,
+                                       (int)T, (int)G, (int)P, b->any_timers, tn.blocks_per_sm * (uint32_t)b->sms,
+                                       b->ctrl,
                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 

@@ -86,7 +86,7 @@ __device__ __forceinline__ uint32_t find_job(const unsigned long long* prefix, u
 }
 
 // One warp iteration: lane l < kpw owns flat keys wbase + g * kpw + l, g < G.
-template <int G>
+template <int G, int kTM>
 __device__ __forceinline__ void lookup_chunk(const TableView* __restrict__ tables, uint32_t n_tables,
                                              const BatchJob* __restrict__ jobs, const unsigned long long* prefix,
                                              uint32_t nj, unsigned long long total, unsigned long long wbase,
@@ -115,7 +115,7 @@ __device__ __forceinline__ void lookup_chunk(const TableView* __restrict__ table
     }
     probe_init(p[g], k, tv.buckets, tv.nb, tv.seed, tv.timers);
   }
-  run_probes<kBloom, false, G>(p, act, now, S);
+  run_probes<kBloom, false, G, kTM>(p, act, now, S);
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     if (!act[g]) continue;
@@ -137,7 +137,8 @@ size_t batched_smem(uint32_t max_jobs) {
   return stage_offset(max_jobs) + (kBatchThreads / 32) * sizeof(WarpStage<G>);
 }
 
-template <int G>
+// kTM: kNoTimers when no table of the batch has timers, else kTimersPerKey.
+template <int G, int kTM>
 __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const TableView* __restrict__ tables,
                                                                        uint32_t n_tables,
                                                                        const BatchJob* __restrict__ jobs,
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
     if (c >= chunks) break;
     const unsigned long long c_end = c + kChunksPerDraw < chunks ? c + kChunksPerDraw : chunks;
     for (; c < c_end; ++c)
-      lookup_chunk<G>(tables, n_tables, jobs, prefix, nj, total, c * per_chunk, kpw, now, pol,
+      lookup_chunk<G, kTM>(tables, n_tables, jobs, prefix, nj, total, c * per_chunk, kpw, now, pol,
                       stages[threadIdx.x >> 5]);
   }
   // Every warp has drawn past the last chunk before it counts itself out, so
@@ -176,18 +177,18 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
   }
 }
 
-template <int G>
+template <int G, int kTM>
 cudaError_t set_smem_limit() {
-  return cudaFuncSetAttribute(batched_lookup_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(batched_lookup_kernel<G, kTM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)batched_smem<G>(kBatchMaxJobs));
 }
 
-template <int G>
+template <int G, int kTM>
 cudaError_t launch_g(const TableView* tables, uint32_t n_tables, const BatchJob* jobs, const uint32_t* n_jobs,
                      uint32_t max_jobs, uint32_t now, uint32_t kpw, uint32_t blocks, unsigned long long* ctrl,
                      cudaStream_t s) {
-  batched_lookup_kernel<G><<<blocks, kBatchThreads, batched_smem<G>(max_jobs), s>>>(tables, n_tables, jobs, n_jobs,
-                                                                                   max_jobs, now, kpw, ctrl);
+  batched_lookup_kernel<G, kTM><<<blocks, kBatchThreads, batched_smem<G>(max_jobs), s>>>(
+      tables, n_tables, jobs, n_jobs, max_jobs, now, kpw, ctrl);
   return cudaGetLastError();
 }
 
@@ -195,20 +196,25 @@ cudaError_t launch_g(const TableView* tables, uint32_t n_tables, const BatchJob*
 
 cudaError_t prepare_batched_lookup() {
   cudaError_t e;
-  if ((e = set_smem_limit<1>()) != cudaSuccess) return e;
-  return set_smem_limit<2>();
+  if ((e = set_smem_limit<1, kNoTimers>()) != cudaSuccess) return e;
+  if ((e = set_smem_limit<2, kNoTimers>()) != cudaSuccess) return e;
+  if ((e = set_smem_limit<1, kTimersPerKey>()) != cudaSuccess) return e;
+  return set_smem_limit<2, kTimersPerKey>();
 }
 
 cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, const void* jobs, const uint32_t* n_jobs,
                                   uint32_t max_jobs, uint32_t now, int threads_per_key, int group_depth,
-                                  int keys_per_warp, uint32_t blocks, unsigned long long* ctrl, cudaStream_t s) {
+                                  int keys_per_warp, bool any_timers, uint32_t blocks, unsigned long long* ctrl,
+                                  cudaStream_t s) {
   const BatchJob* j = static_cast<const BatchJob*>(jobs);
   if (threads_per_key != 4 || (keys_per_warp != 8 && keys_per_warp != 16 && keys_per_warp != 32))
     return cudaErrorInvalidValue;
   const uint32_t kpw = (uint32_t)keys_per_warp;
-  switch (group_depth) {
-    case 1: return launch_g<1>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
-    case 2: return launch_g<2>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
+  switch (group_depth * 2 + (any_timers ? 1 : 0)) {
+    case 2: return launch_g<1, kNoTimers>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
+    case 3: return launch_g<1, kTimersPerKey>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
+    case 4: return launch_g<2, kNoTimers>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
+    case 5: return launch_g<2, kTimersPerKey>(tables, n_tables, j, n_jobs, max_jobs, now, kpw, blocks, ctrl, s);
     default: return cudaErrorInvalidValue;
   }
 }

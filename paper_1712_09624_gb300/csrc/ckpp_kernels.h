@@ -57,7 +57,8 @@ cudaError_t launch_probe_counts(const TableView& t, const uint8_t* keys, uint64_
 cudaError_t prepare_batched_lookup();
 cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, const void* jobs, const uint32_t* n_jobs,
                                   uint32_t max_jobs, uint32_t now, int threads_per_key, int group_depth,
-                                  int keys_per_warp, uint32_t blocks, unsigned long long* ctrl, cudaStream_t s);
+                                  int keys_per_warp, bool any_timers, uint32_t blocks, unsigned long long* ctrl,
+                                  cudaStream_t s);
 
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws,
                          cudaStream_t s);

@@ -27,7 +27,7 @@ constexpr int kWarpsPerBlock = kLookupThreads / 32;
 // the link does worst) when the output pointers allow it.
 // kCount: no results; the secondary-line, record and second-line reads are
 // added to counts[1..3] and the keys to counts[0].
-template <bool kCount, bool kHostIO, int kVariant>
+template <bool kCount, bool kHostIO, int kVariant, int kTM>
 __global__ void __launch_bounds__(kLookupThreads) lookup_kernel(TableView t, const uint8_t* __restrict__ keys,
                                                                 uint64_t n, uint64_t* __restrict__ out_vals,
                                                                 uint8_t* __restrict__ out_found, uint32_t now,
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kLookupThreads) lookup_kernel(TableView t, con
   }
   Probe p[1];
   probe_init(p[0], k, t.buckets, t.nb, t.seed, t.timers);
-  run_probes<kVariant, kCount, 1>(p, act, now, stage[warp]);
+  run_probes<kVariant, kCount, 1, kTM>(p, act, now, stage[warp]);
   if (kCount) {
     const uint32_t nkey = __reduce_add_sync(kFull, act[0] ? 1u : 0u);
     const uint32_t nsec = __reduce_add_sync(kFull, p[0].nsec);
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kLookupThreads) lookup_kernel(TableView t, con
     return;
   }
   // Sec. 4.2: a hit may refresh the entry's expiry.
-  if (act[0] && t.timers && p[0].found && refresh_ttl) set_expiry(t, p[0].hb, p[0].hs, now + refresh_ttl);
+  if (kTM == kWithTimers && act[0] && p[0].found && refresh_ttl) set_expiry(t, p[0].hb, p[0].hs, now + refresh_ttl);
   const bool vec = kHostIO && (reinterpret_cast<uintptr_t>(out_vals) % 16 == 0) &&
                    (reinterpret_cast<uintptr_t>(out_found) % 16 == 0);
   if (vec && c * 32 + 32 <= n) {
@@ -90,8 +90,13 @@ template <bool kCount, bool kHostIO, int kVariant>
 cudaError_t launch(const TableView& t, const uint8_t* keys, uint64_t n, uint64_t* out_vals, uint8_t* out_found,
                    uint32_t now, uint32_t refresh_ttl, unsigned long long* counts, cudaStream_t s) {
   const uint64_t blocks = ((n + 31) / 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  lookup_kernel<kCount, kHostIO, kVariant><<<(unsigned)blocks, kLookupThreads, 0, s>>>(
-      t, keys, n, out_vals, out_found, now, t.timers ? refresh_ttl : 0u, counts);
+  if (t.timers) {
+    lookup_kernel<kCount, kHostIO, kVariant, kWithTimers><<<(unsigned)blocks, kLookupThreads, 0, s>>>(
+        t, keys, n, out_vals, out_found, now, refresh_ttl, counts);
+  } else {
+    lookup_kernel<kCount, kHostIO, kVariant, kNoTimers><<<(unsigned)blocks, kLookupThreads, 0, s>>>(
+        t, keys, n, out_vals, out_found, now, 0u, counts);
+  }
   return cudaGetLastError();
 }
 

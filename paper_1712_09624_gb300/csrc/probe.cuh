@@ -33,6 +33,10 @@ namespace ckpp {
 enum LookupVariant : int { kBloom = 0, kOptimistic = 1, kPessimistic = 2 };
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// Whether the keys' tables have timers: known for the whole launch (a plain
+// lookup is over one table) or per key (the batched form).
+enum TimersMode : int { kNoTimers = 0, kWithTimers = 1, kTimersPerKey = 2 };
 constexpr uint32_t kDone = 4;  // stages: 0 b1 line 0, 1 b1 line 1, 2 b2 line 0, 3 b2 line 1, 4 done
 
 // One key's lookup, owned by one lane.
@@ -120,12 +124,13 @@ __device__ __forceinline__ void resolve(Probe& p, bool found, uint64_t value, ui
 
 // The owner's examination of the line of its current stage (L: the line in the
 // warp's slab, sw: its chunk swizzle), and its next stage.
-template <int kVariant, bool kCount>
+template <int kVariant, bool kCount, int kTM>
 __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw, uint32_t now) {
-  if (p.skip) {  // pessimistic: a read made for its cost only
+  if (kVariant == kPessimistic && p.skip) {  // a read made for its cost only
     p.stage = kDone;
     return;
   }
+  const bool timers = kTM == kWithTimers || (kTM == kTimersPerKey && p.timers);
   auto chunk = [&](uint32_t c) { return L + 16u * (c ^ sw); };
   const uint32_t st = p.stage;
   const uint32_t b = st < 2 ? p.b1 : p.b2;
@@ -138,7 +143,7 @@ __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw,
       p.bloom_ok = (lo64(hd) & bits) == bits;
     }
     uint32_t alive8 = kBusyMask;
-    if (p.timers) {
+    if (timers) {
       const uint4 ex = lds128(chunk(6));
       alive8 = alive_mask(lo64(ex), hi64(ex), now);
     }
@@ -149,7 +154,7 @@ __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw,
       if (kCount) ++p.nrec;
       const uint4 kk = lds128(chunk(2 + s));
       if (lo64(kk) == p.k.k0 && hi64(kk) == p.k.k1) {
-        if (p.timers) {
+        if (timers) {
           if (!((alive8 >> s) & 1u)) {
             resolve<kVariant>(p, false, 0, b, s);  // Sec. 4.2: a dead entry is not returned
           } else {
@@ -169,7 +174,7 @@ __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw,
       return;
     }
   } else {  // second line: keys 4..7, then values
-    const uint32_t vs1 = (p.carry >> 8) & 7u;
+    const uint32_t vs1 = timers ? (p.carry >> 8) & 7u : 0u;
     if (vs1) {  // timers: fetch the value of a live slot 0..3
       const uint32_t s = vs1 - 1;
       resolve<kVariant>(p, true, lds64(chunk(4 + (s >> 1)) + 8 * (s & 1u)), b, s);
@@ -182,10 +187,10 @@ __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw,
       if (kCount) ++p.nrec;
       const uint4 kk = lds128(chunk(s4));
       if (lo64(kk) == p.k.k0 && hi64(kk) == p.k.k1) {
-        if (p.timers && !((p.carry >> (4 + s4)) & 1u)) {
+        if (timers && !((p.carry >> (4 + s4)) & 1u)) {
           resolve<kVariant>(p, false, 0, b, 4 + s4);
         } else {
-          const uint32_t vc = p.timers ? 6 + (s4 >> 1) : 4 + (s4 >> 1);
+          const uint32_t vc = timers ? 6 + (s4 >> 1) : 4 + (s4 >> 1);
           resolve<kVariant>(p, true, lds64(chunk(vc) + 8 * (s4 & 1u)), b, 4 + s4);
         }
         return;
@@ -238,7 +243,7 @@ __device__ __forceinline__ void fetch_lines(uint32_t nj, WarpStage<G>& S) {
 
 // Run the lookups of the warp's lanes until each is resolved. Every lane of
 // the warp must call this; lane l owns keys p[0..G) (act[g] false: no key).
-template <int kVariant, bool kCount, int G>
+template <int kVariant, bool kCount, int G, int kTM>
 __device__ __forceinline__ void run_probes(Probe (&p)[G], const bool (&act)[G], uint32_t now, WarpStage<G>& S) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t below = (1u << lane) - 1u;
@@ -260,7 +265,7 @@ __device__ __forceinline__ void run_probes(Probe (&p)[G], const bool (&act)[G], 
     fetch_lines(nj, S);
 #pragma unroll
     for (int g = 0; g < G; ++g)
-      if (rank[g] != 0xFFFFFFFFu) examine<kVariant, kCount>(p[g], S.line[rank[g]], rank[g] & 7u, now);
+      if (rank[g] != 0xFFFFFFFFu) examine<kVariant, kCount, kTM>(p[g], S.line[rank[g]], rank[g] & 7u, now);
     __syncwarp();
   }
 }
