@@ -134,9 +134,9 @@ int ckpp_create(ckpp_table** out, const ckpp_geometry* geometry, void* dev_buf, 
 int ckpp_destroy(ckpp_table* table);
 
 /* Batched lookup (Sec. 2, Sec. 4.1 and Fig. 4): for every key i, read the primary
- * bucket, compare tags, confirm the full key in the key/value array; on a miss
- * test the two Bloom bits of the primary's filter and read the secondary bucket
- * only if both are set. With timers dead entries are ignored (Sec. 4.2) and,
+ * bucket, compare tags, confirm the full key against the matching slot's key;
+ * on a miss test the two Bloom bits of the primary's filter and read the
+ * secondary bucket only if both are set. With timers dead entries are ignored (Sec. 4.2) and,
  * if refresh_ttl > 0, a hit sets the entry's expiry to now + refresh_ttl.
  *   keys      [n] ckpp_key, 16-byte aligned
  *   out_vals  [n] uint64, 8-byte aligned: the value, or 0 on a miss
