@@ -113,6 +113,12 @@ def alg_bytes_of(counts, n: int) -> float:
     return 32.0 * float(counts[0] + counts[1] + counts[2]) + 25.0 * n
 
 
+def line_bytes_of(counts, n: int) -> float:
+    """Bytes a lookup batch moves as whole 128-byte lines (one per line
+    request) plus its 16 bytes of key in and 9 of result out per lookup."""
+    return 128.0 * lines_of(counts) + 25.0 * n
+
+
 def lines_of(counts) -> float:
     """128-byte line requests a lookup batch makes: one per bucket read, plus
     one per second-line read."""
@@ -298,7 +304,11 @@ def run_ours(args, rank, world, local_rank):
                      "alg_bytes_per_lookup": round(alg_bytes / n, 3),
                      "reads_per_lookup": {"primary": float(counts[0] / n), "secondary": float(counts[1] / n),
                                           "record": float(counts[2] / n)},
-                     "line_requests_per_lookup": round(lines_of(counts) / n, 5)},
+                     "line_requests_per_lookup": round(lines_of(counts) / n, 5),
+                     "whole_lines": {"bytes_per_lookup": round(line_bytes_of(counts, n) / n, 2),
+                                     "frac": round(line_bytes_of(counts, n) / per_launch / 1e9 / peak, 4),
+                                     "note": "the bytes the kernel moves: 128 B per line request plus 25 B "
+                                             "of keys and results; frac above counts the method's bytes"}},
         "gpu_launches": args.steps,
     }
     if sampler:

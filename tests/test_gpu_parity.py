@@ -135,6 +135,49 @@ def test_probe_counts_with_timers():
         assert tuple(int(x) for x in c) == expected_probe_counts(d, q.keys, 0, now)
 
 
+@pytest.mark.parametrize("timers", [False, True])
+def test_tag_collisions_across_lines(timers):
+    """Keys that share their primary bucket and their 16-bit tag, so a tag match
+    is not a key match (Sec. 4.3): key A sits in slot 0 (the bucket's first
+    line), key B in slot 7 (its second line), key C is never inserted. Looking
+    up B examines A's slot first and must go on to the second line; C must
+    miss after examining both. Results equal the oracle's, and the read counts
+    equal the host replay on the downloaded table (B: 2 records, 1 second
+    line)."""
+    nb, seed, now = 512, 77, 20
+    keys = W.make_keys(seed, 90, 4_000_000)
+    a = oracle.address(keys, nb, seed)
+    cell = a["b1"].astype(np.int64) * 65536 + a["tag"].astype(np.int64)
+    order = np.argsort(cell, kind="stable")
+    cs = cell[order]
+    starts = np.flatnonzero(np.r_[True, cs[1:] != cs[:-1]])
+    counts = np.diff(np.r_[starts, cs.shape[0]])
+    i0 = starts[counts >= 3][0]
+    ia, ib, ic = order[i0:i0 + 3]
+    x = int(a["b1"][ia])
+    same = np.flatnonzero((a["b1"] == x) & (a["tag"] != a["tag"][ia]))[:6]
+    seq = [ia, *same, ib]  # inserted one by one: A takes slot 0, B slot 7
+    g = FT(nb, timers=timers, seed=seed)
+    o = oracle.Table(nb, 8, timers, seed)
+    for j, i in enumerate(seq):
+        kk, vv = keys[i:i + 1], np.array([1000 + j], np.uint64)
+        gs = g.insert(kk, vv, now=10, ttl=500 if timers else 0).cpu().numpy()
+        assert (gs == o.insert(kk, vv, 10, 500 if timers else 0)).all()
+    d = download(g)
+    assert d.check() == []
+    slot_of = {d.rec_key[x * 8 + s].tobytes(): s for s in range(8) if d.busy[x, s]}
+    assert slot_of[keys[ia].tobytes()] == 0 and slot_of[keys[ib].tobytes()] == 7
+    q = np.concatenate([keys[[ib, ia, ic]], keys[same], W.make_keys(seed, 91, 1000)])
+    gv, gf = g.lookup(q, now=now)
+    ov, of = o.lookup(q, now)
+    assert (gf.cpu().numpy() == of).all() and (np_vals(gv) == ov).all()
+    assert list(of[:3]) == [1, 1, 0]
+    c = g.probe_counts(q[:1], now=now).cpu().numpy()
+    assert tuple(int(v) for v in c) == (1, 0, 2, 1)
+    c = g.probe_counts(q, now=now).cpu().numpy()
+    assert tuple(int(v) for v in c) == expected_probe_counts(d, q, 0, now)
+
+
 # ----------------------------------------------------- mutation streams
 
 def run_stream(seed, nb, timers, n_batches, max_batch, pool_factor, max_lf=0.9):
