@@ -178,12 +178,6 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   return p;
 }
 
-// 256-bit read-only load (data not written during the kernel), L1 bypassed.
-__device__ __forceinline__ void ld256_ro(const void* p, uint64_t pol, uint64_t (&w)[4]) {
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0,%1,%2,%3}, [%4], %5;"
-               : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3])
-               : "l"(p), "l"(pol));
-}
 // 128-bit read-only streaming load.
 __device__ __forceinline__ Key ld_key_ro(const void* p, uint64_t pol) {
   Key k;

@@ -24,27 +24,39 @@ __global__ void init_header_kernel(uint8_t* base, uint64_t nb, uint32_t slots, u
 __global__ void __launch_bounds__(256) expire_kernel(TableView t, uint32_t now, unsigned long long* n_expired) {
   uint32_t count = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t bb = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; bb < t.nb; bb += stride) {
-    const uint32_t b = (uint32_t)bb;
-    const uint32_t ctrl = ld32_cg(ctrl_ptr(t, b));
-    const uint32_t busy = ctrl & kBusyMask;
-    if (!busy) continue;
-    uint64_t e0, e1;
-    ld128_cg(expiry_ptr(t, b, 0), e0, e1);
-    const uint32_t dead = busy & ~alive_mask(e0, e1, now);
-    if (!dead) continue;
-    uint32_t displaced = (ctrl >> kInsecShift) & dead;
-    while (displaced) {
-      const int s = __ffs(displaced) - 1;
-      displaced &= displaced - 1;
-      Key k;
-      ld128_cg(key_ptr(t, b, s), k.k0, k.k1);
-      const Addr a = address_of(k, t.nb, t.seed);
-      if (atomicSub(moved_ptr(t, a.b1), 1u) == 1u)
-        atomicExch(reinterpret_cast<unsigned long long*>(bloom_ptr(t, a.b1)), 0ull);
+  // Two buckets per thread per step, both buckets' words loaded before either
+  // is examined: twice the reads in flight for this streaming pass.
+  for (uint64_t bb = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; bb < t.nb; bb += 2 * stride) {
+    uint32_t bk[2], ctrl[2];
+    uint64_t e0[2] = {0, 0}, e1[2] = {0, 0};
+    bool have[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint64_t b = bb + u * stride;
+      have[u] = b < t.nb;
+      bk[u] = have[u] ? (uint32_t)b : 0u;
+      ctrl[u] = have[u] ? ld32_cg(ctrl_ptr(t, bk[u])) : 0u;
+      if (have[u] && t.timers) ld128_cg(expiry_ptr(t, bk[u], 0), e0[u], e1[u]);
     }
-    atomicAnd(ctrl_ptr(t, b), ~(dead | (dead << kInsecShift)));
-    count += __popc(dead);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint32_t b = bk[u];
+      const uint32_t busy = ctrl[u] & kBusyMask;
+      const uint32_t dead = busy & ~alive_mask(e0[u], e1[u], now);
+      if (!have[u] || !t.timers || !dead) continue;
+      uint32_t displaced = (ctrl[u] >> kInsecShift) & dead;
+      while (displaced) {
+        const int s = __ffs(displaced) - 1;
+        displaced &= displaced - 1;
+        Key k;
+        ld128_cg(key_ptr(t, b, s), k.k0, k.k1);
+        const Addr a = address_of(k, t.nb, t.seed);
+        if (atomicSub(moved_ptr(t, a.b1), 1u) == 1u)
+          atomicExch(reinterpret_cast<unsigned long long*>(bloom_ptr(t, a.b1)), 0ull);
+      }
+      atomicAnd(ctrl_ptr(t, b), ~(dead | (dead << kInsecShift)));
+      count += __popc(dead);
+    }
   }
   count = __reduce_add_sync(0xFFFFFFFFu, count);
   if ((threadIdx.x & 31) == 0 && count && n_expired) atomicAdd(n_expired, (unsigned long long)count);
