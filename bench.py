@@ -81,6 +81,9 @@ def parse():
 
 # ------------------------------------------------------------------ helpers
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e datasheet figure, reported beside the measured copy peak
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -305,6 +308,8 @@ def run_ours(args, rank, world, local_rank):
                      "reads_per_lookup": {"primary": float(counts[0] / n), "secondary": float(counts[1] / n),
                                           "record": float(counts[2] / n)},
                      "line_requests_per_lookup": round(lines_of(counts) / n, 5),
+                     "nominal_peak_GBs": NOMINAL_HBM_GBS,
+                     "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "whole_lines": {"bytes_per_lookup": round(line_bytes_of(counts, n) / n, 2),
                                      "frac": round(line_bytes_of(counts, n) / per_launch / 1e9 / peak, 4),
                                      "note": "the bytes the kernel moves: 128 B per line request plus 25 B "

@@ -104,9 +104,9 @@ typedef struct ckpp_stats {
  * invalid): a 256-byte header, then n_buckets buckets of 256 bytes. A bucket
  * is two 128-byte lines. Line 0 holds the fields a lookup reads first (8
  * 16-bit tags, the 64-bit filter, the busy / in_secondary / lock word and the
- * moved counter; Sec. 4.1, 4.3) with the keys of slots 0..3 and either their
- * values or, with CKPP_TIMERS, the 8 16-bit expiries (Sec. 4.2). Line 1 holds
- * the keys of slots 4..7 and the remaining values. The keys and values of a
+ * moved counter; Sec. 4.1, 4.3) with the keys and values of slots 0..3, or,
+ * with CKPP_TIMERS, of slots 0..2 and the 8 16-bit expiries (Sec. 4.2). Line 1
+ * holds the keys and values of the other slots. The keys and values of a
  * bucket's slots thus sit in the bucket itself rather than in a separate array
  * at the implicit index of Sec. 4.3: a random access costs one 128-byte line
  * on this GPU, whatever part of the line it uses. */

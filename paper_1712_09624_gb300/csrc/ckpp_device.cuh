@@ -18,15 +18,18 @@
 //   16..23   bloom      64-bit filter of this bucket's displaced keys (Sec. 4.1)
 //   24..27   ctrl       bits 0-7 busy, bits 8-15 in_secondary, bit 31 insert lock
 //   28..31   moved      moved counter (Sec. 4.1)
-//   32..95   key[0..3]  16 bytes each
-//   96..127  value[0..3] (u64 each)          -- tables without timers
-//            expiry[8] (u16 each, 96..111), then 16 zero bytes -- with timers
+//   tables without timers:          tables with timers (Sec. 4.2):
+//   32..95   key[0..3]              32..79   key[0..2]
+//   96..127  value[0..3]            80..95   value[0..1]
+//                                   96..111  expiry[8] (u16 each)
+//                                   112..119 value[2], then 8 zero bytes
 // Line 1, bytes [128, 256):
-//   128..191 key[4..7]
-//   192..223 value[4..7], then 32 zero bytes  -- tables without timers
-//   192..255 value[0..7]                      -- with timers (Sec. 4.2)
-// With timers the expiries sit beside the fields a scan or an insertion
-// decides on (line 0), and every value moves to line 1.
+//   128..191 key[4..7]              128..207 key[3..7]
+//   192..223 value[4..7], then      208..247 value[3..7], then 8 zero bytes
+//            32 zero bytes
+// With timers the expiries sit beside the control word, so an expire scan or
+// an insertion decides from the first line, and a key found in slots 0..2 is
+// confirmed, tested alive and answered from the first line alone.
 #pragma once
 
 #include <cstdint>
@@ -154,13 +157,19 @@ __device__ __forceinline__ uint32_t* moved_ptr(const TableView& t, uint32_t b) {
 __device__ __forceinline__ uint16_t* tag_ptr(const TableView& t, uint32_t b, uint32_t s) {
   return reinterpret_cast<uint16_t*>(bucket_ptr(t, b)) + s;
 }
+// The first slot whose entry lives in the second line.
+__host__ __device__ constexpr uint32_t first_hi_slot(uint32_t timers) { return timers ? 3u : 4u; }
 // Byte offsets of a slot's key, value and expiry within its bucket.
-__device__ __forceinline__ uint32_t key_off(uint32_t s) { return 32u + 16u * s + (s >= 4 ? 32u : 0u); }
+__device__ __forceinline__ uint32_t key_off(uint32_t timers, uint32_t s) {
+  const uint32_t h = first_hi_slot(timers);
+  return s < h ? 32u + 16u * s : kLineBytes + 16u * (s - h);
+}
 __device__ __forceinline__ uint32_t value_off(uint32_t timers, uint32_t s) {
-  return timers ? 192u + 8u * s : 96u + 8u * s + (s >= 4 ? 64u : 0u);
+  if (timers) return s < 2 ? 80u + 8u * s : s == 2 ? 112u : 208u + 8u * (s - 3);
+  return s < 4 ? 96u + 8u * s : 192u + 8u * (s - 4);
 }
 __device__ __forceinline__ uint8_t* key_ptr(const TableView& t, uint32_t b, uint32_t s) {
-  return bucket_ptr(t, b) + key_off(s);
+  return bucket_ptr(t, b) + key_off(t.timers, s);
 }
 __device__ __forceinline__ uint64_t* value_ptr(const TableView& t, uint32_t b, uint32_t s) {
   return reinterpret_cast<uint64_t*>(bucket_ptr(t, b) + value_off(t.timers, s));

@@ -2,9 +2,9 @@
 // run over the 256-byte bucket layout of ckpp_device.cuh.
 //
 // Per key: two hashes; the primary bucket's first line (tags, filter, busy
-// mask and the entries of slots 0..3); its second line only if a tag of slots
-// 4..7 matches (or, with timers, for the value); after a primary miss, the
-// secondary bucket in the same way.
+// mask and the entries of the first slots); its second line only if a tag of
+// the other slots matches; after a primary miss, the secondary bucket in the
+// same way.
 //
 // How a line is read: a random access costs one 128-byte line request whether
 // it brings 32 bytes or the whole line, but only if the line's sectors are
@@ -47,7 +47,7 @@ struct Probe {
   uint32_t bidx;    // the two filter bit indices: i1 | i2 << 6
   uint32_t timers;  // the table has timers
   uint32_t stage;
-  uint32_t carry;   // for a line-1 job: cand4 | alive4 << 4 | (value slot + 1) << 8
+  uint32_t carry;   // for a second-line job: its tag-matching slots | alive mask << 8
   bool bloom_ok;    // both filter bits of the primary are set
   bool skip;        // pessimistic: the key is resolved; the read is made for its cost only
   bool found;
@@ -123,7 +123,9 @@ __device__ __forceinline__ void resolve(Probe& p, bool found, uint64_t value, ui
 }
 
 // The owner's examination of the line of its current stage (L: the line in the
-// warp's slab, sw: its chunk swizzle), and its next stage.
+// warp's slab, sw: its chunk swizzle), and its next stage. A slot's key and
+// value sit at key_off / value_off of ckpp_device.cuh: slots below
+// first_hi_slot in the first line, the others in the second.
 template <int kVariant, bool kCount, int kTM>
 __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw, uint32_t now) {
   if (kVariant == kPessimistic && p.skip) {  // a read made for its cost only
@@ -132,9 +134,13 @@ __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw,
   }
   const bool timers = kTM == kWithTimers || (kTM == kTimersPerKey && p.timers);
   auto chunk = [&](uint32_t c) { return L + 16u * (c ^ sw); };
+  auto at = [&](uint32_t byte) { return chunk(byte >> 4) + (byte & 15u); };  // byte offset within the line
   const uint32_t st = p.stage;
   const uint32_t b = st < 2 ? p.b1 : p.b2;
-  if (!(st & 1u)) {  // a bucket's first line: header, keys 0..3, values 0..3 or expiries
+  const uint32_t lo = (1u << first_hi_slot(timers)) - 1u;  // slots of the first line
+  const uint32_t base = (st & 1u) ? kLineBytes : 0u;       // this line's first byte in the bucket
+  uint32_t cand, alive8;
+  if (!(st & 1u)) {  // a bucket's first line: header, then the first slots' entries and the expiries
     const uint4 tg = lds128(chunk(0));
     const uint4 hd = lds128(chunk(1));
     const uint32_t m8 = tag_mask16(tg, p.tag) & hd.z & kBusyMask;
@@ -142,60 +148,34 @@ __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw,
       const uint64_t bits = (1ull << (p.bidx & 63u)) | (1ull << (p.bidx >> 6));
       p.bloom_ok = (lo64(hd) & bits) == bits;
     }
-    uint32_t alive8 = kBusyMask;
+    alive8 = kBusyMask;
     if (timers) {
       const uint4 ex = lds128(chunk(6));
       alive8 = alive_mask(lo64(ex), hi64(ex), now);
     }
-    uint32_t cand = m8 & 0xFu;
-    while (cand) {
-      const uint32_t s = __ffs(cand) - 1;
-      cand &= cand - 1;
-      if (kCount) ++p.nrec;
-      const uint4 kk = lds128(chunk(2 + s));
-      if (lo64(kk) == p.k.k0 && hi64(kk) == p.k.k1) {
-        if (timers) {
-          if (!((alive8 >> s) & 1u)) {
-            resolve<kVariant>(p, false, 0, b, s);  // Sec. 4.2: a dead entry is not returned
-          } else {
-            p.stage = st + 1;  // the value sits in the second line
-            p.carry = (s + 1) << 8;
-          }
-        } else {
-          resolve<kVariant>(p, true, lds64(chunk(6 + (s >> 1)) + 8 * (s & 1u)), b, s);
-        }
-        return;
+    cand = m8 & lo;
+    p.carry = (m8 & ~lo) | alive8 << 8;  // for the second line, if it is needed
+  } else {
+    cand = p.carry & 0xFFu;
+    alive8 = p.carry >> 8;
+  }
+  while (cand) {
+    const uint32_t s = __ffs(cand) - 1;
+    cand &= cand - 1;
+    if (kCount) ++p.nrec;
+    const uint4 kk = lds128(at(key_off(timers, s) - base));
+    if (lo64(kk) == p.k.k0 && hi64(kk) == p.k.k1) {
+      if (timers && !((alive8 >> s) & 1u)) {
+        resolve<kVariant>(p, false, 0, b, s);  // Sec. 4.2: a dead entry is not returned
+      } else {
+        resolve<kVariant>(p, true, lds64(at(value_off(timers, s) - base)), b, s);
       }
-    }
-    const uint32_t c4 = m8 >> 4;
-    if (c4) {
-      p.stage = st + 1;
-      p.carry = c4 | (alive8 >> 4) << 4;
       return;
     }
-  } else {  // second line: keys 4..7, then values
-    const uint32_t vs1 = timers ? (p.carry >> 8) & 7u : 0u;
-    if (vs1) {  // timers: fetch the value of a live slot 0..3
-      const uint32_t s = vs1 - 1;
-      resolve<kVariant>(p, true, lds64(chunk(4 + (s >> 1)) + 8 * (s & 1u)), b, s);
-      return;
-    }
-    uint32_t cand = p.carry & 0xFu;
-    while (cand) {
-      const uint32_t s4 = __ffs(cand) - 1;
-      cand &= cand - 1;
-      if (kCount) ++p.nrec;
-      const uint4 kk = lds128(chunk(s4));
-      if (lo64(kk) == p.k.k0 && hi64(kk) == p.k.k1) {
-        if (timers && !((p.carry >> (4 + s4)) & 1u)) {
-          resolve<kVariant>(p, false, 0, b, 4 + s4);
-        } else {
-          const uint32_t vc = timers ? 6 + (s4 >> 1) : 4 + (s4 >> 1);
-          resolve<kVariant>(p, true, lds64(chunk(vc) + 8 * (s4 & 1u)), b, 4 + s4);
-        }
-        return;
-      }
-    }
+  }
+  if (!(st & 1u) && (p.carry & 0xFFu)) {  // tag matches in the second line
+    p.stage = st + 1;
+    return;
   }
   // the bucket does not hold the key
   if (st < 2 && (kVariant != kBloom || p.bloom_ok)) {

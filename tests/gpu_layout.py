@@ -17,26 +17,34 @@ SLOTS = 8
 BUCKET = 256
 
 
-def key_offsets() -> np.ndarray:
-    """Byte offset of each slot's key in a bucket: slots 0-3 in line 0 after
-    the 32-byte header, slots 4-7 at the start of line 1."""
+def first_hi_slot(timers: bool) -> int:
+    """The first slot whose entry lives in the bucket's second line."""
+    return 3 if timers else 4
+
+
+def key_offsets(timers: bool) -> np.ndarray:
+    """Byte offset of each slot's key in a bucket: the first slots in line 0
+    after the 32-byte header, the others from the start of line 1."""
+    h = first_hi_slot(timers)
     s = np.arange(SLOTS)
-    return 32 + 16 * s + np.where(s >= 4, 32, 0)
+    return np.where(s < h, 32 + 16 * s, 128 + 16 * (s - h))
 
 
 def value_offsets(timers: bool) -> np.ndarray:
-    """Byte offset of each slot's value: without timers, values 0-3 end line 0
-    and values 4-7 follow keys 4-7; with timers all eight fill the end of
-    line 1."""
+    """Byte offset of each slot's value. Without timers: values 0-3 end line 0,
+    values 4-7 follow keys 4-7. With timers: values 0-1 follow keys 0-2, value 2
+    follows the expiries, values 3-7 follow keys 3-7."""
     s = np.arange(SLOTS)
-    return 192 + 8 * s if timers else 96 + 8 * s + np.where(s >= 4, 64, 0)
+    if timers:
+        return np.where(s < 2, 80 + 8 * s, np.where(s == 2, 112, 208 + 8 * (s - 3)))
+    return np.where(s < 4, 96 + 8 * s, 192 + 8 * (s - 4))
 
 
-EXPIRY_OFF = 96  # timers: expiry[8] in line 0 after keys 0-3
+EXPIRY_OFF = 96  # timers: expiry[8] in line 0
 
 
 def reserved_ranges(timers: bool) -> list[tuple[int, int]]:
-    return [(112, 128)] if timers else [(224, 256)]
+    return [(120, 128), (248, 256)] if timers else [(224, 256)]
 
 
 class Decoded:
@@ -56,7 +64,7 @@ class Decoded:
         else:
             self.expiry = np.zeros((n_buckets, 8), np.uint16)
         self.bucket_reserved = np.concatenate([bk[:, a:b] for a, b in reserved_ranges(timers)], axis=1)
-        ko = key_offsets()
+        ko = key_offsets(timers)
         keys = np.stack([bk[:, o:o + 16] for o in ko], axis=1)  # [nb, 8, 16]
         self.rec_key = np.ascontiguousarray(keys.reshape(n_buckets * SLOTS, 16))
         vo = value_offsets(timers)
@@ -142,6 +150,8 @@ def oracle_live(t: "oracle.Table", now: int) -> dict:
 
 def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int,
                           now: int = 0) -> tuple[int, int, int, int]:
+    # `now` does not change the counts: a key met in a dead entry ends the
+    # search like a live one (Sec. 4.2), and no read depends on liveness.
     """(keys, secondary-bucket reads, record reads, second-line reads) that a
     lookup of ``keys`` with strategy ``variant`` (0 Bloom, 1 optimistic,
     2 pessimistic) makes on the decoded table: candidates are busy slots whose
@@ -149,14 +159,13 @@ def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int,
     secondary is read after a primary miss when both filter bits are set
     (Bloom, Sec. 4.1), after every primary miss (optimistic) or always
     (pessimistic, Sec. 3). A bucket's second line is read when the key is not
-    among slots 0-3 and a tag of slots 4-7 matches, or, with timers, to fetch
-    the value of a live entry found in slots 0-3; a pessimistic read of the
-    secondary after a primary hit reads its first line only."""
+    among the first line's slots and a tag of the second line's slots matches;
+    a pessimistic read of the secondary after a primary hit reads its first
+    line only."""
     a = oracle.address(keys, d.nb, d.seed)
     kv = np.ascontiguousarray(keys).view(np.dtype((np.void, 16))).reshape(-1)
     rk = np.ascontiguousarray(d.rec_key).view(np.dtype((np.void, 16))).reshape(-1)
     slots = np.arange(SLOTS)
-    alive = d.alive(now)
 
     def bucket_reads(b):
         cand = (d.tags[b] == a["tag"][:, None]) & d.busy[b]
@@ -164,9 +173,8 @@ def expected_probe_counts(d: Decoded, keys: np.ndarray, variant: int,
         found = hit.any(axis=1)
         first = np.where(found, hit.argmax(axis=1), SLOTS)
         upto = cand & (slots[None, :] <= first[:, None])
-        low_hit = found & (first < 4)
-        hit_alive = alive[b, np.minimum(first, SLOTS - 1)]
-        line1 = np.where(low_hit, d.timers & hit_alive, cand[:, 4:].any(axis=1))
+        h = first_hi_slot(d.timers)
+        line1 = ~(found & (first < h)) & cand[:, h:].any(axis=1)
         return found, upto.sum(axis=1), line1
 
     f1, r1, l1 = bucket_reads(a["b1"].astype(np.int64))
@@ -201,7 +209,7 @@ def encode_oracle(t: "oracle.Table") -> np.ndarray:
     bk[:, 28:32] = moved.view(np.uint8).reshape(nb, 4)
     ctrl = np.zeros(nb, np.uint32)
     a = oracle.address(d["key"], nb, t.seed)
-    ko, vo = key_offsets(), value_offsets(timers)
+    ko, vo = key_offsets(timers), value_offsets(timers)
     for i in range(d["value"].shape[0]):
         b, s = int(d["bucket"][i]), int(d["slot"][i])
         ctrl[b] |= np.uint32(1 << s) | np.uint32(int(d["in_secondary"][i]) << (8 + s))

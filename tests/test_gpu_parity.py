@@ -119,9 +119,9 @@ def test_probe_counts_match_method():
 
 
 def test_probe_counts_with_timers():
-    """With timers every value sits in line 1, so a live entry found in slots
-    0-3 costs a second line read and a dead one does not; the counting kernel
-    agrees with the replay at a time when part of the table has expired."""
+    """With timers the first line holds slots 0-2 (and the expiries), the
+    second slots 3-7; the counting kernel agrees with the replay at a time
+    when part of the table has expired."""
     nb = 1 << 12
     f = W.fill(4, int(0.9 * nb * 8))
     g = FT(nb, timers=True, seed=4)
@@ -139,7 +139,8 @@ def test_probe_counts_with_timers():
 def test_tag_collisions_across_lines(timers):
     """Keys that share their primary bucket and their 16-bit tag, so a tag match
     is not a key match (Sec. 4.3): key A sits in slot 0 (the bucket's first
-    line), key B in slot 7 (its second line), key C is never inserted. Looking
+    line), key B in slot 7 (its second line, with or without timers), key C is
+    never inserted. Looking
     up B examines A's slot first and must go on to the second line; C must
     miss after examining both. Results equal the oracle's, and the read counts
     equal the host replay on the downloaded table (B: 2 records, 1 second

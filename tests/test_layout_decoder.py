@@ -26,7 +26,7 @@ def test_decoder_round_trip_and_read_counts():
         assert sec < sec_opt < sec_pes == n
         assert rec <= rec_opt == rec_pes
         assert l1 <= l1_opt == l1_pes
-        # without timers a second line is read only for a tag match in slots 4-7
+        # a second line is read only for a tag match among the second line's slots
         assert 0 < l1 < n
 
 
