@@ -7,7 +7,7 @@
 // replayed while the caller rewrites jobs between replays. Every block scans
 // the job sizes into a prefix array in shared memory; warps then take chunks
 // of the flat key range [0, total) from a counter in the batch descriptor, in
-// order (eight chunks per draw, so one counter can serve the whole grid), so that (as with a plain launch's short-lived blocks) the resident
+// order (up to eight chunks per draw, so one counter can serve the whole grid), so that (as with a plain launch's short-lived blocks) the resident
 // warps read keys and write results within one narrow window of the batch. A
 // key finds its job by binary search in the prefix array, and the warp runs
 // the cooperative lookup of probe.cuh over keys of possibly different tables.
@@ -37,7 +37,7 @@ struct BatchJob {  // layout of ckpp_lookup_job
 namespace {
 
 constexpr int kBatchThreads = 512;  // 16 warps share one copy of the job prefix array
-constexpr unsigned long long kChunksPerDraw = 8;
+constexpr unsigned long long kMaxChunksPerDraw = 8;
 
 // Exclusive prefix sums of the first nj job sizes into prefix[0..nj].
 __device__ void scan_jobs(const BatchJob* __restrict__ jobs, uint32_t nj, unsigned long long* prefix) {
@@ -154,13 +154,18 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
   const uint32_t lane = threadIdx.x & 31;
   const unsigned long long per_chunk = (unsigned long long)kpw * G;
   const unsigned long long chunks = (total + per_chunk - 1) / per_chunk;
+  // Chunks per atomic draw: up to kMaxChunksPerDraw on large launches (one
+  // counter word serves every warp of the grid), fewer on small ones, so that
+  // every warp gets about four draws rather than a few warps all the work.
+  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  unsigned long long per_draw = chunks / (4 * warps);
+  per_draw = per_draw < 1 ? 1 : (per_draw > kMaxChunksPerDraw ? kMaxChunksPerDraw : per_draw);
   for (;;) {
-    // kChunksPerDraw chunks per atomic: one counter word serves every warp of the grid
     unsigned long long c = 0;
-    if (lane == 0) c = atomicAdd(ctrl, 1ull) * kChunksPerDraw;
+    if (lane == 0) c = atomicAdd(ctrl, 1ull) * per_draw;
     c = __shfl_sync(kFull, c, 0);
     if (c >= chunks) break;
-    const unsigned long long c_end = c + kChunksPerDraw < chunks ? c + kChunksPerDraw : chunks;
+    const unsigned long long c_end = c + per_draw < chunks ? c + per_draw : chunks;
     for (; c < c_end; ++c)
       lookup_chunk<G, kTM>(tables, n_tables, jobs, prefix, nj, total, c * per_chunk, kpw, now, pol,
                       stages[threadIdx.x >> 5]);
@@ -169,8 +174,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
   // the last one out can reset the counters for the next launch.
   if (lane == 0) {
     unsigned int* out = reinterpret_cast<unsigned int*>(ctrl + 1);
-    const unsigned int warps = gridDim.x * (blockDim.x >> 5);
-    if (atomicAdd(out, 1u) == warps - 1) {
+    if (atomicAdd(out, 1u) == (unsigned int)(warps - 1)) {
       atomicExch(ctrl, 0ull);
       atomicExch(out, 0u);
     }

@@ -202,19 +202,10 @@ class Service:
                         fit = 1  # a burst larger than the budget goes alone
                     hi = nxt + fit
                     sel = slice(nxt, hi)
-                    ev_start = torch.cuda.Event(enable_timing=True)
-                    ev_start.record(cuda)
                     ins = st.insert[sel]
-                    if ins.any():  # the admitted inserts form one contiguous range of the insert pool
-                        first = int(st.offset[sel][ins][0])
-                        n_ins = int(st.size[sel][ins].sum())
-                        lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
-                                              self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
-                                              n_ins, 0, 0, self.ins_status[first:].data_ptr(),
-                                              self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
-                        launches += 1
                     look = ~ins
                     nj = int(look.sum())
+                    # the turn's host work comes first, so that its launches go out back to back
                     if nj:
                         if ring_event[slot] is not None:
                             ring_event[slot].synchronize()  # the copy that last read this buffer is done
@@ -226,6 +217,17 @@ class Service:
                         view["out_found"][:nj] = pool_found[tb] + off
                         view["n"][:nj] = st.size[sel][look]
                         view["table"][:nj] = tb
+                    ev_start = torch.cuda.Event(enable_timing=True)
+                    ev_start.record(cuda)
+                    if ins.any():  # the admitted inserts form one contiguous range of the insert pool
+                        first = int(st.offset[sel][ins][0])
+                        n_ins = int(st.size[sel][ins].sum())
+                        lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
+                                              self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
+                                              n_ins, 0, 0, self.ins_status[first:].data_ptr(),
+                                              self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
+                        launches += 1
+                    if nj:
                         nbytes_jobs = nj * K.JOB_BYTES
                         self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
                         # the job count is known here: the prefix scan is sized to it (no device count)
