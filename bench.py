@@ -16,6 +16,8 @@ One JSON line on rank 0. Beside the headline `value` it reports:
              library's probe-count kernel, plus 25 B of key/result streaming)
              over its measured duration, against the measured HBM copy peak;
   pos / neg  the same measurement on all-positive and all-negative batches;
+  at_100M_entries  the same measurement on the same table when the fill stands at exactly
+             100,000,000 entries (LF 0.745);
   mutations  bulk_insert / bulk_delete / expire throughput on the same table;
   cpu_baseline  the CPU oracle's lookup rate on a bounded sample (rank 0, N=1).
 
@@ -206,6 +208,38 @@ class ClockSampler:
 
 # ------------------------------------------------------------- our arm
 
+def lookup_side(args, K, W, table, fill, m, n, seed, dev, stream, steps=20, warmup=3):
+    """Lookups on the table as it stands with the first m fill keys inserted:
+    a checked, timed n-key batch (negative rate as the headline) drawn from
+    those keys, with its algorithmic bytes and line requests."""
+    import torch
+    sub = W.FillWorkload(fill.keys[:m], fill.values[:m])
+    q = W.lookup_batch(seed, n, sub, args.neg_rate, batch_id=100)
+    kk = torch.from_numpy(q.keys).to(dev)
+    ov = torch.empty(n, dtype=torch.int64, device=dev)
+    of = torch.empty(n, dtype=torch.bool, device=dev)
+    K.ckpp_bulk_lookup(table.handle, kk, ov, of, 0, 0, stream)
+    torch.cuda.synchronize()
+    exact = bool((of.cpu().numpy() == q.expect_found).all()) and \
+        bool((ov.cpu().numpy().view(np.uint64) == q.expect_value).all())
+    c = table.probe_counts(kk).cpu().numpy()
+    for _ in range(warmup):
+        K.ckpp_bulk_lookup(table.handle, kk, ov, of, 0, 0, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        K.ckpp_bulk_lookup(table.handle, kk, ov, of, 0, 0, stream)
+    e1.record(stream)
+    e1.synchronize()
+    per = e0.elapsed_time(e1) / 1e3 / steps
+    peak, _ = measured_peaks()
+    return {"entries": m, "load_factor": round(m / (8 * table.n_buckets), 4), "value": round(n / per / 1e9, 4),
+            "unit": UNIT, "neg_rate": args.neg_rate, "exact": exact,
+            "alg_bytes_per_lookup": round(alg_bytes_of(c, n) / n, 3),
+            "frac": round(alg_bytes_of(c, n) / per / 1e9 / peak, 4),
+            "line_requests_per_lookup": round(lines_of(c) / n, 5)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -226,9 +260,15 @@ def run_ours(args, rank, world, local_rank):
     table = FlowTable(nb, timers=False, seed=seed, device=dev)
     chunk = 1 << 24
     ins_times = []
-    for lo in range(0, n_fill, chunk):
-        k = torch.from_numpy(fill.keys[lo:lo + chunk]).to(dev)
-        v = torch.from_numpy(fill.values[lo:lo + chunk].view(np.int64)).to(dev)
+    # the fill stops once at exactly 100,000,000 entries (LF 0.745 on 2^27 slots) for a side measurement
+    stop_100m = 100_000_000 if (rank == 0 and not args.no_side and n_fill > 100_000_000) else None
+    bounds = sorted(set(list(range(0, n_fill, chunk)) + ([stop_100m] if stop_100m else [])) | {n_fill})
+    at_100m = None
+    for lo, hi in zip(bounds[:-1], bounds[1:]):
+        if lo == stop_100m:
+            at_100m = lookup_side(args, K, W, table, fill, lo, n, seed, dev, stream)
+        k = torch.from_numpy(fill.keys[lo:hi]).to(dev)
+        v = torch.from_numpy(fill.values[lo:hi].view(np.int64)).to(dev)
         st = torch.empty(k.shape[0], dtype=torch.uint8, device=dev)
         ws = table.workspace(k.shape[0])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -331,6 +371,8 @@ def run_ours(args, rank, world, local_rank):
                           "line_requests_per_lookup": round(lines_of(c) / n, 5),
                           "frac": round(b / (s / max(10, args.steps // 4)) / 1e9 / peak, 4)}
         out.update(side)
+        if at_100m:
+            out["at_100M_entries"] = at_100m
         out["e2e"] = e2e_lookup(args, table, q, dev, stream)
         out["mutations"] = mutation_rates(table, dev, stream, ins_times, seed)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
