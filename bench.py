@@ -77,6 +77,10 @@ def parse():
     p.add_argument("--mixed-batches", type=int, default=400, help="mixed: batches (time units) to run")
     p.add_argument("--serve-seconds", type=float, default=0.2, help="served: seconds of offered traffic")
     p.add_argument("--serve-modes", default="batched,plain", help="served: arms to run")
+    p.add_argument("--serve-flush-keys", type=int, default=None,
+                   help="served: coalesced inserts go out once this many keys wait (default: the loop's own)")
+    p.add_argument("--serve-flush-us", type=float, default=None,
+                   help="served: ... or once the oldest waiting insert burst is this old")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
     return p.parse_args()
 
@@ -811,6 +815,10 @@ def run_served(args):
     from paper_1712_09624_gb300.serve import ServeConfig, Service
     torch.cuda.set_device(0)
     cfg = ServeConfig(duration_s=args.serve_seconds, seed=args.seed)
+    if args.serve_flush_keys is not None:
+        cfg.insert_flush_keys = args.serve_flush_keys
+    if args.serve_flush_us is not None:
+        cfg.insert_flush_s = args.serve_flush_us * 1e-6
     out = {}
     for mode in args.serve_modes.split(","):
         svc = Service(cfg)
@@ -824,7 +832,8 @@ def run_served(args):
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "served form: 64 ports, Poisson bursts of 32..4096 keys, 2 G lookups/s offered, "
                                    "256 tables / 500M slots, 10% inserts", "duration_s": cfg.duration_s,
-                       "footprint_budget_bytes": cfg.footprint_bytes},
+                       "footprint_budget_bytes": cfg.footprint_bytes, "insert_flush_keys": cfg.insert_flush_keys,
+                       "insert_flush_us": round(cfg.insert_flush_s * 1e6, 1)},
             "batched": b, "plain_per_burst": out.get("plain")}
 
 

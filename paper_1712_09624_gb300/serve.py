@@ -10,9 +10,12 @@ new flows. The loop runs in real time on the host:
   staging footprint (keys in, results out) of work in flight stays within an
   HBM budget; a burst that does not fit waits for the next turn;
 * it launches the admitted work without waiting for the previous launch: the
-  admitted inserts as one multi-table ``ckpp_batch_insert`` and the admitted
-  lookups as one persistent ``ckpp_batch_lookup`` (one job per burst), both
-  on one stream, so the next launch is queued while the current one runs.
+  admitted lookups as one persistent ``ckpp_batch_lookup`` (one job per burst)
+  every turn, and the admitted inserts coalesced into one multi-table
+  ``ckpp_batch_insert`` once enough keys wait or the oldest has waited long
+  enough (an insert call has a fixed cost of several dependent kernels, so
+  coalescing writes keeps that cost from every turn); both on one stream, so
+  the next launch is queued while the current one runs.
 
 Lookups read flows of the warm fill (and unknown flows); inserts add new
 flows. Lookup results therefore do not depend on how bursts are grouped, and
@@ -54,6 +57,8 @@ class ServeConfig:
     neg_rate: float = 0.2
     duration_s: float = 0.2
     footprint_bytes: int = 256 << 20
+    insert_flush_keys: int = 32768    # coalesced inserts go out once this many keys wait ...
+    insert_flush_s: float = 300e-6    # ... or the oldest has waited this long
     seed: int = 7
 
 
@@ -90,6 +95,13 @@ def draw_stream(cfg: ServeConfig) -> Stream:
         s = size[sel]
         offset[sel] = np.cumsum(s) - s
     return Stream(arrival, table, size, insert, offset)
+
+
+def percentiles(lat: np.ndarray) -> dict | None:
+    if lat.size == 0:
+        return None
+    return {"p50": round(float(np.percentile(lat, 50)), 1), "p99": round(float(np.percentile(lat, 99)), 1),
+            "p99_9": round(float(np.percentile(lat, 99.9)), 1), "max": round(float(lat.max()), 1)}
 
 
 class Service:
@@ -147,9 +159,11 @@ class Service:
         n_bursts = st.arrival.shape[0]
         done_at = np.full(n_bursts, np.nan)
         foot = st.size.astype(np.int64) * KEY_BYTES_IO
-        in_flight = deque()  # (event, first, last, bytes)
+        in_flight = deque()  # (event, bursts it completes, bytes)
         flight_bytes = 0
         nxt = 0
+        pend = []  # admitted insert bursts not yet launched (contiguous in the insert pool)
+        pend_keys = 0
         lib = K.library()
         job_dtype = np.dtype([("keys", "<u8"), ("out_vals", "<u8"), ("out_found", "<u8"), ("n", "<u4"),
                               ("table", "<u4")])
@@ -163,7 +177,7 @@ class Service:
         pool_found = np.array([p["found"].data_ptr() for p in self.pools], np.uint64)
         handles = [t.handle for t in self.tables]
         ws_small = torch.empty(K.ckpp_workspace_bytes(cfg.max_burst), dtype=torch.uint8, device=dev)
-        launches = 0
+        launches = flushes = 0
         starts, groups, gpu_busy = [], [], []
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -173,9 +187,9 @@ class Service:
         def retire(block: bool):
             nonlocal flight_bytes
             while in_flight and (block or in_flight[0][0].query()):
-                ev, a, b, nbytes = in_flight.popleft()
+                ev, idx, nbytes = in_flight.popleft()
                 ev.synchronize()
-                done_at[a:b] = ev_time(ev)
+                done_at[idx] = ev_time(ev)
                 flight_bytes -= nbytes
                 if starts:
                     gpu_busy.append(starts.pop(0).elapsed_time(ev) / 1e3)
@@ -185,84 +199,109 @@ class Service:
             return e0.elapsed_time(ev) / 1e3
 
         sh = cuda.cuda_stream
-        while nxt < n_bursts or in_flight:
+        while nxt < n_bursts or in_flight or pend:
             retire(False)
             now = time.perf_counter() - t0
-            if nxt < n_bursts and st.arrival[nxt] <= now:
-                hi = int(np.searchsorted(st.arrival, now, side="right"))
-                if mode == "batched":
+            arrived = nxt < n_bursts and st.arrival[nxt] <= now
+            if mode == "batched":
+                flush_due = bool(pend) and (pend_keys >= cfg.insert_flush_keys or nxt >= n_bursts or
+                                            now - st.arrival[pend[0]] >= cfg.insert_flush_s)
+                if not arrived and not flush_due:
+                    if not in_flight:
+                        wake = st.arrival[nxt] if nxt < n_bursts else now
+                        if pend:
+                            wake = min(wake, st.arrival[pend[0]] + cfg.insert_flush_s)
+                        time.sleep(max(0.0, min(50e-6, wake - now)))
+                    continue
+                sel = slice(nxt, nxt)
+                if arrived:
+                    hi = int(np.searchsorted(st.arrival, now, side="right"))
                     hi = min(hi, nxt + K.BATCH_MAX_JOBS)
                     room = cfg.footprint_bytes - flight_bytes
                     cum = np.cumsum(foot[nxt:hi])
                     fit = int(np.searchsorted(cum, room, side="right"))
                     if fit == 0:
-                        if in_flight:
+                        if pend:
+                            flush_due = True  # waiting inserts hold the budget: send them
+                        elif in_flight:
                             retire(True)
                             continue
-                        fit = 1  # a burst larger than the budget goes alone
-                    hi = nxt + fit
-                    sel = slice(nxt, hi)
-                    ins = st.insert[sel]
-                    look = ~ins
-                    nj = int(look.sum())
-                    # the turn's host work comes first, so that its launches go out back to back
-                    if nj:
-                        if ring_event[slot] is not None:
-                            ring_event[slot].synchronize()  # the copy that last read this buffer is done
-                        view = ring_views[slot]
-                        tb = st.table[sel][look]
-                        off = st.offset[sel][look].astype(np.uint64)
-                        view["keys"][:nj] = pool_keys[tb] + off * np.uint64(16)
-                        view["out_vals"][:nj] = pool_vals[tb] + off * np.uint64(8)
-                        view["out_found"][:nj] = pool_found[tb] + off
-                        view["n"][:nj] = st.size[sel][look]
-                        view["table"][:nj] = tb
-                    ev_start = torch.cuda.Event(enable_timing=True)
-                    ev_start.record(cuda)
-                    if ins.any():  # the admitted inserts form one contiguous range of the insert pool
-                        first = int(st.offset[sel][ins][0])
-                        n_ins = int(st.size[sel][ins].sum())
-                        lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
-                                              self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
-                                              n_ins, 0, 0, self.ins_status[first:].data_ptr(),
-                                              self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
-                        launches += 1
-                    if nj:
-                        nbytes_jobs = nj * K.JOB_BYTES
-                        self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
-                        # the job count is known here: the prefix scan is sized to it (no device count)
-                        K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs, nj, None, 0, self.batch.tuning, cuda)
-                        launches += 1
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(cuda)
-                    if nj:
-                        ring_event[slot] = ev
-                        slot = (slot + 1) % len(ring)
-                    nbytes = int(cum[fit - 1])
-                    in_flight.append((ev, nxt, hi, nbytes))
-                    starts.append(ev_start)
-                    groups.append(hi - nxt)
-                    flight_bytes += nbytes
-                    nxt = hi
-                else:  # plain: one launch per burst, as it arrives
-                    for b in range(nxt, hi):
-                        t = int(st.table[b])
-                        n = int(st.size[b])
-                        off = int(st.offset[b])
-                        if st.insert[b]:
-                            lib.ckpp_bulk_insert(handles[t], self.ins_keys[off:].data_ptr(),
-                                                 self.ins_vals[off:].data_ptr(), n, 0, 0,
-                                                 self.ins_status[off:].data_ptr(), ws_small.data_ptr(),
-                                                 ws_small.numel(), sh)
                         else:
-                            p = self.pools[t]
-                            lib.ckpp_bulk_lookup(handles[t], p["keys"][off:].data_ptr(), n, p["vals"][off:].data_ptr(),
-                                                 p["found"][off:].data_ptr(), 0, 0, sh)
-                        launches += 1
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(cuda)
-                    in_flight.append((ev, nxt, hi, 0))
-                    nxt = hi
+                            fit = 1  # a burst larger than the budget goes alone
+                    sel = slice(nxt, nxt + fit)
+                    flight_bytes += int(foot[sel].sum())
+                ins = st.insert[sel]
+                look_idx = np.arange(sel.start, sel.stop)[~ins]
+                for b in np.arange(sel.start, sel.stop)[ins]:
+                    pend.append(int(b))
+                    pend_keys += int(st.size[b])
+                flush = bool(pend) and (flush_due or pend_keys >= cfg.insert_flush_keys or sel.stop >= n_bursts or
+                                        now - st.arrival[pend[0]] >= cfg.insert_flush_s)
+                nj = look_idx.shape[0]
+                if not nj and not flush:
+                    nxt = sel.stop
+                    continue
+                # the turn's host work comes first, so that its launches go out back to back
+                if nj:
+                    if ring_event[slot] is not None:
+                        ring_event[slot].synchronize()  # the copy that last read this buffer is done
+                    view = ring_views[slot]
+                    tb = st.table[look_idx]
+                    off = st.offset[look_idx].astype(np.uint64)
+                    view["keys"][:nj] = pool_keys[tb] + off * np.uint64(16)
+                    view["out_vals"][:nj] = pool_vals[tb] + off * np.uint64(8)
+                    view["out_found"][:nj] = pool_found[tb] + off
+                    view["n"][:nj] = st.size[look_idx]
+                    view["table"][:nj] = tb
+                done = list(look_idx)
+                ev_start = torch.cuda.Event(enable_timing=True)
+                ev_start.record(cuda)
+                if flush:  # the pending inserts form one contiguous range of the insert pool
+                    first = int(st.offset[pend[0]])
+                    lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
+                                          self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
+                                          pend_keys, 0, 0, self.ins_status[first:].data_ptr(),
+                                          self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
+                    launches += 1
+                    flushes += 1
+                    done += pend
+                    pend, pend_keys = [], 0
+                if nj:
+                    nbytes_jobs = nj * K.JOB_BYTES
+                    self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
+                    # the job count is known here: the prefix scan is sized to it (no device count)
+                    K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs, nj, None, 0, self.batch.tuning, cuda)
+                    launches += 1
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(cuda)
+                if nj:
+                    ring_event[slot] = ev
+                    slot = (slot + 1) % len(ring)
+                done = np.asarray(done, dtype=np.int64)
+                in_flight.append((ev, done, int(foot[done].sum())))
+                starts.append(ev_start)
+                groups.append(sel.stop - sel.start)
+                nxt = sel.stop
+            elif arrived:  # plain: one launch per burst, as it arrives
+                hi = int(np.searchsorted(st.arrival, now, side="right"))
+                for b in range(nxt, hi):
+                    t = int(st.table[b])
+                    n = int(st.size[b])
+                    off = int(st.offset[b])
+                    if st.insert[b]:
+                        lib.ckpp_bulk_insert(handles[t], self.ins_keys[off:].data_ptr(),
+                                             self.ins_vals[off:].data_ptr(), n, 0, 0,
+                                             self.ins_status[off:].data_ptr(), ws_small.data_ptr(),
+                                             ws_small.numel(), sh)
+                    else:
+                        p = self.pools[t]
+                        lib.ckpp_bulk_lookup(handles[t], p["keys"][off:].data_ptr(), n, p["vals"][off:].data_ptr(),
+                                             p["found"][off:].data_ptr(), 0, 0, sh)
+                    launches += 1
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(cuda)
+                in_flight.append((ev, np.arange(nxt, hi), 0))
+                nxt = hi
             elif not in_flight and nxt < n_bursts:
                 time.sleep(max(0.0, min(50e-6, st.arrival[nxt] - now)))
         retire(True)
@@ -280,10 +319,10 @@ class Service:
             "bursts_per_group": round(float(np.mean(groups)), 1) if groups else None,
             "gpu_busy_fraction": round(float(np.sum(gpu_busy)) / wall, 3) if gpu_busy else None,
             "gpu_ms_per_group": round(float(np.mean(gpu_busy)) * 1e3, 4) if gpu_busy else None,
-            "latency_us": {"p50": round(float(np.percentile(lat[keep], 50)), 1),
-                           "p99": round(float(np.percentile(lat[keep], 99)), 1),
-                           "p99_9": round(float(np.percentile(lat[keep], 99.9)), 1),
-                           "max": round(float(lat[keep].max()), 1)},
+            "latency_us": percentiles(lat[keep]),
+            "lookup_latency_us": percentiles(lat[keep & lk]),
+            "insert_latency_us": percentiles(lat[keep & st.insert]),
+            "insert_flushes": flushes if mode == "batched" else None,
         }
 
     def check(self) -> dict:
