@@ -7,7 +7,8 @@
 // replayed while the caller rewrites jobs between replays. Every block scans
 // the job sizes into a prefix array in shared memory; warps then take chunks
 // of the flat key range [0, total) from a counter in the batch descriptor, in
-// order (up to eight chunks per draw, so one counter can serve the whole grid), so that (as with a plain launch's short-lived blocks) the resident
+// order (up to eight chunks per draw, so one counter can serve the whole
+// grid), so that (as with a plain launch's short-lived blocks) the resident
 // warps read keys and write results within one narrow window of the batch. A
 // key finds its job by binary search in the prefix array, and the warp runs
 // the cooperative lookup of probe.cuh over keys of possibly different tables.
@@ -127,10 +128,9 @@ __device__ __forceinline__ void lookup_chunk(const TableView* __restrict__ table
 
 // Dynamic shared memory: the job prefix array, then one line slab per warp
 // (128-byte aligned).
-__device__ __forceinline__ size_t stage_offset_dev(uint32_t max_jobs) {
+__host__ __device__ __forceinline__ size_t stage_offset(uint32_t max_jobs) {
   return ((size_t)(max_jobs + 1) * sizeof(unsigned long long) + 127) & ~(size_t)127;
 }
-size_t stage_offset(uint32_t max_jobs) { return ((size_t)(max_jobs + 1) * sizeof(unsigned long long) + 127) & ~(size_t)127; }
 
 template <int G>
 size_t batched_smem(uint32_t max_jobs) {
@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
                                                                        uint32_t max_jobs, uint32_t now, uint32_t kpw,
                                                                        unsigned long long* __restrict__ ctrl) {
   extern __shared__ __align__(128) unsigned long long prefix[];
-  WarpStage<G>* stages = reinterpret_cast<WarpStage<G>*>(reinterpret_cast<uint8_t*>(prefix) + stage_offset_dev(max_jobs));
+  WarpStage<G>* stages =
+      reinterpret_cast<WarpStage<G>*>(reinterpret_cast<uint8_t*>(prefix) + stage_offset(max_jobs));
   const uint32_t nj = n_jobs_ptr ? min(ld32_cg(n_jobs_ptr), max_jobs) : max_jobs;
   scan_jobs(jobs, nj, prefix);
   const unsigned long long total = prefix[nj];

@@ -60,6 +60,10 @@ cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, co
                                   int keys_per_warp, bool any_timers, uint32_t blocks, unsigned long long* ctrl,
                                   cudaStream_t s);
 
+// Resets a carved workspace for a new batch: counter_words counters to 0, the
+// dedup set's set_first words to empty and set_last words to 0 (one launch).
+cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, cudaStream_t s);
+
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws,
                          cudaStream_t s);
 

@@ -23,11 +23,11 @@
 //             those locks; retry a bounded number of times. Keys still
 //             unplaced get a wider search by 8 single-warp blocks, then the
 //             widest by 16 single-thread blocks; only then FULL.
-//   fixup   - reset the filter of buckets whose moved counter reached zero off
-//             their lock (the reset of Sec. 4.1, deferred so that it never races
-//             a concurrent setter).
-//   finish  - non-leader occurrences copy their leader's outcome (UPDATED, or
-//             FULL/BUSY).
+//   fixup and finish (one kernel) - reset the filter of buckets whose moved
+//             counter reached zero off their lock (the reset of Sec. 4.1,
+//             deferred so that it never races a concurrent setter); non-leader
+//             occurrences copy their leader's outcome (UPDATED, or FULL/BUSY).
+// Before them, one kernel clears the workspace (counters and the dedup set).
 #include "mutate.cuh"
 
 namespace ckpp {
@@ -562,33 +562,46 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
 }
 
 // ----------------------------------------------------- fixup and finish
-__global__ void bloom_fixup(TableSet ts, Workspace ws) {
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+// The two parts touch disjoint words (filters of the fixup list's buckets;
+// status bytes of non-leader keys), so one launch runs both: every thread
+// takes its share of the fixup list, and thread i < n finishes key i.
+__global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uint64_t n, uint8_t* __restrict__ status,
+                                                                Workspace ws) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (ld32_cg(ws.counters + 2)) {  // the list overflowed: scan every bucket of every table
     for (uint32_t tb = 0; tb < ts.n_tables; ++tb) {
       const TableView t = ts.table(tb);
-      for (uint64_t b = tid; b < t.nb; b += stride)
+      for (uint64_t b = i; b < t.nb; b += stride)
         if (ld32_cg(moved_ptr(t, (uint32_t)b)) == 0u) st64_cg(bloom_ptr(t, (uint32_t)b), 0ull);
     }
   } else {
     const uint32_t count = min(ld32_cg(ws.counters + 1), ws.fix_cap);
-    for (uint32_t j = tid; j < count; j += stride) {
+    for (uint64_t j = i; j < count; j += stride) {
       const unsigned long long e = ws.fixup[j];
       const TableView t = ts.table((uint32_t)(e >> 32));
       const uint32_t b = (uint32_t)e;
       if (ld32_cg(moved_ptr(t, b)) == 0u) st64_cg(bloom_ptr(t, b), 0ull);
     }
   }
-}
-
-__global__ void __launch_bounds__(kThreads) insert_finish(uint64_t n, uint8_t* __restrict__ status, Workspace ws) {
-  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t leader = ws.set_first[ws.slot_of[i]];
   if (leader == (uint32_t)i) return;
   const uint8_t st = status[leader];
   status[i] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;  // FULL, BUSY, NO_TABLE copy through
+}
+
+// ------------------------------------------------------- workspace reset
+__global__ void __launch_bounds__(kThreads) workspace_clear(uint32_t* __restrict__ counters, uint32_t counter_words,
+                                                            uint4* __restrict__ first, uint4* __restrict__ last,
+                                                            uint64_t m4) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (tid < counter_words) counters[tid] = 0u;
+  for (uint64_t j = tid; j < m4; j += stride) {
+    first[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+    last[j] = make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) delete_kernel(TableSet ts, const uint8_t* __restrict__ keys, uint64_t n,
@@ -638,6 +651,17 @@ unsigned grid_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1)
 
 }  // namespace
 
+cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, cudaStream_t s) {
+  // m is a power of two >= 64 and the set arrays are 256-byte aligned, so
+  // they clear as whole 16-byte vectors
+  const uint64_t m4 = ((uint64_t)ws.m_mask + 1) / 4;
+  const uint64_t want = (m4 > counter_words ? m4 : counter_words);
+  const uint64_t blocks = (want + kThreads - 1) / kThreads;
+  workspace_clear<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), kThreads, 0, s>>>(
+      ws.counters, counter_words, reinterpret_cast<uint4*>(ws.set_first), reinterpret_cast<uint4*>(ws.set_last), m4);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws, cudaStream_t s) {
   dedup_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(keys, n, ts, ws);
   return cudaGetLastError();
@@ -668,9 +692,8 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
   insert_phase2<1, 2048, 6><<<kLastPassBlocks, 1, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.retry,
                                                           ws.counters + 6, nullptr, nullptr, kLastPassKeys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bloom_fixup<<<152 * 2, 256, 0, s>>>(ts, ws);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  insert_finish<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, status, ws);
+  const unsigned fin_blocks = grid_for(n, kThreads);
+  insert_fixup_finish<<<fin_blocks > 152 * 2 ? fin_blocks : 152 * 2, kThreads, 0, s>>>(ts, n, status, ws);
   return cudaGetLastError();
 }
 
