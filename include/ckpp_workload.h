@@ -62,6 +62,16 @@ int ckpp_wl_random_read(const uint8_t* buf, uint64_t bytes, uint32_t unit, uint6
 int ckpp_wl_line_read(const uint8_t* buf, uint64_t bytes, int mode, uint64_t n, uint64_t seed, uint64_t* sink,
                       ckpp_wl_stream_t stream);
 
+/* Host-link probe (measurement): the host I/O of a lookup on host buffers,
+ * without a table. keys [n][16] (16-byte aligned), out_vals [n] (8-byte
+ * aligned) and out_found [n] may be pinned host or device memory; for each i,
+ * with k0, k1 the key's two little-endian 64-bit words, out_vals[i] =
+ * k0 ^ (k1 << 1) and out_found[i] = k1 & 1. Each lane reads one key and each
+ * warp writes its 32 results as 16-byte vectors when both outputs are 16-byte
+ * aligned. Returns 0, -1 (bad argument) or -2. */
+int ckpp_wl_host_io(const uint8_t* keys, uint64_t n, uint64_t* out_vals, uint8_t* out_found,
+                    ckpp_wl_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

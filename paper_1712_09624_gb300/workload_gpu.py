@@ -29,6 +29,8 @@ def _load():
     L.ckpp_wl_random_read.argtypes = [vp, u64, C.c_uint32, u64, u64, vp, vp]
     L.ckpp_wl_line_read.restype = C.c_int
     L.ckpp_wl_line_read.argtypes = [vp, u64, C.c_int, u64, u64, vp, vp]
+    L.ckpp_wl_host_io.restype = C.c_int
+    L.ckpp_wl_host_io.argtypes = [vp, u64, vp, vp, vp]
     return L
 
 
@@ -88,3 +90,14 @@ def line_read(buf: torch.Tensor, mode: int, n: int, seed: int, sink: torch.Tenso
     rc = _lib.ckpp_wl_line_read(buf.data_ptr(), buf.numel(), mode, n, seed, sink.data_ptr(), _stream(stream))
     if rc != 0:
         raise RuntimeError(f"ckpp_wl_line_read failed ({rc})")
+
+
+def host_io(keys: torch.Tensor, out_vals: torch.Tensor, out_found: torch.Tensor, stream=None):
+    """The host I/O of a lookup without the table (see ckpp_wl_host_io): keys
+    [n, 16] uint8, out_vals [n] int64, out_found [n] uint8 or bool, each pinned
+    host or device memory."""
+    n = keys.shape[0]
+    rc = _lib.ckpp_wl_host_io(keys.data_ptr() if n else None, n, out_vals.data_ptr() if n else None,
+                              out_found.data_ptr() if n else None, _stream(stream))
+    if rc != 0:
+        raise RuntimeError(f"ckpp_wl_host_io failed ({rc})")

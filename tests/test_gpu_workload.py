@@ -35,3 +35,27 @@ def test_keys_at_match_host():
     k = WG.keys_at(9, torch.from_numpy(idx).cuda())
     ref = W.fill(9, 1001).keys[idx]
     assert (k.cpu().numpy() == ref).all()
+
+
+@pytest.mark.parametrize("n,host,offset", [(1, True, 0), (4099, True, 0), (4096, False, 0), (1000, True, 1)])
+def test_host_io_probe_outputs(n, host, offset):
+    """The host-link probe writes k0 ^ (k1 << 1) and k1 & 1 for every key,
+    through the vector path (aligned outputs) and the per-lane path (outputs
+    offset by one element, and the ragged last warp)."""
+    import torch
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    keys_np = W.make_keys(31, 5, n)
+    words = keys_np.view(np.uint64).reshape(n, 2)
+    want_v = words[:, 0] ^ (words[:, 1] << np.uint64(1))
+    want_f = (words[:, 1] & np.uint64(1)).astype(np.uint8)
+    keys = torch.from_numpy(keys_np)
+    vals = torch.zeros(n + offset, dtype=torch.int64)
+    found = torch.full((n + offset,), 7, dtype=torch.uint8)
+    if host:
+        keys, vals, found = keys.pin_memory(), vals.pin_memory(), found.pin_memory()
+    else:
+        keys, vals, found = keys.cuda(), vals.cuda(), found.cuda()
+    WG.host_io(keys, vals[offset:], found[offset:])
+    torch.cuda.synchronize()
+    assert (vals[offset:].cpu().numpy().view(np.uint64) == want_v).all()
+    assert (found[offset:].cpu().numpy() == want_f).all()
