@@ -42,7 +42,7 @@ extern "C" {
 /* cudaStream_t without including the CUDA runtime headers. */
 typedef struct CUstream_st* ckpp_stream_t;
 
-#define CKPP_ABI_VERSION 2
+#define CKPP_ABI_VERSION 3
 
 /* return codes */
 #define CKPP_OK 0

@@ -19,17 +19,17 @@
 //   24..27   ctrl       bits 0-7 busy, bits 8-15 in_secondary, bit 31 insert lock
 //   28..31   moved      moved counter (Sec. 4.1)
 //   tables without timers:          tables with timers (Sec. 4.2):
-//   32..95   key[0..3]              32..79   key[0..2]
-//   96..127  value[0..3]            80..95   value[0..1]
-//                                   96..111  expiry[8] (u16 each)
-//                                   112..119 value[2], then 8 zero bytes
+//   32..95   key[0..3]              32..47   expiry[8] (u16 each)
+//   96..127  value[0..3]            48..95   key[0..2]
+//                                   96..119  value[0..2], then 8 zero bytes
 // Line 1, bytes [128, 256):
 //   128..191 key[4..7]              128..207 key[3..7]
 //   192..223 value[4..7], then      208..247 value[3..7], then 8 zero bytes
 //            32 zero bytes
-// With timers the expiries sit beside the control word, so an expire scan or
-// an insertion decides from the first line, and a key found in slots 0..2 is
-// confirmed, tested alive and answered from the first line alone.
+// With timers the expiries follow the control word, so an insertion decides
+// from the first line, an expire scan reads only the first 64 bytes of each
+// bucket, and a key found in slots 0..2 is confirmed, tested alive and
+// answered from the first line alone.
 #pragma once
 
 #include <cstdint>
@@ -42,7 +42,7 @@ constexpr uint64_t kHeaderBytes = 256;
 constexpr uint32_t kBucketBytes = 256;
 constexpr uint32_t kLineBytes = 128;
 constexpr uint32_t kMagic = 0x50504B43u;  // "CKPP"
-constexpr uint32_t kAbiVersion = 2;       // written to the header; equals CKPP_ABI_VERSION
+constexpr uint32_t kAbiVersion = 3;       // written to the header; equals CKPP_ABI_VERSION
 constexpr uint64_t kSeed2Xor = 0x9E3779B97F4A7C15ull;
 constexpr uint32_t kAliveWindow = 1024;   // Sec. 4.2
 constexpr uint32_t kMaxStale = 64512;     // Sec. 4.2: 65536 - 1024
@@ -159,13 +159,15 @@ __device__ __forceinline__ uint16_t* tag_ptr(const TableView& t, uint32_t b, uin
 }
 // The first slot whose entry lives in the second line.
 __host__ __device__ constexpr uint32_t first_hi_slot(uint32_t timers) { return timers ? 3u : 4u; }
-// Byte offsets of a slot's key, value and expiry within its bucket.
+// Byte offset of a timers table's 8 expiries within a bucket.
+constexpr uint32_t kExpiryOff = 32;
+// Byte offsets of a slot's key and value within its bucket.
 __device__ __forceinline__ uint32_t key_off(uint32_t timers, uint32_t s) {
-  const uint32_t h = first_hi_slot(timers);
-  return s < h ? 32u + 16u * s : kLineBytes + 16u * (s - h);
+  if (timers) return s < 3 ? 48u + 16u * s : kLineBytes + 16u * (s - 3);
+  return s < 4 ? 32u + 16u * s : kLineBytes + 16u * (s - 4);
 }
 __device__ __forceinline__ uint32_t value_off(uint32_t timers, uint32_t s) {
-  if (timers) return s < 2 ? 80u + 8u * s : s == 2 ? 112u : 208u + 8u * (s - 3);
+  if (timers) return s < 3 ? 96u + 8u * s : 208u + 8u * (s - 3);
   return s < 4 ? 96u + 8u * s : 192u + 8u * (s - 4);
 }
 __device__ __forceinline__ uint8_t* key_ptr(const TableView& t, uint32_t b, uint32_t s) {
@@ -175,7 +177,7 @@ __device__ __forceinline__ uint64_t* value_ptr(const TableView& t, uint32_t b, u
   return reinterpret_cast<uint64_t*>(bucket_ptr(t, b) + value_off(t.timers, s));
 }
 __device__ __forceinline__ uint16_t* expiry_ptr(const TableView& t, uint32_t b, uint32_t s) {
-  return reinterpret_cast<uint16_t*>(bucket_ptr(t, b) + 96) + s;
+  return reinterpret_cast<uint16_t*>(bucket_ptr(t, b) + kExpiryOff) + s;
 }
 
 // ---------------------------------------------------------- memory access

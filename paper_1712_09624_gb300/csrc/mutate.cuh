@@ -29,9 +29,8 @@ __device__ __forceinline__ uint32_t or_acquire(uint32_t* p, uint32_t v) {
 }
 
 __device__ __forceinline__ void exch_release(uint32_t* p, uint32_t v) {
-  uint32_t old;
+  [[maybe_unused]] uint32_t old;
   asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  (void)old;
 }
 
 __device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint32_t& ctrl) {

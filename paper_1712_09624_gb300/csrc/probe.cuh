@@ -150,7 +150,7 @@ __device__ __forceinline__ void examine(Probe& p, const uint8_t* L, uint32_t sw,
     }
     alive8 = kBusyMask;
     if (timers) {
-      const uint4 ex = lds128(chunk(6));
+      const uint4 ex = lds128(chunk(kExpiryOff / 16u));
       alive8 = alive_mask(lo64(ex), hi64(ex), now);
     }
     cand = m8 & lo;

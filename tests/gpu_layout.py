@@ -22,25 +22,27 @@ def first_hi_slot(timers: bool) -> int:
     return 3 if timers else 4
 
 
+EXPIRY_OFF = 32  # timers: expiry[8] in line 0, right after the 32-byte header
+
+
 def key_offsets(timers: bool) -> np.ndarray:
     """Byte offset of each slot's key in a bucket: the first slots in line 0
-    after the 32-byte header, the others from the start of line 1."""
+    after the 32-byte header (and, with timers, the 16 bytes of expiries), the
+    others from the start of line 1."""
     h = first_hi_slot(timers)
     s = np.arange(SLOTS)
-    return np.where(s < h, 32 + 16 * s, 128 + 16 * (s - h))
+    first = 48 if timers else 32
+    return np.where(s < h, first + 16 * s, 128 + 16 * (s - h))
 
 
 def value_offsets(timers: bool) -> np.ndarray:
-    """Byte offset of each slot's value. Without timers: values 0-3 end line 0,
-    values 4-7 follow keys 4-7. With timers: values 0-1 follow keys 0-2, value 2
-    follows the expiries, values 3-7 follow keys 3-7."""
+    """Byte offset of each slot's value: the first line's values from byte 96
+    (after keys 0-3, or after the expiries and keys 0-2 with timers), the second
+    line's after its keys."""
     s = np.arange(SLOTS)
     if timers:
-        return np.where(s < 2, 80 + 8 * s, np.where(s == 2, 112, 208 + 8 * (s - 3)))
+        return np.where(s < 3, 96 + 8 * s, 208 + 8 * (s - 3))
     return np.where(s < 4, 96 + 8 * s, 192 + 8 * (s - 4))
-
-
-EXPIRY_OFF = 96  # timers: expiry[8] in line 0
 
 
 def reserved_ranges(timers: bool) -> list[tuple[int, int]]:

@@ -47,7 +47,7 @@ def test_every_declared_symbol_is_exported(K):
 
 
 def test_host_only_calls(K):
-    assert K.ckpp_abi_version() == 2
+    assert K.ckpp_abi_version() == 3
     g = K.geometry(1 << 24)
     assert K.ckpp_required_bytes(g) == 256 + (1 << 24) * 256  # 256-byte buckets, entries inside
     gt = K.geometry(1 << 24, timers=True)
