@@ -33,13 +33,13 @@ inline bool geometry_ok(const ckpp_geometry* g) {
 
 inline size_t table_bytes(const ckpp_geometry* g) { return kHeaderBytes + (size_t)g->n_buckets * kBucketBytes; }
 
-// Workspace of an n-key batch: counters | set_first[m] | set_last[m] |
-// slot_of[n] | pending[n] | retry[n] | fixup[fix_cap] (8 bytes each), each
-// part 256-byte aligned.
+// Workspace of an n-key batch: counters | set[2m] (first and last index per
+// position, interleaved) | slot_of[n] | pending[n] | retry[n] |
+// fixup[fix_cap] (8 bytes each), each part 256-byte aligned.
 struct WsLayout {
   uint64_t m = 0;
   uint32_t fix_cap = 0;
-  size_t off_first = 0, off_last = 0, off_slot = 0, off_pending = 0, off_retry = 0, off_fixup = 0, total = 0;
+  size_t off_set = 0, off_slot = 0, off_pending = 0, off_retry = 0, off_fixup = 0, total = 0;
 };
 
 constexpr WsLayout ws_layout(uint64_t n) {
@@ -49,10 +49,8 @@ constexpr WsLayout ws_layout(uint64_t n) {
   L.m = m;
   L.fix_cap = (uint32_t)(n < (1ull << 22) ? n : (1ull << 22)) + 64;
   size_t off = kAlign;  // counters
-  L.off_first = off;
-  off = align_up(off + 4 * m, kAlign);
-  L.off_last = off;
-  off = align_up(off + 4 * m, kAlign);
+  L.off_set = off;
+  off = align_up(off + 8 * m, kAlign);
   L.off_slot = off;
   off = align_up(off + 4 * n, kAlign);
   L.off_pending = off;
@@ -70,8 +68,7 @@ inline int prepare_workspace(uint64_t n, void* workspace, size_t bytes, cudaStre
   if (!workspace || bytes < L.total || !aligned(workspace, kAlign)) return CKPP_EINVAL;
   uint8_t* w = static_cast<uint8_t*>(workspace);
   ws.counters = reinterpret_cast<uint32_t*>(w);
-  ws.set_first = reinterpret_cast<uint32_t*>(w + L.off_first);
-  ws.set_last = reinterpret_cast<uint32_t*>(w + L.off_last);
+  ws.set = reinterpret_cast<uint32_t*>(w + L.off_set);
   ws.slot_of = reinterpret_cast<uint32_t*>(w + L.off_slot);
   ws.pending = reinterpret_cast<uint32_t*>(w + L.off_pending);
   ws.retry = reinterpret_cast<uint32_t*>(w + L.off_retry);

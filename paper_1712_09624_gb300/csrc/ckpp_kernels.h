@@ -14,14 +14,18 @@ struct Workspace {
   uint32_t* counters;   // [0] pending count, [1] fixup count, [2] fixup overflow flag; list counts of the
                         // displacement passes: [3] after move1 (in `retry`), [5] after the grid search
                         // (in `pending`), [6] after the block search (in `retry`)
-  uint32_t* set_first;  // [m] open-addressing set of batch keys: lowest batch index of the key
-  uint32_t* set_last;   // [m] highest batch index of the key
+  uint32_t* set;        // [2m] open-addressing set of batch keys; position p holds two words side by
+                        // side (one line for both): the lowest batch index of the key (kEmpty when
+                        // free) and the highest
   uint32_t* slot_of;    // [n] set position of each batch key
   uint32_t* pending;    // [n] leaders left for the displacement pass
   uint32_t* retry;      // [n] leaders a displacement pass passes on to the next
   unsigned long long* fixup;  // [fix_cap] (table << 32 | bucket) whose moved counter fell to 0 off-lock
   uint32_t m_mask;      // m - 1 (m a power of two >= 2n)
   uint32_t fix_cap;
+
+  __device__ __forceinline__ uint32_t* first_at(uint32_t p) const { return set + 2 * (uint64_t)p; }
+  __device__ __forceinline__ uint32_t* last_at(uint32_t p) const { return set + 2 * (uint64_t)p + 1; }
 };
 
 // The table(s) a mutation batch works on: one table, or many (key i goes to
@@ -61,7 +65,7 @@ cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, co
                                   cudaStream_t s);
 
 // Resets a carved workspace for a new batch: counter_words counters to 0, the
-// dedup set's set_first words to empty and set_last words to 0 (one launch).
+// dedup set's first-index words to empty and last-index words to 0 (one launch).
 cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, cudaStream_t s);
 
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws,

@@ -53,21 +53,21 @@ __global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restri
   const uint32_t tid = ts.id(i);
   uint32_t pos = (uint32_t)(hash_key(k, 0x51ED270B27A2B5E3ull ^ tid) >> 16) & ws.m_mask;
   for (uint32_t probe = 0; probe <= ws.m_mask; ++probe) {
-    uint32_t cur = ld32_cg(ws.set_first + pos);
+    uint32_t cur = ld32_cg(ws.first_at(pos));
     if (cur == kEmpty) {
-      cur = atomicCAS(ws.set_first + pos, kEmpty, (uint32_t)i);
+      cur = atomicCAS(ws.first_at(pos), kEmpty, (uint32_t)i);
       if (cur == kEmpty) {
-        atomicMax(ws.set_last + pos, (uint32_t)i);
+        atomicMax(ws.last_at(pos), (uint32_t)i);
         ws.slot_of[i] = pos;
         return;
       }
     }
-    // set_first only ever holds batch indices of one key group, so the key at
-    // index cur is that group's key even while atomicMin lowers cur.
+    // A first-index word only ever holds batch indices of one key group, so
+    // the key at index cur is that group's key even while atomicMin lowers cur.
     const Key o = load_key(keys, cur);
     if (o.k0 == k.k0 && o.k1 == k.k1 && ts.id(cur) == tid) {
-      atomicMin(ws.set_first + pos, (uint32_t)i);
-      atomicMax(ws.set_last + pos, (uint32_t)i);
+      atomicMin(ws.first_at(pos), (uint32_t)i);
+      atomicMax(ws.last_at(pos), (uint32_t)i);
       ws.slot_of[i] = pos;
       return;
     }
@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restri
 
 __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint32_t& last) {
   const uint32_t pos = ws.slot_of[i];
-  if (ws.set_first[pos] != (uint32_t)i) return false;
-  last = ws.set_last[pos];
+  if (*ws.first_at(pos) != (uint32_t)i) return false;
+  last = *ws.last_at(pos);
   return true;
 }
 
@@ -134,25 +134,34 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
                                                           Workspace ws) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  uint32_t last;
-  if (!is_leader(ws, i, last)) return;
+  // The leader test's set words and the primary's lock are independent round
+  // trips: the words are requested before the lock and tested after it, so
+  // the two overlap. A key that is not its group's leader releases the lock
+  // untouched.
+  const uint32_t pos = ws.slot_of[i];
+  const uint32_t first = *ws.first_at(pos), last = *ws.last_at(pos);
   if (!ts.valid(i)) {
-    status[i] = kStNoTable;
+    if (first == (uint32_t)i) status[i] = kStNoTable;
     return;
   }
   const TableView t = ts.of(i);
   const uint32_t tid = ts.id(i);
-  const uint64_t v = vals[last];
   const Key k = load_key(keys, i);
   const Addr a = address_of(k, t.nb, t.seed);
   uint32_t c1, c2;
-  if (!lock_bucket(t, a.b1, c1)) {
+  const bool locked = lock_bucket(t, a.b1, c1);
+  if (first != (uint32_t)i) {
+    if (locked) unlock_bucket(t, a.b1, c1);
+    return;
+  }
+  if (!locked) {
     status[i] = kStBusy;
     latch_error(t, kErrLockTimeout);
     return;
   }
   Snap s1, s2;
   snap_bucket(t, a.b1, s1);
+  const uint64_t v = vals[last];
   const int slot = find_key(t, a.b1, c1, s1, k, a.tag);
   if (slot >= 0) {
     const bool was_alive = !t.timers || alive16(snap_expiry(s1, slot), now);
@@ -492,7 +501,7 @@ __global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint
     }
     int rc = 0;
     if (found) {
-      const uint64_t v = vals[ws.set_last[ws.slot_of[i]]];
+      const uint64_t v = vals[*ws.last_at(ws.slot_of[i])];
       rc = execute_path(t, ts.id(i), path, slot, 1, hole, k, v, a, now, expiry, ws);
     }
     if (rc == 0) {
@@ -532,7 +541,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
     const uint32_t i = list[j];
     const TableView t = ts.of(i);
     const uint32_t tid = ts.id(i);
-    const uint64_t v = vals[ws.set_last[ws.slot_of[i]]];
+    const uint64_t v = vals[*ws.last_at(ws.slot_of[i])];
     const Key k = load_key(keys, i);
     const Addr a = address_of(k, t.nb, t.seed);
     uint8_t st = kStFull;
@@ -585,23 +594,21 @@ __global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uin
     }
   }
   if (i >= n) return;
-  const uint32_t leader = ws.set_first[ws.slot_of[i]];
+  const uint32_t leader = *ws.first_at(ws.slot_of[i]);
   if (leader == (uint32_t)i) return;
   const uint8_t st = status[leader];
   status[i] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;  // FULL, BUSY, NO_TABLE copy through
 }
 
 // ------------------------------------------------------- workspace reset
+// The set's words alternate first (empty) and last (0), so each 16-byte
+// vector holds two positions.
 __global__ void __launch_bounds__(kThreads) workspace_clear(uint32_t* __restrict__ counters, uint32_t counter_words,
-                                                            uint4* __restrict__ first, uint4* __restrict__ last,
-                                                            uint64_t m4) {
+                                                            uint4* __restrict__ set, uint64_t n_vec) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (tid < counter_words) counters[tid] = 0u;
-  for (uint64_t j = tid; j < m4; j += stride) {
-    first[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-    last[j] = make_uint4(0u, 0u, 0u, 0u);
-  }
+  for (uint64_t j = tid; j < n_vec; j += stride) set[j] = make_uint4(kEmpty, 0u, kEmpty, 0u);
 }
 
 __global__ void __launch_bounds__(kThreads) delete_kernel(TableSet ts, const uint8_t* __restrict__ keys, uint64_t n,
@@ -652,13 +659,13 @@ unsigned grid_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1)
 }  // namespace
 
 cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, cudaStream_t s) {
-  // m is a power of two >= 64 and the set arrays are 256-byte aligned, so
-  // they clear as whole 16-byte vectors
-  const uint64_t m4 = ((uint64_t)ws.m_mask + 1) / 4;
-  const uint64_t want = (m4 > counter_words ? m4 : counter_words);
+  // m is a power of two >= 64 and the set is 256-byte aligned: 2m words clear
+  // as m / 2 whole 16-byte vectors
+  const uint64_t n_vec = ((uint64_t)ws.m_mask + 1) / 2;
+  const uint64_t want = (n_vec > counter_words ? n_vec : counter_words);
   const uint64_t blocks = (want + kThreads - 1) / kThreads;
   workspace_clear<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), kThreads, 0, s>>>(
-      ws.counters, counter_words, reinterpret_cast<uint4*>(ws.set_first), reinterpret_cast<uint4*>(ws.set_last), m4);
+      ws.counters, counter_words, reinterpret_cast<uint4*>(ws.set), n_vec);
   return cudaGetLastError();
 }
 
