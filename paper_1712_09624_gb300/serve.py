@@ -1,21 +1,18 @@
 """Served form: a continuous-batching request loop over device-resident tables.
 
-Packet bursts arrive from many ports (Poisson arrivals, uniform burst sizes);
-each burst targets one table and is either a lookup of flows or an insert of
-new flows. The loop runs in real time on the host:
+Packet bursts arrive from many ports (``serve_policy.draw_stream``). The loop
+runs in real time on the host:
 
 * it retires finished launches (CUDA event queries) and frees their staging
   footprint;
-* it admits every burst that has arrived, in arrival order, while the
-  staging footprint (keys in, results out) of work in flight stays within an
-  HBM budget; a burst that does not fit waits for the next turn;
-* it launches the admitted work without waiting for the previous launch: the
-  admitted lookups as one persistent ``ckpp_batch_lookup`` (one job per burst)
-  every turn, and the admitted inserts coalesced into one multi-table
-  ``ckpp_batch_insert`` once enough keys wait or the oldest has waited long
-  enough (an insert call has a fixed cost of several dependent kernels, so
-  coalescing writes keeps that cost from every turn); both on one stream, so
-  the next launch is queued while the current one runs.
+* it asks the turn planner (``serve_policy.TurnPlanner``: admission within an
+  HBM footprint budget, write coalescing) what to launch;
+* it launches that without waiting for the previous launch: the turn's
+  lookups as one persistent ``ckpp_batch_lookup`` (one job per burst), and,
+  when the planner flushes them, the waiting inserts as one multi-table
+  ``ckpp_batch_insert`` (an insert call has a fixed cost of several dependent
+  kernels, so coalescing writes keeps that cost from every turn); both on one
+  stream, so the next launch is queued while the current one runs.
 
 Lookups read flows of the warm fill (and unknown flows); inserts add new
 flows. Lookup results therefore do not depend on how bursts are grouped, and
@@ -31,7 +28,6 @@ from __future__ import annotations
 
 import time
 from collections import deque
-from dataclasses import dataclass
 
 import numpy as np
 import torch
@@ -39,62 +35,8 @@ import torch
 from . import _ckpp as K
 from . import workload_gpu as WG
 from .batched import BatchedLookup
+from .serve_policy import ServeConfig, Stream, TurnPlanner, draw_stream  # noqa: F401 (re-exported)
 from .table import FlowTable
-
-KEY_BYTES_IO = 16 + 8 + 1  # key in, value and flag out
-
-
-@dataclass
-class ServeConfig:
-    n_tables: int = 256
-    total_slots: int = 500_000_000
-    warm_lf: float = 0.8
-    ports: int = 64
-    min_burst: int = 32
-    max_burst: int = 4096
-    offered_lookups_per_s: float = 2e9
-    insert_fraction: float = 0.10
-    neg_rate: float = 0.2
-    duration_s: float = 0.2
-    footprint_bytes: int = 256 << 20
-    insert_flush_keys: int = 32768    # coalesced inserts go out once this many keys wait ...
-    insert_flush_s: float = 300e-6    # ... or the oldest has waited this long
-    seed: int = 7
-
-
-@dataclass
-class Stream:
-    """Pre-drawn request stream (arrival order)."""
-    arrival: np.ndarray    # seconds since start
-    table: np.ndarray      # target table
-    size: np.ndarray       # keys in the burst
-    insert: np.ndarray     # True: insert of new flows
-    offset: np.ndarray     # lookups: offset in the table's lookup pool; inserts: offset in the insert pool
-
-
-def draw_stream(cfg: ServeConfig) -> Stream:
-    rng = np.random.default_rng(cfg.seed)
-    mean_burst = (cfg.min_burst + cfg.max_burst) / 2
-    rate_per_port = cfg.offered_lookups_per_s / (cfg.ports * mean_burst)
-    per_port = []
-    for _ in range(cfg.ports):
-        n = int(rate_per_port * cfg.duration_s * 1.2) + 16
-        t = np.cumsum(rng.exponential(1.0 / rate_per_port, n))
-        per_port.append(t[t < cfg.duration_s])
-    arrival = np.sort(np.concatenate(per_port))
-    nb = arrival.shape[0]
-    table = rng.integers(0, cfg.n_tables, nb)
-    size = rng.integers(cfg.min_burst, cfg.max_burst + 1, nb)
-    insert = rng.random(nb) < cfg.insert_fraction
-    offset = np.zeros(nb, np.int64)
-    ins_sizes = np.where(insert, size, 0)
-    offset[insert] = (np.cumsum(ins_sizes) - ins_sizes)[insert]
-    look = ~insert
-    for t in range(cfg.n_tables):
-        sel = look & (table == t)
-        s = size[sel]
-        offset[sel] = np.cumsum(s) - s
-    return Stream(arrival, table, size, insert, offset)
 
 
 def percentiles(lat: np.ndarray) -> dict | None:
@@ -158,12 +100,9 @@ class Service:
         cuda = torch.cuda.current_stream(dev)
         n_bursts = st.arrival.shape[0]
         done_at = np.full(n_bursts, np.nan)
-        foot = st.size.astype(np.int64) * KEY_BYTES_IO
-        in_flight = deque()  # (event, bursts it completes, bytes)
-        flight_bytes = 0
-        nxt = 0
-        pend = []  # admitted insert bursts not yet launched (contiguous in the insert pool)
-        pend_keys = 0
+        in_flight = deque()  # (event, bursts it completes, turn or None)
+        planner = TurnPlanner(st, cfg, K.BATCH_MAX_JOBS)
+        nxt = 0  # plain mode: first burst not yet launched
         lib = K.library()
         job_dtype = np.dtype([("keys", "<u8"), ("out_vals", "<u8"), ("out_found", "<u8"), ("n", "<u4"),
                               ("table", "<u4")])
@@ -185,12 +124,12 @@ class Service:
         e0.record(cuda)
 
         def retire(block: bool):
-            nonlocal flight_bytes
             while in_flight and (block or in_flight[0][0].query()):
-                ev, idx, nbytes = in_flight.popleft()
+                ev, idx, turn = in_flight.popleft()
                 ev.synchronize()
                 done_at[idx] = ev_time(ev)
-                flight_bytes -= nbytes
+                if turn is not None:
+                    planner.complete(turn)
                 if starts:
                     gpu_busy.append(starts.pop(0).elapsed_time(ev) / 1e3)
                 block = False
@@ -199,48 +138,22 @@ class Service:
             return e0.elapsed_time(ev) / 1e3
 
         sh = cuda.cuda_stream
-        while nxt < n_bursts or in_flight or pend:
+        while (not planner.finished() if mode == "batched" else nxt < n_bursts) or in_flight:
             retire(False)
             now = time.perf_counter() - t0
-            arrived = nxt < n_bursts and st.arrival[nxt] <= now
             if mode == "batched":
-                flush_due = bool(pend) and (pend_keys >= cfg.insert_flush_keys or nxt >= n_bursts or
-                                            now - st.arrival[pend[0]] >= cfg.insert_flush_s)
-                if not arrived and not flush_due:
+                action, turn, wake = planner.plan(now, bool(in_flight))
+                if action == "idle":
                     if not in_flight:
-                        wake = st.arrival[nxt] if nxt < n_bursts else now
-                        if pend:
-                            wake = min(wake, st.arrival[pend[0]] + cfg.insert_flush_s)
                         time.sleep(max(0.0, min(50e-6, wake - now)))
                     continue
-                sel = slice(nxt, nxt)
-                if arrived:
-                    hi = int(np.searchsorted(st.arrival, now, side="right"))
-                    hi = min(hi, nxt + K.BATCH_MAX_JOBS)
-                    room = cfg.footprint_bytes - flight_bytes
-                    cum = np.cumsum(foot[nxt:hi])
-                    fit = int(np.searchsorted(cum, room, side="right"))
-                    if fit == 0:
-                        if pend:
-                            flush_due = True  # waiting inserts hold the budget: send them
-                        elif in_flight:
-                            retire(True)
-                            continue
-                        else:
-                            fit = 1  # a burst larger than the budget goes alone
-                    sel = slice(nxt, nxt + fit)
-                    flight_bytes += int(foot[sel].sum())
-                ins = st.insert[sel]
-                look_idx = np.arange(sel.start, sel.stop)[~ins]
-                for b in np.arange(sel.start, sel.stop)[ins]:
-                    pend.append(int(b))
-                    pend_keys += int(st.size[b])
-                flush = bool(pend) and (flush_due or pend_keys >= cfg.insert_flush_keys or sel.stop >= n_bursts or
-                                        now - st.arrival[pend[0]] >= cfg.insert_flush_s)
-                nj = look_idx.shape[0]
-                if not nj and not flush:
-                    nxt = sel.stop
+                if action == "block":
+                    retire(True)
                     continue
+                if action == "none":
+                    continue
+                look_idx = turn.lookups
+                nj = look_idx.shape[0]
                 # the turn's host work comes first, so that its launches go out back to back
                 if nj:
                     if ring_event[slot] is not None:
@@ -253,19 +166,16 @@ class Service:
                     view["out_found"][:nj] = pool_found[tb] + off
                     view["n"][:nj] = st.size[look_idx]
                     view["table"][:nj] = tb
-                done = list(look_idx)
                 ev_start = torch.cuda.Event(enable_timing=True)
                 ev_start.record(cuda)
-                if flush:  # the pending inserts form one contiguous range of the insert pool
-                    first = int(st.offset[pend[0]])
+                if turn.inserts:  # one contiguous range of the insert pool
+                    first = turn.insert_first
                     lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
                                           self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
-                                          pend_keys, 0, 0, self.ins_status[first:].data_ptr(),
+                                          turn.insert_keys, 0, 0, self.ins_status[first:].data_ptr(),
                                           self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
                     launches += 1
                     flushes += 1
-                    done += pend
-                    pend, pend_keys = [], 0
                 if nj:
                     nbytes_jobs = nj * K.JOB_BYTES
                     self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
@@ -277,12 +187,10 @@ class Service:
                 if nj:
                     ring_event[slot] = ev
                     slot = (slot + 1) % len(ring)
-                done = np.asarray(done, dtype=np.int64)
-                in_flight.append((ev, done, int(foot[done].sum())))
+                in_flight.append((ev, turn.done, turn))
                 starts.append(ev_start)
-                groups.append(sel.stop - sel.start)
-                nxt = sel.stop
-            elif arrived:  # plain: one launch per burst, as it arrives
+                groups.append(turn.admitted.stop - turn.admitted.start)
+            elif nxt < n_bursts and st.arrival[nxt] <= now:  # plain: one launch per burst, as it arrives
                 hi = int(np.searchsorted(st.arrival, now, side="right"))
                 for b in range(nxt, hi):
                     t = int(st.table[b])
@@ -300,7 +208,7 @@ class Service:
                     launches += 1
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(cuda)
-                in_flight.append((ev, np.arange(nxt, hi), 0))
+                in_flight.append((ev, np.arange(nxt, hi), None))
                 nxt = hi
             elif not in_flight and nxt < n_bursts:
                 time.sleep(max(0.0, min(50e-6, st.arrival[nxt] - now)))
