@@ -76,9 +76,25 @@ __device__ void scan_jobs(const BatchJob* __restrict__ jobs, uint32_t nj, unsign
   __syncthreads();
 }
 
-// Index of the job holding flat key idx: the last j with prefix[j] <= idx.
-__device__ __forceinline__ uint32_t find_job(const unsigned long long* prefix, uint32_t nj, unsigned long long idx) {
-  uint32_t lo = 0, hi = nj;  // prefix[lo] <= idx < prefix[hi]
+// Index of the job holding flat key idx: the last j with prefix[j] <= idx,
+// searched from hint, a job with prefix[hint] <= idx (the job of an earlier
+// key of the same lane: a lane's keys only move forward through the batch).
+// Usually idx is still in job hint; otherwise the search gallops forward to
+// bracket idx, then bisects the bracket.
+__device__ __forceinline__ uint32_t find_job(const unsigned long long* prefix, uint32_t nj, unsigned long long idx,
+                                             uint32_t hint) {
+  if (prefix[hint + 1] > idx) return hint;
+  uint32_t lo = hint + 1, hi = nj, step = 1;  // prefix[lo] <= idx < prefix[hi]
+  for (;;) {
+    const uint32_t probe = lo + step;
+    if (probe >= nj) break;
+    if (prefix[probe] > idx) {
+      hi = probe;
+      break;
+    }
+    lo = probe;
+    step <<= 1;
+  }
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
     if (prefix[mid] <= idx) lo = mid; else hi = mid;
@@ -87,11 +103,13 @@ __device__ __forceinline__ uint32_t find_job(const unsigned long long* prefix, u
 }
 
 // One warp iteration: lane l < kpw owns flat keys wbase + g * kpw + l, g < G.
+// hint: the job of the lane's last key so far (0 at the start).
 template <int G, int kTM>
 __device__ __forceinline__ void lookup_chunk(const TableView* __restrict__ tables, uint32_t n_tables,
                                              const BatchJob* __restrict__ jobs, const unsigned long long* prefix,
                                              uint32_t nj, unsigned long long total, unsigned long long wbase,
-                                             uint32_t kpw, uint32_t now, uint64_t pol, WarpStage<G>& S) {
+                                             uint32_t kpw, uint32_t now, uint64_t pol, uint32_t& hint,
+                                             WarpStage<G>& S) {
   const uint32_t lane = threadIdx.x & 31;
   Probe p[G];
   bool act[G];
@@ -104,7 +122,7 @@ __device__ __forceinline__ void lookup_chunk(const TableView* __restrict__ table
     jobi[g] = 0;
     local[g] = 0;
     if (act[g]) {
-      jobi[g] = find_job(prefix, nj, idx);
+      jobi[g] = hint = find_job(prefix, nj, idx, hint);
       act[g] = jobs[jobi[g]].table < n_tables;  // jobs naming no table are skipped
     }
     TableView tv{};
@@ -161,6 +179,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
   const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
   unsigned long long per_draw = chunks / (4 * warps);
   per_draw = per_draw < 1 ? 1 : (per_draw > kMaxChunksPerDraw ? kMaxChunksPerDraw : per_draw);
+  uint32_t hint = 0;  // chunks are drawn in increasing order, so a lane's keys only move forward
   for (;;) {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(ctrl, 1ull) * per_draw;
@@ -168,8 +187,8 @@ __global__ void __launch_bounds__(kBatchThreads) batched_lookup_kernel(const Tab
     if (c >= chunks) break;
     const unsigned long long c_end = c + per_draw < chunks ? c + per_draw : chunks;
     for (; c < c_end; ++c)
-      lookup_chunk<G, kTM>(tables, n_tables, jobs, prefix, nj, total, c * per_chunk, kpw, now, pol,
-                      stages[threadIdx.x >> 5]);
+      lookup_chunk<G, kTM>(tables, n_tables, jobs, prefix, nj, total, c * per_chunk, kpw, now, pol, hint,
+                           stages[threadIdx.x >> 5]);
   }
   // Every warp has drawn past the last chunk before it counts itself out, so
   // the last one out can reset the counters for the next launch.
