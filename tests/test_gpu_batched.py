@@ -123,6 +123,39 @@ def test_batched_skips_jobs_without_table_and_replays_graph(batch_setup):
         assert torch.equal(rv, ov) and torch.equal(rf, of)
 
 
+def test_batched_max_jobs_mostly_tiny_and_empty():
+    """8192 jobs (the maximum), most with 0-2 keys and a few large, in random
+    order: a lane's key often lies many jobs past its previous key's job, so
+    the job search gallops far and crosses runs of empty jobs. Every output
+    equals the plain per-table lookup."""
+    from paper_1712_09624_gb300 import _ckpp as K
+    from paper_1712_09624_gb300.batched import BatchedLookup
+    tables, fills = make_tables(12, 54)
+    rng = np.random.default_rng(55)
+    pools = [torch.from_numpy(W.lookup_batch(54 * 1000 + ti, 20000, fills[ti], 0.3, batch_id=2).keys).cuda()
+             for ti in range(len(tables))]
+    n_jobs = K.BATCH_MAX_JOBS
+    sizes = rng.choice([0, 0, 0, 1, 1, 2, 33, 2000], size=n_jobs, p=[0.3, 0.1, 0.1, 0.2, 0.1, 0.1, 0.07, 0.03])
+    qs = []
+    for j in range(n_jobs):
+        ti = int(rng.integers(0, len(tables)))
+        lo = int(rng.integers(0, 20000 - int(sizes[j])))
+        qs.append((ti, pools[ti][lo:lo + int(sizes[j])]))
+    ref = plain_results(tables, qs)
+    outs = [(torch.full((k.shape[0],), -7, dtype=torch.int64, device="cuda"),
+             torch.full((k.shape[0],), 9, dtype=torch.uint8, device="cuda")) for _, k in qs]
+    batch = BatchedLookup(tables, max_jobs=n_jobs)
+    batch.set_jobs([(ti, k, ov, of) for (ti, k), (ov, of) in zip(qs, outs)])
+    for tuning in [(4, 1, 2, 32), (4, 2, 1, 8)]:
+        for ov, of in outs:
+            ov.fill_(-7)
+            of.fill_(9)
+        batch.launch(20, tuning)
+        torch.cuda.synchronize()
+        for (rv, rf), (ov, of) in zip(ref, outs):
+            assert torch.equal(rv, ov) and torch.equal(rf, of)
+
+
 def test_batched_matches_oracle_small():
     """Batched results against the oracle on a few small tables."""
     from paper_1712_09624_gb300.batched import BatchedLookup
