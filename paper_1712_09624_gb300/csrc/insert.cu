@@ -28,6 +28,10 @@
 //             deferred so that it never races a concurrent setter); non-leader
 //             occurrences copy their leader's outcome (UPDATED, or FULL/BUSY).
 // Before them, one kernel clears the workspace (counters and the dedup set).
+// Each kernel after the workspace clear is launched with programmatic stream
+// serialization and waits for its predecessor in its first instruction
+// (pdl_wait in mutate.cuh), so the GPU schedules it while the predecessor
+// drains instead of after it.
 #include "mutate.cuh"
 
 namespace ckpp {
@@ -47,6 +51,8 @@ __device__ __forceinline__ Key load_key(const uint8_t* keys, uint64_t i) {
 // Equal keys bound for different tables are different keys.
 __global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restrict__ keys, uint64_t n, TableSet ts,
                                                          Workspace ws) {
+  pdl_wait();
+  pdl_release();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Key k = load_key(keys, i);
@@ -132,6 +138,8 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
                                                           const uint64_t* __restrict__ vals, uint64_t n,
                                                           uint32_t now, uint32_t expiry, uint8_t* __restrict__ status,
                                                           Workspace ws) {
+  pdl_wait();
+  pdl_release();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   // The leader test's set words and the primary's lock are independent round
@@ -454,6 +462,8 @@ __global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint
                                                          uint32_t expiry, uint8_t* __restrict__ status, Workspace ws,
                                                          const uint32_t* list, const uint32_t* count_ptr,
                                                          uint32_t* next, uint32_t* next_count) {
+  pdl_wait();
+  pdl_release();
   const uint32_t count = ld32_cg(count_ptr);
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
     const uint32_t i = list[j];
@@ -523,6 +533,8 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
                                                                   Workspace ws, const uint32_t* list,
                                                                   const uint32_t* count_ptr, uint32_t* retry,
                                                                   uint32_t* retry_count, uint32_t max_keys) {
+  pdl_wait();
+  pdl_release();
   constexpr bool kHashed = SeenSet<kBfsNodes>::kHashed;
   static_assert(kThreadsPerBlock * (kBfsNodes * sizeof(Node) + (kHashed ? SeenSet<kBfsNodes>::kSize * 4 : 0)) <=
                     48 * 1024,
@@ -576,6 +588,8 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
 // takes its share of the fixup list, and thread i < n finishes key i.
 __global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uint64_t n, uint8_t* __restrict__ status,
                                                                 Workspace ws) {
+  pdl_wait();
+  pdl_release();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (ld32_cg(ws.counters + 2)) {  // the list overflowed: scan every bucket of every table
@@ -605,6 +619,7 @@ __global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uin
 // vector holds two positions.
 __global__ void __launch_bounds__(kThreads) workspace_clear(uint32_t* __restrict__ counters, uint32_t counter_words,
                                                             uint4* __restrict__ set, uint64_t n_vec) {
+  pdl_release();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (tid < counter_words) counters[tid] = 0u;
@@ -613,6 +628,8 @@ __global__ void __launch_bounds__(kThreads) workspace_clear(uint32_t* __restrict
 
 __global__ void __launch_bounds__(kThreads) delete_kernel(TableSet ts, const uint8_t* __restrict__ keys, uint64_t n,
                                                           uint32_t now, uint8_t* __restrict__ status, Workspace ws) {
+  pdl_wait();
+  pdl_release();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (!ts.valid(i)) {
@@ -656,6 +673,23 @@ __global__ void __launch_bounds__(kThreads) delete_kernel(TableSet ts, const uin
 
 unsigned grid_for(uint64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Launch a kernel of an insert or delete call after its predecessor on the
+// same stream, with programmatic stream serialization (see pdl_wait).
+template <typename... Params, typename... Args>
+cudaError_t launch_chained(void (*kernel)(Params...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace
 
 cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, cudaStream_t s) {
@@ -670,46 +704,45 @@ cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, 
 }
 
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws, cudaStream_t s) {
-  dedup_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(keys, n, ts, ws);
-  return cudaGetLastError();
+  return launch_chained(dedup_kernel, grid_for(n, kThreads), kThreads, s, keys, n, ts, ws);
 }
 
 cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_t* vals, uint64_t n, uint32_t now,
                           uint32_t expiry, uint8_t* status, const Workspace& ws, cudaStream_t s) {
   cudaError_t e = launch_dedup(ts, keys, n, ws, s);
   if (e != cudaSuccess) return e;
-  insert_phase1<<<grid_for(n, kThreads), kThreads, 0, s>>>(ts, keys, vals, n, now, expiry, status, ws);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_chained(insert_phase1, grid_for(n, kThreads), kThreads, s, ts, keys, vals, n, now, expiry, status, ws);
+  if (e != cudaSuccess) return e;
   // lists: phase 1 -> pending [0] -> move1 -> retry [3] -> grid search ->
   // pending [5] -> block search -> retry [6] -> last search
-  insert_move1<<<152 * 8, kThreads, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 0,
-                                            ws.retry, ws.counters + 3);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  insert_phase2<kP2Threads, 96, 4><<<152 * 4, kP2Threads, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.retry,
-                                                                  ws.counters + 3, ws.pending, ws.counters + 5,
-                                                                  0xFFFFFFFFu);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_chained(insert_move1, 152 * 8, kThreads, s, ts, keys, vals, now, expiry, status, ws,
+                     (const uint32_t*)ws.pending, (const uint32_t*)(ws.counters + 0), ws.retry, ws.counters + 3);
+  if (e != cudaSuccess) return e;
+  e = launch_chained(insert_phase2<kP2Threads, 96, 4>, 152 * 4, kP2Threads, s, ts, keys, vals, now, expiry, status,
+                     ws, (const uint32_t*)ws.retry, (const uint32_t*)(ws.counters + 3), ws.pending, ws.counters + 5,
+                     0xFFFFFFFFu);
+  if (e != cudaSuccess) return e;
   // second pass, 8 single-warp blocks: the keys the grid pass could not place
-  insert_phase2<32, 192, 5><<<kSecondPassBlocks, 32, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.pending,
-                                                             ws.counters + 5, ws.retry, ws.counters + 6,
-                                                             kSecondPassKeys);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_chained(insert_phase2<32, 192, 5>, kSecondPassBlocks, 32, s, ts, keys, vals, now, expiry, status, ws,
+                     (const uint32_t*)ws.pending, (const uint32_t*)(ws.counters + 5), ws.retry, ws.counters + 6,
+                     kSecondPassKeys);
+  if (e != cudaSuccess) return e;
   // last pass, 16 single-thread blocks: the widest search, a few searches at
   // a time; a key is FULL only if it finds no path
-  insert_phase2<1, 2048, 6><<<kLastPassBlocks, 1, 0, s>>>(ts, keys, vals, now, expiry, status, ws, ws.retry,
-                                                          ws.counters + 6, nullptr, nullptr, kLastPassKeys);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_chained(insert_phase2<1, 2048, 6>, kLastPassBlocks, 1, s, ts, keys, vals, now, expiry, status, ws,
+                     (const uint32_t*)ws.retry, (const uint32_t*)(ws.counters + 6), (uint32_t*)nullptr,
+                     (uint32_t*)nullptr, kLastPassKeys);
+  if (e != cudaSuccess) return e;
   const unsigned fin_blocks = grid_for(n, kThreads);
-  insert_fixup_finish<<<fin_blocks > 152 * 2 ? fin_blocks : 152 * 2, kThreads, 0, s>>>(ts, n, status, ws);
-  return cudaGetLastError();
+  return launch_chained(insert_fixup_finish, fin_blocks > 152 * 2 ? fin_blocks : 152 * 2, kThreads, s, ts, n, status,
+                        ws);
 }
 
 cudaError_t launch_delete(const TableSet& ts, const uint8_t* keys, uint64_t n, uint32_t now, uint8_t* status,
                           const Workspace& ws, cudaStream_t s) {
   cudaError_t e = launch_dedup(ts, keys, n, ws, s);
   if (e != cudaSuccess) return e;
-  delete_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(ts, keys, n, now, status, ws);
-  return cudaGetLastError();
+  return launch_chained(delete_kernel, grid_for(n, kThreads), kThreads, s, ts, keys, n, now, status, ws);
 }
 
 }  // namespace ckpp

@@ -19,6 +19,16 @@
 
 namespace ckpp {
 
+// The kernels of one insert or delete call run back to back on one stream,
+// each launched with programmatic stream serialization, so that the GPU can
+// schedule a kernel while its predecessor finishes instead of after it.
+// Each such kernel calls pdl_wait() before touching memory: it returns once
+// the predecessor grid has completed and its writes are visible (for a kernel
+// launched without the attribute it returns at once). pdl_release() lets the
+// successor be scheduled; it does not let the successor past its own wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Lock word access: taking a lock is an acquire (later reads see what the
 // previous holder wrote), releasing it a release (everything written under the
 // lock is visible before the word clears). No full fence is needed.
