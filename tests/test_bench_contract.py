@@ -68,3 +68,18 @@ def test_default_scale_config():
     assert cfg["l2"] == "inputs larger than L2 (table 4.3 GB, keys 256 MB); no flush"
     # the committed DRAM-traffic capture is of this configuration
     assert (args.log2_buckets, args.log2_batch, args.load_factor, args.neg_rate) == bench.TRAFFIC_CONFIG
+
+
+def test_roofline_byte_counts():
+    """Algorithmic bytes: 32 per bucket read (primary or secondary) and per
+    record examined, plus 25 of streamed key and result per lookup; line bytes:
+    128 per line request (one per bucket read, one per second-line read) plus
+    the same 25."""
+    bench = load_bench()
+    n, prim, sec, rec, line1 = 1000, 1000, 64, 500, 225
+    counts = [prim, sec, rec, line1]
+    assert bench.alg_bytes_of(counts, n) == 32 * (prim + sec + rec) + 25 * n
+    assert bench.lines_of(counts) == prim + sec + line1
+    assert bench.line_bytes_of(counts, n) == 128 * (prim + sec + line1) + 25 * n
+    # the headline batch's counts give the per-lookup figures the bench reports
+    assert abs(bench.alg_bytes_of([1.0, 0.0645, 0.5], 1) - 75.06) < 0.01
