@@ -150,7 +150,11 @@ static oc_addr address_of(const oc_table* t, const uint8_t* key) {
   a.tag = (uint16_t)(h1 & 0xFFFF);
 #endif
   a.bit1 = (unsigned)(h2 & 63);
+#if OC_MUTANT == 4
+  a.bit2 = (unsigned)(h2 & 63);
+#else
   a.bit2 = (unsigned)((h2 >> 6) & 63);
+#endif
   return a;
 }
 
@@ -336,7 +340,9 @@ static void store(oc_table* t, uint64_t b, uint32_t s, const uint8_t* key, uint6
 static void move_entry(oc_table* t, uint64_t x, uint32_t s, uint64_t y, uint32_t u) {
   oc_slot moved = *at(t, x, s);
   oc_addr a = address_of(t, moved.key);
+#if OC_MUTANT != 14
   if (moved.in_secondary) bloom_remove(t, &a);
+#endif
   memset(at(t, x, s), 0, sizeof(oc_slot));
   oc_slot* d = at(t, y, u);
   *d = moved;
@@ -390,7 +396,9 @@ static int insert_one(oc_table* t, const uint8_t* key, uint64_t value, uint32_t 
     oc_slot* e = at(t, b, (uint32_t)s);
     int was_alive = slot_alive(t, e, now);
     e->value = value;
+#if OC_MUTANT != 15
     if (t->timers) e->expiry = expiry;
+#endif
 #if OC_MUTANT == 10
     (void)was_alive;
     return OC_UPDATED;
@@ -453,7 +461,9 @@ int oc_lookup(oc_table* t, const uint8_t* keys, uint64_t n, uint32_t now, uint32
     found[i] = 0;
     if (s < 0) continue;
     oc_slot* e = at(t, b, (uint32_t)s);
+#if OC_MUTANT != 12
     if (!slot_alive(t, e, now)) continue; /* Sec. 4.2: dead entries are ignored */
+#endif
     values[i] = e->value;
     found[i] = 1;
     if (t->timers && refresh_ttl) e->expiry = (uint16_t)(now + refresh_ttl);
@@ -493,7 +503,11 @@ int64_t oc_expire(oc_table* t, uint32_t now) {
       for (uint32_t s = 0; s < t->slots; ++s) {
         oc_slot* e = at(t, b, s);
         if (e->busy && !oc_alive(e->expiry, now)) {
+#if OC_MUTANT == 13
+          memset(e, 0, sizeof *e);
+#else
           remove_entry(t, b, s);
+#endif
           ++n;
         }
       }

@@ -34,6 +34,7 @@ MUTANTS = {
     1: "filter insertion sets only one of the two bits",
     2: "filter never reset when the moved counter reaches zero",
     3: "tag taken from the secondary hash",
+    4: "both filter bit indices taken from the same six hash bits",
     5: "alive test uses <= 1024",
     6: "in_secondary flag not updated on a cuckoo move",
     7: "removal forgets the moved counter",
@@ -41,6 +42,10 @@ MUTANTS = {
     9: "dead slots not reused by insertion",
     10: "upsert always reports UPDATED",
     11: "b2 may equal b1",
+    12: "lookup returns dead entries",
+    13: "the expire scan removes dead entries without the moved-counter upkeep",
+    14: "a cuckoo move out of a secondary bucket keeps the primary's moved counter",
+    15: "an update in place keeps the old expiry",
 }
 
 
