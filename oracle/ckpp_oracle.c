@@ -49,6 +49,12 @@
  *   staleness : every timed call checks (uint32)(now - last_scan) <= 64512, where
  *               last_scan is the time of the last expire scan (or of the first
  *               timed call); otherwise it returns OC_ESTALE and does nothing.
+ *
+ * Parity unpinned: which keys come back FULL near capacity (the path search
+ * bound above is this project's; the paper's failure points are in figure data
+ * it does not print). The tests only require zero FULL keys at load factors up
+ * to 0.95 and that a FULL key is legitimate (not stored, both buckets full of
+ * live entries).
  */
 #include <stdint.h>
 #include <stdlib.h>
