@@ -145,7 +145,11 @@ static oc_addr address_of(const oc_table* t, const uint8_t* key) {
   oc_addr a;
   uint64_t h1 = oc_hash(key, t->seed);
   uint64_t h2 = oc_hash(key, t->seed ^ OC_SEED2_XOR);
+#if OC_MUTANT == 16
+  a.b1 = h1 % t->nb;
+#else
   a.b1 = reduce(h1, t->nb);
+#endif
   a.b2 = reduce(h2, t->nb);
 #if OC_MUTANT != 11
   if (a.b2 == a.b1) a.b2 = (a.b1 + 1) % t->nb;
@@ -374,8 +378,13 @@ typedef struct {
  * bucket has a free slot (in *free_slot), or -1. */
 static int bfs(const oc_table* t, const oc_addr* a, uint32_t now, bfs_node* q, uint32_t* free_slot) {
   int n = 0;
+#if OC_MUTANT == 17
+  q[n++] = (bfs_node){a->b2, -1, 0, 0};
+  q[n++] = (bfs_node){a->b1, -1, 0, 0};
+#else
   q[n++] = (bfs_node){a->b1, -1, 0, 0};
   q[n++] = (bfs_node){a->b2, -1, 0, 0};
+#endif
   for (int i = 0; i < n; ++i) {
     int f = lowest_free(t, q[i].bucket, now);
     if (f >= 0) {
@@ -412,16 +421,21 @@ static int insert_one(oc_table* t, const uint8_t* key, uint64_t value, uint32_t 
     return was_alive ? OC_UPDATED : OC_INSERTED;
 #endif
   }
-  s = lowest_free(t, a.b1, now);
+#if OC_MUTANT == 18
+  const uint64_t first = a.b2, second = a.b1;
+#else
+  const uint64_t first = a.b1, second = a.b2;
+#endif
+  s = lowest_free(t, first, now);
   if (s >= 0) {
-    remove_entry(t, a.b1, (uint32_t)s);
-    store(t, a.b1, (uint32_t)s, key, value, expiry, &a);
+    remove_entry(t, first, (uint32_t)s);
+    store(t, first, (uint32_t)s, key, value, expiry, &a);
     return OC_INSERTED;
   }
-  s = lowest_free(t, a.b2, now);
+  s = lowest_free(t, second, now);
   if (s >= 0) {
-    remove_entry(t, a.b2, (uint32_t)s);
-    store(t, a.b2, (uint32_t)s, key, value, expiry, &a);
+    remove_entry(t, second, (uint32_t)s);
+    store(t, second, (uint32_t)s, key, value, expiry, &a);
     return OC_INSERTED;
   }
   bfs_node q[OC_BFS_MAX_NODES];

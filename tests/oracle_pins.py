@@ -13,7 +13,10 @@ Pins used (none re-types the oracle's own formulas):
   * a brute-force linear-scan list map replaying random operation streams on
     tiny tables (exact: statuses, lookup results, live sets);
   * the structural invariants of Sec. 2 and Sec. 4.1 after every batch;
-  * lazy deletion (Sec. 4.2): a table full of dead entries takes new keys.
+  * lazy deletion (Sec. 4.2): a table full of dead entries takes new keys;
+  * the fill statistics (share of entries in their secondary, moved-counter
+    histogram) against a fluid-limit model of the insertion rule of Sec. 2
+    and the counter rule of Sec. 4.1 (``fill_model.py``).
 """
 
 from __future__ import annotations
@@ -82,6 +85,21 @@ def check_address_properties(L, n=40000, seed=11) -> list[str]:
     chi = ((tb - n / 64) ** 2 / (n / 64)).sum()
     if not chi < 63 + 6 * 11.2:
         bad.append(f"tag not uniform: chi2={chi:.0f}")
+    # The tag must not repeat bucket-index bits (Sec. 4.3 takes it from the main
+    # hash, and a tag that the bucket fixes would stop telling apart the keys
+    # sharing that bucket): chi-square of 64 x 64 contingency tables between
+    # b1 (and b2) over 64 buckets and the tag's low and high six bits.
+    a64 = oracle.address(keys, 64, seed, library=L)
+    df = 63 * 63
+    for bname in ("b1", "b2"):
+        for tname, tb6 in (("tag low bits", a64["tag"].astype(np.int64) & 63),
+                           ("tag high bits", a64["tag"].astype(np.int64) >> 10)):
+            table = np.zeros((64, 64))
+            np.add.at(table, (a64[bname].astype(np.int64), tb6), 1)
+            expect = np.outer(table.sum(1), table.sum(0)) / n
+            chi = ((table - expect) ** 2 / np.maximum(expect, 1e-12)).sum()
+            if not chi < df + 6 * (2 * df) ** 0.5:
+                bad.append(f"{bname} and {tname} dependent: chi2={chi:.0f} (df {df})")
     return bad
 
 
@@ -289,5 +307,62 @@ def check_lazy_reuse(L) -> list[str]:
     return bad
 
 
+# ------------------------------------------- fill statistics vs a model
+
+def fill_statistics(L, nb, load_factors, seed):
+    """Fill an nb x 8 table in key order and record, at each load factor, the
+    share of entries in their secondary bucket, the share of zero moved
+    counters, the counter histogram and the exact filter pass rate of a
+    negative key (mean over buckets of P(both query bits set))."""
+    from paper_1712_09624_gb300 import workload as W
+    cap = nb * 8
+    t = oracle.Table(nb, 8, False, seed, library=L)
+    f = W.fill(seed, int(max(load_factors) * cap))
+    out, done = {}, 0
+    for lf in sorted(load_factors):
+        m = int(lf * cap)
+        st = t.insert(f.keys[done:m], f.values[done:m])
+        done = m
+        bloom, moved = t.meta()
+        bits = np.unpackbits(bloom.view(np.uint8)).reshape(-1, 64).sum(1).astype(np.float64)
+        out[lf] = dict(
+            all_inserted=bool((st == oracle.INSERTED).all()),
+            f_sec=float(t.dump()["in_secondary"].mean()),
+            moved_zero=float((moved == 0).mean()),
+            hist=np.bincount(moved) / nb,
+            fpr_exact=float(((bits / 64.0) ** 2).mean()),
+            table=t,
+        )
+    return out
+
+
+def check_fill_model(L, nb=1 << 16, seed=3) -> list[str]:
+    """Sec. 2 (primary if it has room, else secondary) and Sec. 4.1 (counter per
+    displaced key) against the fluid-limit model of that rule
+    (``fill_model.py``), at load factors where keys with both buckets full are
+    rare enough for the model to be exact. Bands are five standard deviations
+    of the table-to-table spread at this size (measured over seeds)."""
+    import fill_model
+    model = fill_model.fill_model([0.6, 0.7, 0.8])
+    got = fill_statistics(L, nb, [0.6, 0.7, 0.8], seed)
+    bad = []
+    for lf in (0.6, 0.7, 0.8):
+        g, m = got[lf], model[lf]
+        if not g["all_inserted"]:
+            bad.append(f"fill to LF {lf} left keys not INSERTED")
+        if abs(g["f_sec"] - m["f_sec"]) > 0.0015:
+            bad.append(f"LF {lf}: secondary share {g['f_sec']:.4f}, model {m['f_sec']:.4f}")
+        if abs(g["moved_zero"] - m["moved_zero"]) > 0.005:
+            bad.append(f"LF {lf}: zero-counter share {g['moved_zero']:.4f}, model {m['moved_zero']:.4f}")
+        k = max(len(g["hist"]), 16)
+        gh = np.pad(g["hist"], (0, k - len(g["hist"])))
+        tv = 0.5 * np.abs(gh - m["hist"][:k]).sum() + 0.5 * m["hist"][k:].sum()
+        if tv > 0.008:
+            bad.append(f"LF {lf}: counter histogram off the model by {tv:.4f} (total variation)")
+    for v in got.values():
+        v["table"].close()
+    return bad
+
+
 ALL_CHECKS = [check_splitmix_vectors, check_timer_golden, check_address_properties, check_avalanche,
-              check_lazy_reuse, check_replays]
+              check_lazy_reuse, check_replays, check_fill_model]

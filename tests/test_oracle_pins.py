@@ -3,9 +3,10 @@
 The oracle is what the CUDA path is checked against, so it is itself pinned
 to things other than itself: published SplitMix64 outputs, the timer arithmetic
 of Sec. 4.2, properties of the hash readings, a brute-force list map on tiny
-tables, the structural invariants of Sec. 2 / Sec. 4.1, and the statistics the
-paper prints (Fig. 2, Fig. 5, Table 2). A mutation test plants known mistakes
-in the oracle and checks that these pins catch every one.
+tables, the structural invariants of Sec. 2 / Sec. 4.1, a fluid-limit model of
+the insertion rule, and the statistics the paper prints (Fig. 2, Fig. 5,
+Table 2). A mutation test plants known mistakes in the oracle and checks that
+these pins catch every one.
 """
 
 import os
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
+import fill_model
 import oracle_pins as P
 from oracle.odef import MapTable
 from paper_1712_09624_gb300 import workload as W
@@ -46,6 +48,9 @@ MUTANTS = {
     13: "the expire scan removes dead entries without the moved-counter upkeep",
     14: "a cuckoo move out of a secondary bucket keeps the primary's moved counter",
     15: "an update in place keeps the old expiry",
+    16: "b1 taken from the low bits of H1, which the tag also uses",
+    17: "the cuckoo-path search starts from the secondary bucket",
+    18: "insertion tries the secondary bucket before the primary",
 }
 
 
@@ -117,75 +122,109 @@ def fill_stats(L):
     """Fill a 2^17 x 8 table step by step and record the statistics the paper
     plots (Fig. 2: fraction in secondary; Fig. 5: moved counters; Table 2: FPR)."""
     nb = 1 << 17
-    cap = nb * 8
-    t = oracle.Table(nb, 8, False, 7)
-    f = W.fill(7, int(0.95 * cap))
+    stats = P.fill_statistics(L, nb, [0.45, 0.6, 0.7, 0.8, 0.95], 7)
     neg = W.make_keys(7, W.STREAM_NEGATIVE_KEYS, 200000)
-    out, done = {}, 0
-    for lf in (0.45, 0.6, 0.7, 0.8, 0.95):
-        m = int(lf * cap)
-        st = t.insert(f.keys[done:m], f.values[done:m])
-        assert (st == oracle.INSERTED).all()
-        done = m
-        bloom, moved = t.meta()
-        pop = np.unpackbits(bloom.view(np.uint8)).reshape(-1, 64).sum(1).astype(np.float64)
-        sec_reads, _ = t.probe_counts(neg)
-        hist = np.bincount(moved)
-        out[lf] = dict(
-            f_sec=float(t.dump()["in_secondary"].mean()),
-            fpr_exact=float(((pop / 64.0) ** 2).mean()),
-            fpr_closed=float(sum(hist[c] / nb * (1 - (1 - 1 / 64) ** (2 * c)) ** 2 for c in range(len(hist)))),
-            fpr_measured=sec_reads / neg.shape[0],
-            moved_zero=float((moved == 0).mean()),
-        )
+    # the table holds the 0.95 fill; the negative-lookup counts are taken there
+    t = stats[0.95]["table"]
+    for lf, s in stats.items():
+        assert s["all_inserted"], lf
+        s["fpr_closed"] = float((s["hist"] * fill_model.pass_rate(np.arange(len(s["hist"])))).sum())
+    sec_reads, _ = t.probe_counts(neg)
+    stats[0.95]["fpr_measured"] = sec_reads / neg.shape[0]
     assert t.check() == 0
-    return out
+    for s in stats.values():
+        s.pop("table").close()
+    return stats
+
+
+@pytest.fixture(scope="module")
+def model():
+    return fill_model.fill_model([0.45, 0.6, 0.7, 0.8, 0.95])
 
 
 def paper_statistics():
-    """Rows of tests/golden/paper_statistics.txt: (quantity, LF) -> (paper, lo, hi)."""
+    """Rows of tests/golden/paper_statistics.txt: (quantity, LF) -> (paper, lo, hi),
+    lo and hi None where the row reads "model"."""
     rows = {}
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_statistics.txt")) as f:
         for line in f:
             if line.strip() and not line.startswith("#"):
                 q, lf, paper, lo, hi = line.split()
-                rows[(q, float(lf))] = (float(paper), float(lo), float(hi))
+                band = (None, None) if lo == "model" else (float(lo), float(hi))
+                rows[(q, float(lf))] = (float(paper),) + band
     return rows
 
 
-def test_fig2_fraction_in_secondary(fill_stats):
+def test_fig2_fraction_in_secondary(fill_stats, model):
     """Sec. 3 / Fig. 2 (8 slots): almost none below LF 0.5, 6% at 0.7, 16% at 0.95.
-    The paper used CityHash64 on a 32M table; the bands allow for the different hash."""
+
+    Below 0.5 and at 0.95 the oracle sits in a band around the paper's value.
+    At 0.7 the paper's 6% is beyond the insertion rule of Sec. 2 with a uniform
+    hash: the rule's fluid limit, which is exact at this load factor, gives
+    4.38%. The oracle must equal the model there, and the paper's value must be
+    above both: the gap belongs to the rule, not to this oracle."""
     rows = {lf: v for (q, lf), v in paper_statistics().items() if q == "secondary_fraction"}
     assert sorted(rows) == [0.45, 0.7, 0.95]
-    for lf, (_, lo, hi) in rows.items():
-        assert lo <= fill_stats[lf]["f_sec"] < hi, (lf, fill_stats[lf]["f_sec"])
+    for lf, (paper, lo, hi) in rows.items():
+        got = fill_stats[lf]["f_sec"]
+        if lo is None:
+            assert abs(got - model[lf]["f_sec"]) < 0.0015, (lf, got, model[lf]["f_sec"])
+            assert model[lf]["f_sec"] < paper - 0.01
+        else:
+            assert lo <= got < hi, (lf, got)
 
 
-def test_table2_bloom_false_positive_rate(fill_stats):
-    """Table 2: FPR 0.0002 / 0.001 / 0.003 at LF 0.6 / 0.8 / 0.95, within x1.6."""
+def test_fill_matches_rule_model(fill_stats, model):
+    """The whole fill against the fluid limit of the insertion rule (Sec. 2) and
+    the counter rule (Sec. 4.1). Exact while keys with both buckets full are
+    rare (LF <= 0.8); at 0.95 a cuckoo path can displace more than one entry,
+    which only raises the secondary share and lowers the zero-counter share."""
+    for lf in (0.45, 0.6, 0.7, 0.8):
+        assert abs(fill_stats[lf]["f_sec"] - model[lf]["f_sec"]) < 0.0015, lf
+        assert abs(fill_stats[lf]["moved_zero"] - model[lf]["moved_zero"]) < 0.004, lf
+    g, m = fill_stats[0.95], model[0.95]
+    assert m["f_sec"] - 0.001 < g["f_sec"] < m["f_sec"] + 0.015, (g["f_sec"], m["f_sec"])
+    assert m["moved_zero"] - 0.03 < g["moved_zero"] < m["moved_zero"] + 0.002, (g["moved_zero"], m["moved_zero"])
+
+
+def test_table2_bloom_false_positive_rate(fill_stats, model):
+    """Table 2: FPR 0.0002 / 0.001 / 0.003 at LF 0.6 / 0.8 / 0.95, within x1.6 of
+    the paper; and within 8% of the rate the model's counter histogram gives
+    (exact bit-collision formula, ``fill_model.pass_rate``), 15% at 0.95 where
+    the model undercounts displaced keys."""
     rows = {lf: v for (q, lf), v in paper_statistics().items() if q == "bloom_fpr"}
     assert sorted(rows) == [0.6, 0.8, 0.95]
     for lf, (paper, lo, hi) in rows.items():
         assert abs(lo - paper / 1.6) < 1e-9 and abs(hi - paper * 1.6) < 1e-9
         got = fill_stats[lf]["fpr_exact"]
         assert lo < got < hi, (lf, got)
+        assert lo < model[lf]["fpr"] < hi, (lf, model[lf]["fpr"])
+        rel = 0.15 if lf > 0.9 else 0.08
+        assert abs(got / model[lf]["fpr"] - 1) < rel, (lf, got, model[lf]["fpr"])
 
 
 def test_fpr_closed_form_and_measured_pass_rate(fill_stats):
     """The negative-lookup filter pass rate equals mean((popcount/64)^2) (two
-    independent uniform bit indices), and the popcount follows from the moved
-    counters as 64 (1 - (1 - 1/64)^(2c))."""
+    independent uniform bit indices), and that equals the rate the counter
+    histogram gives through the bit-collision formula."""
     for lf, s in fill_stats.items():
         exp = s["fpr_exact"]
-        sd = (exp / 200000) ** 0.5
-        assert abs(s["fpr_measured"] - exp) < 4.5 * sd + 1e-6, (lf, s)
-        assert abs(s["fpr_closed"] - exp) <= 0.05 * exp + 1e-6, (lf, s)
+        assert abs(s["fpr_closed"] - exp) <= 0.05 * exp + 1e-6, (lf, s["fpr_closed"], exp)
+    s = fill_stats[0.95]
+    sd = (s["fpr_exact"] / 200000) ** 0.5
+    assert abs(s["fpr_measured"] - s["fpr_exact"]) < 4.5 * sd + 1e-6
 
 
-def test_fig5_moved_counter_zero(fill_stats):
-    """Sec. 4.1 / Fig. 5: at LF 0.95 about half the buckets (the paper: more than
-    50%) have a zero moved counter; this hash gives ~47%, so the band is 0.40-0.60."""
-    _, lo, hi = paper_statistics()[("moved_zero_fraction", 0.95)]
-    assert lo < fill_stats[0.95]["moved_zero"] < hi
-    assert fill_stats[0.6]["moved_zero"] > fill_stats[0.95]["moved_zero"]
+def test_fig5_moved_counter_zero(fill_stats, model):
+    """Sec. 4.1 / Fig. 5: the paper says more than 50% of buckets have a zero
+    moved counter at LF 0.95. The rule's fluid limit gives 48.7% (one counter
+    step per key whose primary is full), and cuckoo paths that displace more
+    than one entry only lower it, so the printed value is beyond the rule with
+    a uniform hash. The oracle must sit between the model less 3 points and
+    the model, and the share must fall as the table fills."""
+    paper, lo, hi = paper_statistics()[("moved_zero_fraction", 0.95)]
+    assert lo is None and model[0.95]["moved_zero"] < paper
+    got = fill_stats[0.95]["moved_zero"]
+    assert model[0.95]["moved_zero"] - 0.03 < got < model[0.95]["moved_zero"] + 0.002, got
+    zs = [fill_stats[lf]["moved_zero"] for lf in (0.45, 0.6, 0.7, 0.8, 0.95)]
+    assert zs == sorted(zs, reverse=True)
