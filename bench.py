@@ -36,7 +36,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -67,10 +66,10 @@ def parse():
     p.add_argument("--no-side", action="store_true", help="skip pos/neg/e2e/mutation side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle timing budget")
     p.add_argument("--workload", default="scale",
-                   choices=["scale", "batched", "sweep", "random-read", "served", "mixed", "insert"],
+                   choices=["scale", "batched", "sweep", "served", "mixed", "insert"],
                    help="scale: the headline at-scale lookup (default); batched: many tables in one launch vs "
                         "one launch per table; sweep: load factor x negative rate x lookup strategy grid; "
-                        "random-read: the GPU's random 32/64-byte read ceiling; served: continuous-batching "
+                        "served: continuous-batching "
                         "request loop vs one launch per burst; mixed: insert/lookup/delete/expire mix on a "
                         "200M-slot table with timers; insert: bulk insert rate as a table fills from LF 0.85 "
                         "to 0.99")
@@ -82,6 +81,8 @@ def parse():
     p.add_argument("--serve-flush-us", type=float, default=None,
                    help="served: ... or once the oldest waiting insert burst is this old")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
+    p.add_argument("--record-traffic", metavar="CSV", default=None,
+                   help="write profiles/lookup_traffic.json from an ncu --csv log of the lookup kernel and exit")
     return p.parse_args()
 
 
@@ -153,20 +154,58 @@ def lines_of(counts) -> float:
     return float(counts[0] + counts[1] + counts[3])
 
 
-def profiled_traffic(summary: str):
-    """Per-launch DRAM bytes of the lookup kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (sha256 over the
-    files the kernel is built from), else None."""
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "lookup_traffic.json")
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the lookup kernel from the committed capture
+    (profiles/lookup_traffic.json, written by --record-traffic), if it was
+    taken on the current kernel sources (sha256 over the files the kernel is
+    built from), else None."""
     try:
-        text = open(os.path.join(ROOT, "profiles", summary)).read()
-        current = sources_sha256()
-    except OSError:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        current = sources_sha256(tuple(d["sources"]))
+    except (OSError, ValueError, KeyError):
         return None
-    m = re.search(r"sources_sha256:\s*([0-9a-f]{64})", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != current:
+    if d.get("sources_sha256") != current:
         return None
-    return float(t.group(1))
+    return float(d["traffic_bytes_per_launch"])
+
+
+_UNIT_SCALE = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
+               "nsecond": 1e-3, "usecond": 1.0, "msecond": 1e3, "second": 1e6}
+
+
+def record_traffic(csv_path: str):
+    """Write profiles/lookup_traffic.json from an ncu --csv log of the lookup
+    kernel with dram__bytes_read.sum, dram__bytes_write.sum and
+    gpu__time_duration.sum (the first captured launch), stamped with the
+    sha256 of the current kernel sources."""
+    import csv
+    rows = list(csv.DictReader(line for line in open(csv_path) if line.startswith('"')))
+    rows = [r for r in rows if "lookup_kernel" in r.get("Kernel Name", "")]
+    if not rows:
+        raise SystemExit(f"{csv_path}: no lookup_kernel rows")
+    first = rows[0]["ID"]
+    m = {}
+    for r in rows:
+        if r["ID"] == first:
+            m[r["Metric Name"]] = float(r["Metric Value"].replace(",", "")) * _UNIT_SCALE[r["Metric Unit"].lower()]
+    rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]
+    d = {"kernel": rows[0]["Kernel Name"],
+         "config": dict(zip(("log2_buckets", "log2_batch", "load_factor", "neg_rate"), TRAFFIC_CONFIG)),
+         "traffic_bytes_per_launch": int(round(rd + wr)), "dram_bytes_read": int(round(rd)),
+         "dram_bytes_write": int(round(wr)), "gpu_time_us": round(m["gpu__time_duration.sum"], 2),
+         "sources": list(LOOKUP_SOURCES), "sources_sha256": sources_sha256(),
+         "command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                    "--clock-control none -k regex:lookup_kernel -s 2 -c 1 --csv --log-file traffic.csv "
+                    "python bench.py --steps 20 --warmup 3 --no-cpu-baseline --no-side; "
+                    "python bench.py --record-traffic traffic.csv"}
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(d, f, indent=1)
+        f.write("\n")
+    print(json.dumps(d))
 
 
 class ClockSampler:
@@ -357,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = alg_bytes / per_launch / 1e9
     # the committed capture is of the default configuration only
     same = (args.log2_buckets, args.log2_batch, args.load_factor, args.neg_rate) == TRAFFIC_CONFIG
-    traffic = profiled_traffic("lookup_kernel_2e24_lf09_traffic.md") if same else None
+    traffic = profiled_traffic() if same else None
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 5), "higher_is_better": True,
@@ -777,60 +816,6 @@ def run_sweep(args):
                        "n_buckets": nb, "batch": n}, "cells": cells}
 
 
-def run_random_read(args):
-    """Random-read ceiling of this GPU: 2^26 independent reads of 32 or 64
-    bytes at random aligned offsets of buffers from 64 MiB (L2-resident) to
-    8 GiB, timed with CUDA events; then 2^26 random accesses of each request
-    shape of the line-read probe on a 4 GiB buffer."""
-    import torch
-
-    from paper_1712_09624_gb300 import workload_gpu as WG
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    n = 1 << 26
-    buf = torch.ones(8 << 30, dtype=torch.uint8, device=dev)
-    sink = torch.zeros(1, dtype=torch.int64, device=dev)
-    rows = []
-    for size in (64 << 20, 512 << 20, 1 << 30, 4 << 30, 8 << 30):
-        view = buf[:size]
-        for unit in (32, 64):
-            for w in range(3):
-                WG.random_read(view, unit, n, w + 1, sink, stream)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for r in range(10):
-                WG.random_read(view, unit, n, 100 + r, sink, stream)
-            e1.record(stream)
-            e1.synchronize()
-            sec = e0.elapsed_time(e1) / 1e3 / 10
-            rows.append({"buffer_MiB": size >> 20, "unit_B": unit, "greads_per_s": round(n / sec / 1e9, 2),
-                         "useful_GBs": round(n * unit / sec / 1e9, 1)})
-    big = [r for r in rows if r["buffer_MiB"] == 8192 and r["unit_B"] == 32][0]
-    # request shapes on a 4 GiB buffer: what one random access costs
-    shapes = {0: "1 lane x 32 B", 1: "1 lane, 2 loads of 32 B (64 B)", 2: "4 lanes x 32 B, one 128 B line",
-              3: "8 lanes x 32 B, two lines (256 B)", 4: "32 B, then a dependent 32 B in the same line",
-              5: "as above, first load with the L2::128B prefetch hint",
-              6: "cp.async, 8 lanes x 16 B per line, 32 lines per warp"}
-    view = buf[:4 << 30]
-    lines = []
-    for mode, what in shapes.items():
-        for w in range(3):
-            WG.line_read(view, mode, n, w + 1, sink, stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for r in range(10):
-            WG.line_read(view, mode, n, 100 + r, sink, stream)
-        e1.record(stream)
-        e1.synchronize()
-        sec = e0.elapsed_time(e1) / 1e3 / 10
-        lines.append({"mode": mode, "shape": what, "g_accesses_per_s": round(n / sec / 1e9, 2)})
-    return {"metric": "random 32-byte reads per second (8 GiB buffer)", "value": big["greads_per_s"],
-            "unit": "Greads/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": "random-read probe, 2^26 reads per launch"}, "rows": rows,
-            "request_shapes_4GiB": lines}
-
-
 def run_served(args):
     """Served form: 64 ports of Poisson packet bursts (32..4096 keys, 2 G
     lookups/s offered, 10% inserts of new flows, 20% unknown flows) against
@@ -1048,9 +1033,11 @@ def run_insert_load(args):
 
 def main():
     args = parse()
+    if args.record_traffic:
+        record_traffic(args.record_traffic)
+        return
     if args.workload != "scale" and args.impl == "ours":
-        run = {"batched": run_batched, "sweep": run_sweep, "random-read": run_random_read,
-               "served": run_served, "mixed": run_mixed, "insert": run_insert_load}[args.workload]
+        run = {"batched": run_batched, "sweep": run_sweep, "served": run_served, "mixed": run_mixed, "insert": run_insert_load}[args.workload]
         print(json.dumps(run(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -278,7 +278,9 @@ int ckpp_bulk_delete(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32
  *    routine. It clears the parts of the array that must start at zero.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture. Call with the table's device current.
+ *    before any stream capture. Call with the table's device current. The
+ *    address is kept for the life of the process: after cudaDeviceReset,
+ *    reload libckpp.so before calling again.
  *  - All calls share the one array: calls whose work overlaps on the GPU
  *    (different streams, or several tables at once) race and corrupt each
  *    other's results. Order them on one stream or with events.

@@ -40,27 +40,13 @@ int ckpp_wl_keys_at(uint64_t seed, const uint64_t* idx, uint64_t n, uint8_t* out
 int ckpp_wl_lookup_batch(uint64_t seed, uint64_t batch_id, uint64_t n, uint64_t n_inserted, double neg_rate,
                          uint8_t* out_keys, uint8_t* expect_found, uint64_t* expect_value, ckpp_wl_stream_t stream);
 
-/* Random-read probe (measurement, not traffic): n independent reads of `unit`
- * bytes (32 or 64) at scrambled unit-aligned offsets of buf (`bytes` a power
- * of two, 64-byte aligned device memory). sink: device uint64 that the loads
- * feed (left unchanged in practice). Time it with events on `stream`. */
-int ckpp_wl_random_read(const uint8_t* buf, uint64_t bytes, uint32_t unit, uint64_t n, uint64_t seed,
-                        uint64_t* sink, ckpp_wl_stream_t stream);
-
-/* Line-read probe (measurement): n random accesses to buf (`bytes` a power of
- * two >= 256, 256-byte aligned device memory), each of one shape (mode):
- *   0  one lane reads 32 bytes;
- *   1  one lane reads two adjacent 32-byte sectors with two loads;
- *   2  4 lanes read the 4 sectors of one 128-byte line in one instruction;
- *   3  8 lanes read two adjacent lines (256 bytes) in one instruction;
- *   4  one lane reads 32 bytes, then (dependent on it) another sector of the
- *      same line;
- *   5  as 4, with the .L2::128B prefetch-size hint on the first load;
- *   6  each warp copies 32 lines into shared memory with cp.async (8 lanes x
- *      16 bytes per line, four lines per instruction).
- * sink as for ckpp_wl_random_read. Returns 0, -1 (bad argument) or -2. */
-int ckpp_wl_line_read(const uint8_t* buf, uint64_t bytes, int mode, uint64_t n, uint64_t seed, uint64_t* sink,
-                      ckpp_wl_stream_t stream);
+/* L2 read probe (measurement): `passes` streaming reads of buf (`bytes` a
+ * multiple of 16, 16-byte aligned device memory; a buffer smaller than L2 is
+ * read from L2 after the first pass) with 16-byte ld.global.cg loads, one
+ * grid of 8 blocks of 256 threads per SM. sink: device uint64 the loads feed
+ * (left unchanged in practice). Bytes read = bytes x passes; time it with
+ * events on `stream`. Returns 0, -1 (bad argument) or -2. */
+int ckpp_wl_l2_read(const uint8_t* buf, uint64_t bytes, uint32_t passes, uint64_t* sink, ckpp_wl_stream_t stream);
 
 /* Host-link probe (measurement): the host I/O of a lookup on host buffers,
  * without a table. keys [n][16] (16-byte aligned), out_vals [n] (8-byte

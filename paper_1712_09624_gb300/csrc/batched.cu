@@ -10,8 +10,10 @@
 // order (up to eight chunks per draw, so one counter can serve the whole
 // grid), so that (as with a plain launch's short-lived blocks) the resident
 // warps read keys and write results within one narrow window of the batch. A
-// key finds its job by binary search in the prefix array, and the warp runs
-// the cooperative lookup of probe.cuh over keys of possibly different tables.
+// lane finds its key's job in the prefix array by galloping forward from the
+// job of its previous key (keys are drawn in increasing order), and the warp
+// runs the cooperative lookup of probe.cuh over keys of possibly different
+// tables.
 // The last warp to finish resets the counter for the next launch, so
 // launches that use one batch descriptor must not overlap on the GPU.
 // Tuning (picked by the autotuner):

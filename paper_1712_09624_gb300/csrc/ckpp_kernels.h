@@ -1,12 +1,35 @@
 // Internal launchers of the GB300 Cuckoo++ kernels (host side, C++).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "ckpp_device.cuh"
 
 namespace ckpp {
+
+// Streaming multiprocessors of the current device, queried once per device
+// and cached (grid sizes of the grid-stride and persistent kernels are
+// multiples of it). A failed query is not cached and returns 1, which keeps a
+// grid valid; the launch that follows reports the device's error.
+inline int device_sm_count() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 1;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 
 // Device scratch for one insert or delete batch (carved out of the caller's
 // workspace buffer, see workspace_layout in api.cu).

@@ -698,7 +698,8 @@ cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, 
   const uint64_t n_vec = ((uint64_t)ws.m_mask + 1) / 2;
   const uint64_t want = (n_vec > counter_words ? n_vec : counter_words);
   const uint64_t blocks = (want + kThreads - 1) / kThreads;
-  workspace_clear<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), kThreads, 0, s>>>(
+  const uint64_t cap = 16ull * device_sm_count();
+  workspace_clear<<<(unsigned)(blocks < cap ? blocks : cap), kThreads, 0, s>>>(
       ws.counters, counter_words, reinterpret_cast<uint4*>(ws.set), n_vec);
   return cudaGetLastError();
 }
@@ -715,10 +716,11 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
   if (e != cudaSuccess) return e;
   // lists: phase 1 -> pending [0] -> move1 -> retry [3] -> grid search ->
   // pending [5] -> block search -> retry [6] -> last search
-  e = launch_chained(insert_move1, 152 * 8, kThreads, s, ts, keys, vals, now, expiry, status, ws,
+  const unsigned sms = (unsigned)device_sm_count();
+  e = launch_chained(insert_move1, sms * 8, kThreads, s, ts, keys, vals, now, expiry, status, ws,
                      (const uint32_t*)ws.pending, (const uint32_t*)(ws.counters + 0), ws.retry, ws.counters + 3);
   if (e != cudaSuccess) return e;
-  e = launch_chained(insert_phase2<kP2Threads, 96, 4>, 152 * 4, kP2Threads, s, ts, keys, vals, now, expiry, status,
+  e = launch_chained(insert_phase2<kP2Threads, 96, 4>, sms * 4, kP2Threads, s, ts, keys, vals, now, expiry, status,
                      ws, (const uint32_t*)ws.retry, (const uint32_t*)(ws.counters + 3), ws.pending, ws.counters + 5,
                      0xFFFFFFFFu);
   if (e != cudaSuccess) return e;
@@ -734,7 +736,7 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
                      (uint32_t*)nullptr, kLastPassKeys);
   if (e != cudaSuccess) return e;
   const unsigned fin_blocks = grid_for(n, kThreads);
-  return launch_chained(insert_fixup_finish, fin_blocks > 152 * 2 ? fin_blocks : 152 * 2, kThreads, s, ts, n, status,
+  return launch_chained(insert_fixup_finish, fin_blocks > sms * 2 ? fin_blocks : sms * 2, kThreads, s, ts, n, status,
                         ws);
 }
 

@@ -34,13 +34,19 @@ std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Address of the scratch array on the current device (set-up on first use).
+// The address is cached for the life of the process: after cudaDeviceReset the
+// module is loaded again and the cached address is no longer valid, so a
+// process that resets a device must reload libckpp.so before calling again.
 int scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CKPP_ECUDA;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CKPP_ECUDA;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();  // clear it, so that a later call's launch check does not report it
+      return CKPP_ECUDA;
+    }
     g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];

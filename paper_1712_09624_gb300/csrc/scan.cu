@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) stats_kernel(TableView t, uint32_t now, u
 
 unsigned scan_blocks(uint64_t nb) {
   const uint64_t want = (nb + 255) / 256;
-  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 8));
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 8ull * device_sm_count()));
 }
 
 }  // namespace

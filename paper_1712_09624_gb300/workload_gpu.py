@@ -25,10 +25,8 @@ def _load():
     L.ckpp_wl_lookup_batch.argtypes = [u64, u64, u64, u64, C.c_double, vp, vp, vp, vp]
     L.ckpp_wl_keys_at.restype = C.c_int
     L.ckpp_wl_keys_at.argtypes = [u64, vp, u64, vp, vp]
-    L.ckpp_wl_random_read.restype = C.c_int
-    L.ckpp_wl_random_read.argtypes = [vp, u64, C.c_uint32, u64, u64, vp, vp]
-    L.ckpp_wl_line_read.restype = C.c_int
-    L.ckpp_wl_line_read.argtypes = [vp, u64, C.c_int, u64, u64, vp, vp]
+    L.ckpp_wl_l2_read.restype = C.c_int
+    L.ckpp_wl_l2_read.argtypes = [vp, u64, C.c_uint32, vp, vp]
     L.ckpp_wl_host_io.restype = C.c_int
     L.ckpp_wl_host_io.argtypes = [vp, u64, vp, vp, vp]
     return L
@@ -78,18 +76,12 @@ def lookup_batch(seed: int, n: int, n_inserted: int, neg_rate: float, batch_id: 
     return keys, found, value
 
 
-def random_read(buf: torch.Tensor, unit: int, n: int, seed: int, sink: torch.Tensor, stream=None):
-    """Launch the random-read probe over the whole of buf (a power-of-two-sized uint8 CUDA tensor)."""
-    rc = _lib.ckpp_wl_random_read(buf.data_ptr(), buf.numel(), unit, n, seed, sink.data_ptr(), _stream(stream))
-    if rc:
-        raise RuntimeError(f"ckpp_wl_random_read failed ({rc})")
-
-
-def line_read(buf: torch.Tensor, mode: int, n: int, seed: int, sink: torch.Tensor, stream=None):
-    """n random accesses of one request shape (see ckpp_wl_line_read)."""
-    rc = _lib.ckpp_wl_line_read(buf.data_ptr(), buf.numel(), mode, n, seed, sink.data_ptr(), _stream(stream))
+def l2_read(buf: torch.Tensor, passes: int, sink: torch.Tensor, stream=None):
+    """Stream buf (a uint8 CUDA tensor, size a multiple of 16) passes times
+    through the L2 read probe (ckpp_wl_l2_read)."""
+    rc = _lib.ckpp_wl_l2_read(buf.data_ptr(), buf.numel(), passes, sink.data_ptr(), _stream(stream))
     if rc != 0:
-        raise RuntimeError(f"ckpp_wl_line_read failed ({rc})")
+        raise RuntimeError(f"ckpp_wl_l2_read failed ({rc})")
 
 
 def host_io(keys: torch.Tensor, out_vals: torch.Tensor, out_found: torch.Tensor, stream=None):

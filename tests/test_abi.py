@@ -30,8 +30,8 @@ def test_workload_library_exports(K):
     text = open(os.path.join(ROOT, "include", "ckpp_workload.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = sorted(set(re.findall(r"\b(ckpp_wl_[a-z_0-9]+)\s*\(", text)))
-    assert names == ["ckpp_wl_fill_keys", "ckpp_wl_host_io", "ckpp_wl_keys_at", "ckpp_wl_line_read",
-                     "ckpp_wl_lookup_batch", "ckpp_wl_random_read"]
+    assert names == ["ckpp_wl_fill_keys", "ckpp_wl_host_io", "ckpp_wl_keys_at", "ckpp_wl_l2_read",
+                     "ckpp_wl_lookup_batch"]
     lib = ctypes.CDLL(build.WL_LIB)
     for name in names:
         assert hasattr(lib, name)

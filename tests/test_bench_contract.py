@@ -83,3 +83,33 @@ def test_roofline_byte_counts():
     assert bench.line_bytes_of(counts, n) == 128 * (prim + sec + line1) + 25 * n
     # the headline batch's counts give the per-lookup figures the bench reports
     assert abs(bench.alg_bytes_of([1.0, 0.0645, 0.5], 1) - 75.06) < 0.01
+
+
+def test_traffic_record_and_read(tmp_path):
+    """--record-traffic turns an ncu --csv log of the lookup kernel (units as
+    ncu prints them) into the traffic data file, stamped with the current
+    sources' sha256; the bench reports it only while that stamp matches."""
+    bench = load_bench()
+    name = "void ckpp::<unnamed>::lookup_kernel<0, 0, 0, 0>(ckpp::TableView)"
+    head = '"ID","Process ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = [("0", "dram__bytes_read.sum", "Gbyte", "2.5"), ("0", "dram__bytes_write.sum", "Mbyte", "1,500.5"),
+            ("0", "gpu__time_duration.sum", "usecond", "400.0"), ("1", "dram__bytes_read.sum", "Gbyte", "9.0")]
+    csv_path = tmp_path / "t.csv"
+    csv_path.write_text("==PROF== noise\n" + head + "".join(f'"{i}","1","{name}","{m}","{u}","{v}"\n'
+                                                           for i, m, u, v in rows))
+    bench.TRAFFIC_FILE = str(tmp_path / "traffic.json")
+    bench.record_traffic(str(csv_path))
+    d = json.loads(open(bench.TRAFFIC_FILE).read())
+    assert d["traffic_bytes_per_launch"] == 2_500_000_000 + 1_500_500_000
+    assert d["gpu_time_us"] == 400.0 and d["sources_sha256"] == bench.sources_sha256()
+    assert bench.profiled_traffic() == float(d["traffic_bytes_per_launch"])
+    d["sources_sha256"] = "0" * 64
+    open(bench.TRAFFIC_FILE, "w").write(json.dumps(d))
+    assert bench.profiled_traffic() is None
+
+
+def test_committed_traffic_file_names_the_lookup_sources():
+    bench = load_bench()
+    d = json.loads(open(os.path.join(ROOT, "profiles", "lookup_traffic.json")).read())
+    assert tuple(d["sources"]) == bench.LOOKUP_SOURCES
+    assert d["config"] == dict(zip(("log2_buckets", "log2_batch", "load_factor", "neg_rate"), bench.TRAFFIC_CONFIG))
