@@ -19,6 +19,8 @@ One JSON line on rank 0. Beside the headline `value` it reports:
   at_100M_entries  the same measurement on the same table when the fill stands at exactly
              100,000,000 entries (LF 0.745);
   mutations  bulk_insert / bulk_delete / expire throughput on the same table;
+  small_config  the small configuration (2^17 buckets x 8, LF 0.9, 1M-key
+             batch), L2-resident, against the measured L2 read bandwidth;
   cpu_baseline  the CPU oracle's lookup rate on a bounded sample (rank 0, N=1).
 
 --impl reference times the CPU oracle itself (the reference arm of this
@@ -436,10 +438,84 @@ def run_ours(args, rank, world, local_rank):
             out["at_100M_entries"] = at_100m
         out["e2e"] = e2e_lookup(args, table, q, dev, stream)
         out["mutations"] = mutation_rates(table, dev, stream, ins_times, seed)
+        out["small_config"] = small_config(args, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, fill, q, nb, seed)
         out["cpu_baseline_all_cores"] = cpu_baseline_share_nothing(args)
     return out
+
+
+def l2_read_peak(dev, stream, mib: int = 48, passes: int = 20, steps: int = 10):
+    """Streaming read bandwidth of a buffer that sits in L2 (the L2 read probe
+    of the workload library, 16-byte ld.global.cg loads), by CUDA events:
+    bytes x passes per launch over the launch time, best of `steps` launches
+    after 3 warm-ups."""
+    import torch
+
+    from paper_1712_09624_gb300 import workload_gpu as WG
+    buf = torch.ones(mib << 20, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        WG.l2_read(buf, passes, sink, stream)
+    best = None
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        WG.l2_read(buf, passes, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        best = sec if best is None else min(best, sec)
+    return (mib << 20) * passes / best / 1e9
+
+
+def small_config(args, dev, stream, steps: int = 200, warmup: int = 5):
+    """The small configuration: 2^17 buckets x 8 slots filled to LF 0.9
+    (943,718 keys), one 2^20-key lookup batch with 50% negatives. The table
+    (32 MiB), the keys (16 MiB) and the results (9 MiB) all sit in L2, so the
+    batch is measured against the L2 read bandwidth (measured here by the L2
+    read probe) rather than the HBM copy peak. Results are checked against the
+    workload's key -> value map."""
+    import torch
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    from paper_1712_09624_gb300 import workload as W
+    from paper_1712_09624_gb300.table import FlowTable
+    nb, lf, n, neg = 1 << 17, 0.9, 1 << 20, 0.5
+    fill = W.fill(args.seed, int(lf * nb * 8))
+    t = FlowTable(nb, seed=args.seed, device=dev)
+    st = t.insert(fill.keys, fill.values, 0, 0, stream)
+    q = W.lookup_batch(args.seed, n, fill, neg)
+    kk = torch.from_numpy(q.keys).to(dev)
+    ov = torch.empty(n, dtype=torch.int64, device=dev)
+    of = torch.empty(n, dtype=torch.bool, device=dev)
+    K.ckpp_bulk_lookup(t.handle, kk, ov, of, 0, 0, stream)
+    torch.cuda.synchronize()
+    exact = bool((st == K.ST_INSERTED).all()) and bool((of.cpu().numpy() == q.expect_found).all()) and \
+        bool((ov.cpu().numpy().view(np.uint64) == q.expect_value).all())
+    c = t.probe_counts(kk).cpu().numpy()
+    for _ in range(warmup):
+        K.ckpp_bulk_lookup(t.handle, kk, ov, of, 0, 0, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        K.ckpp_bulk_lookup(t.handle, kk, ov, of, 0, 0, stream)
+    e1.record(stream)
+    e1.synchronize()
+    per = e0.elapsed_time(e1) / 1e3 / steps
+    l2 = l2_read_peak(dev, stream)
+    hbm, _ = measured_peaks()
+    b = alg_bytes_of(c, n)
+    return {"workload": "plain Cuckoo++ small: 2^17 buckets x 8 slots, LF 0.9, 1M-key bulk_lookup, 50% negative",
+            "value": round(n / per / 1e9, 4), "unit": UNIT, "steps": steps, "ms_per_step": round(per * 1e3, 5),
+            "exact": exact, "l2": "table, keys and results L2-resident; no flush",
+            "alg_bytes_per_lookup": round(b / n, 3), "line_requests_per_lookup": round(lines_of(c) / n, 5),
+            "roofline": {"bound": "l2", "achieved": round(b / per / 1e9, 1), "peak": round(l2, 1), "unit": "GB/s",
+                         "frac": round(b / per / 1e9 / l2, 4),
+                         "peak_kind": "measured L2 streaming read (ckpp_wl_l2_read, 48 MiB buffer, 20 passes, "
+                                      "best of 10 launches)",
+                         "whole_lines_frac": round(line_bytes_of(c, n) / per / 1e9 / l2, 4),
+                         "frac_of_hbm_copy": round(b / per / 1e9 / hbm, 4)}}
 
 
 def e2e_lookup(args, table, q, dev, stream):
@@ -857,7 +933,14 @@ def run_mixed(args):
     - delete 250K live flows (uniform);
     - expire (full scan).
     A flow is named by its index in one global sequence of keys (the device
-    generator), so the live window is known without host bookkeeping."""
+    generator, value = index), so the live window is known without host
+    bookkeeping. Every batch's results are checked outside its timed region,
+    against the sequential answer kept in a device map of deleted flows: every
+    insert status is INSERTED (new flows); a lookup hits exactly the flows of
+    the live window that no delete removed, with the flow's index as value;
+    a delete batch reports DELETED for exactly its distinct flows that were
+    still there. The warm fill's sub-batches expire in order (Sec. 4.2), and
+    the window starts past the sub-batches whose expiry has passed."""
     import torch
 
     from paper_1712_09624_gb300 import _ckpp as K
@@ -906,6 +989,12 @@ def run_mixed(args):
     st_ins = torch.empty(n_ins, dtype=torch.uint8, device=dev)
     st_del = torch.empty(n_del, dtype=torch.uint8, device=dev)
     n_expired = torch.zeros(1, dtype=torch.int64, device=dev)
+    total_flows = warm + n_ins * int((ops == 0).sum())
+    gone = torch.zeros(total_flows, dtype=torch.bool, device=dev)  # flows a delete removed
+    bad = {"insert_status": torch.zeros(1, dtype=torch.int64, device=dev),
+           "lookup": torch.zeros(1, dtype=torch.int64, device=dev),
+           "delete_status": torch.zeros(1, dtype=torch.int64, device=dev)}
+    hits_expected = torch.zeros(1, dtype=torch.int64, device=dev)
     for b, op in enumerate(ops):
         now += 1
         lo_live = min(warm, per * (now // 20))  # warm sub-batches whose expiry passed are dead
@@ -932,10 +1021,21 @@ def run_mixed(args):
         else:
             K.ckpp_expire(t.handle, now, n_expired, stream)
         e1.record(stream)
-        if op == 1:
+        # checks, after the timed region on the same stream
+        if op == 0:
+            bad["insert_status"] += (st_ins != K.ST_INSERTED).sum()
+        elif op == 1:
+            want = ~gone[idx]
             hits += out_f.sum()
+            hits_expected += want.sum()
+            bad["lookup"] += ((out_f != want.to(torch.uint8)) | (want & (out_v != idx))).sum()
         elif op == 2:
-            deleted += (st_del == K.ST_DELETED).sum()
+            del_ok = st_del == K.ST_DELETED
+            deleted += del_ok.sum()
+            uniq = torch.unique(idx)
+            # DELETED exactly once per distinct flow still there, never for a flow already gone
+            bad["delete_status"] += (del_ok.sum() - (~gone[uniq]).sum()).abs() + (del_ok & gone[idx]).sum()
+            gone[uniq] = True
         e1.synchronize()
         time_by[op] += e0.elapsed_time(e1) / 1e3
         count_by[op] += 1
@@ -956,6 +1056,9 @@ def run_mixed(args):
                        "n_buckets": nb, "warm_entries": warm, "batches": int(args.mixed_batches),
                        "warm_fill_s": round(fill_s, 1)},
             "per_op": per_op, "lookup_hit_rate": round(float(hits.item()) / max(1, keys_by[1]), 4),
+            "lookup_hit_rate_expected": round(float(hits_expected.item()) / max(1, keys_by[1]), 4),
+            "mismatches": {k: int(v.item()) for k, v in bad.items()},
+            "results_match": all(int(v.item()) == 0 for v in bad.values()) and t.sync_status() == 0,
             "deleted_live": int(deleted.item()), "expired": int(n_expired.item()),
             "table_after": {"live": st["n_live"], "occupied": st["n_occupied"],
                             "load_factor_live": round(st["n_live"] / (nb * 8), 4),

@@ -7,18 +7,22 @@ runs in real time on the host:
   footprint;
 * it asks the turn planner (``serve_policy.TurnPlanner``: admission within an
   HBM footprint budget, write coalescing) what to launch;
-* it launches that without waiting for the previous launch: the turn's
-  lookups as one persistent ``ckpp_batch_lookup`` (one job per burst), and,
-  when the planner flushes them, the waiting inserts as one multi-table
+* it launches that without waiting for the previous launch, all on one
+  stream, in the turn's order: the lookups whose table has no waiting insert
+  as one persistent ``ckpp_batch_lookup`` (one job per burst); when the
+  planner flushes them, the waiting inserts as one multi-table
   ``ckpp_batch_insert`` (an insert call has a fixed cost of several dependent
-  kernels, so coalescing writes keeps that cost from every turn); both on one
-  stream, so the next launch is queued while the current one runs.
+  kernels, so coalescing writes keeps that cost from every turn); then the
+  lookups that were held behind those inserts as a second batched lookup. The
+  next turn is queued while the current one runs.
 
-Lookups read flows of the warm fill (and unknown flows); inserts add new
-flows. Lookup results therefore do not depend on how bursts are grouped, and
-every burst's result equals what it gets when run alone; the tests check
-this. Per-burst latency is completion time (the launch's CUDA event, mapped
-to host time) minus arrival time.
+Each table applies its lookups and inserts in arrival order (the planner's
+rule), so every burst gets the result it gets when every burst runs alone in
+arrival order. Lookups read flows of the warm fill, unknown flows, and (a
+``raw_fraction`` of their keys) flows inserted by earlier insert bursts of
+the same table during the run; the tests compare every result with that
+sequential answer. Per-burst latency is completion time (the launch's CUDA
+event, mapped to host time) minus arrival time.
 
 The comparison arm serves the same arrival stream with one plain launch per
 burst (``ckpp_bulk_lookup`` / ``ckpp_bulk_insert``) as bursts arrive.
@@ -67,18 +71,28 @@ class Service:
             K.ckpp_bulk_insert(tb.handle, k, v, s, ws, 0, 0, cuda)
             self.tables.append(tb)
         del ws
-        # per-table lookup pools (keys, expected answers, outputs), arrival order
-        look = ~st.insert
-        self.pools = []
-        for t in range(cfg.n_tables):
-            n = int(st.size[look & (st.table == t)].sum())
-            keys, ef, ev = WG.lookup_batch(cfg.seed * 1000 + t, n, self.warm, cfg.neg_rate, 1, device=dev)
-            self.pools.append(dict(keys=keys, expect_found=ef, expect_value=ev,
-                                   vals=torch.zeros(n, dtype=torch.int64, device=dev),
-                                   found=torch.zeros(n, dtype=torch.uint8, device=dev)))
         # one insert pool for all tables, arrival order: new flows never in any table
         n_ins = int(st.size[st.insert].sum())
         self.ins_keys, self.ins_vals = WG.fill_keys(cfg.seed * 1000 + 999_999, 0, n_ins, dev)
+        # per-table lookup pools (keys, expected answers, outputs), arrival order; the stream's
+        # read-after-write keys name flows of the insert pool that an earlier burst of the table
+        # inserts, so their expected answer is that flow's value
+        look = ~st.insert
+        self.pools = []
+        raw_bounds = np.searchsorted(st.raw_table, np.arange(cfg.n_tables + 1))  # raw_table is sorted
+        for t in range(cfg.n_tables):
+            n = int(st.size[look & (st.table == t)].sum())
+            keys, ef, ev = WG.lookup_batch(cfg.seed * 1000 + t, n, self.warm, cfg.neg_rate, 1, device=dev)
+            lo, hi = int(raw_bounds[t]), int(raw_bounds[t + 1])
+            if hi > lo:
+                pos = torch.from_numpy(st.raw_pos[lo:hi]).to(dev)
+                src = torch.from_numpy(st.raw_src[lo:hi]).to(dev)
+                keys[pos] = self.ins_keys[src]
+                ef[pos] = 1
+                ev[pos] = self.ins_vals[src]
+            self.pools.append(dict(keys=keys, expect_found=ef, expect_value=ev,
+                                   vals=torch.zeros(n, dtype=torch.int64, device=dev),
+                                   found=torch.zeros(n, dtype=torch.uint8, device=dev)))
         tids = np.repeat(st.table[st.insert], st.size[st.insert]).astype(np.int32)
         self.ins_tables = torch.from_numpy(tids).to(dev)
         self.ins_status = torch.zeros(n_ins, dtype=torch.uint8, device=dev)
@@ -116,7 +130,7 @@ class Service:
         pool_found = np.array([p["found"].data_ptr() for p in self.pools], np.uint64)
         handles = [t.handle for t in self.tables]
         ws_small = torch.empty(K.ckpp_workspace_bytes(cfg.max_burst), dtype=torch.uint8, device=dev)
-        launches = flushes = 0
+        launches = flushes = held = 0
         starts, groups, gpu_busy = [], [], []
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -152,7 +166,8 @@ class Service:
                     continue
                 if action == "none":
                     continue
-                look_idx = turn.lookups
+                look_idx = np.concatenate([turn.lookups, turn.lookups_after])
+                n_first = turn.lookups.shape[0]
                 nj = look_idx.shape[0]
                 # the turn's host work comes first, so that its launches go out back to back
                 if nj:
@@ -166,9 +181,18 @@ class Service:
                     view["out_found"][:nj] = pool_found[tb] + off
                     view["n"][:nj] = st.size[look_idx]
                     view["table"][:nj] = tb
+                    nbytes_jobs = nj * K.JOB_BYTES
+                    self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
                 ev_start = torch.cuda.Event(enable_timing=True)
                 ev_start.record(cuda)
-                if turn.inserts:  # one contiguous range of the insert pool
+                # 1. lookups whose table has no waiting insert (the job count is known here: the
+                #    prefix scan is sized to it, no device count)
+                if n_first:
+                    K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs, n_first, None, 0, self.batch.tuning,
+                                        cuda)
+                    launches += 1
+                # 2. the waiting inserts, one contiguous range of the insert pool
+                if turn.inserts:
                     first = turn.insert_first
                     lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
                                           self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
@@ -176,12 +200,12 @@ class Service:
                                           self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
                     launches += 1
                     flushes += 1
-                if nj:
-                    nbytes_jobs = nj * K.JOB_BYTES
-                    self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
-                    # the job count is known here: the prefix scan is sized to it (no device count)
-                    K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs, nj, None, 0, self.batch.tuning, cuda)
+                # 3. lookups held behind those inserts
+                if nj > n_first:
+                    K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs[n_first * K.JOB_BYTES:], nj - n_first,
+                                        None, 0, self.batch.tuning, cuda)
                     launches += 1
+                    held += nj - n_first
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(cuda)
                 if nj:
@@ -231,11 +255,14 @@ class Service:
             "lookup_latency_us": percentiles(lat[keep & lk]),
             "insert_latency_us": percentiles(lat[keep & st.insert]),
             "insert_flushes": flushes if mode == "batched" else None,
+            "held_lookup_bursts": held if mode == "batched" else None,
+            "read_after_write_keys": int(st.raw_pos.shape[0]),
         }
 
     def check(self) -> dict:
-        """Every lookup output equals the workload's map; every insert status is
-        INSERTED and the inserted flows are found afterwards."""
+        """Every lookup output equals the sequential answer (the warm fill's map
+        plus the flows inserted by earlier bursts of the same table); every
+        insert status is INSERTED."""
         ok_lookups = all(bool(torch.equal(p["found"], p["expect_found"])) and
                          bool(torch.equal(p["vals"], p["expect_value"])) for p in self.pools)
         ok_inserts = bool((self.ins_status == K.ST_INSERTED).all())

@@ -20,8 +20,18 @@ Turn planner, called whenever the loop is free to launch:
 * write coalescing: admitted insert bursts wait and go out together (one
   multi-table insert call over a contiguous range of the insert pool) once
   ``insert_flush_keys`` keys wait, the oldest has waited ``insert_flush_s``,
-  the stream has ended, or waiting inserts hold the footprint budget that a
-  newly arrived burst needs.
+  a lookup held behind them has waited ``lookup_hold_s``, the stream has
+  ended, or waiting inserts hold the footprint budget that a newly arrived
+  burst needs;
+* per-table arrival order: on every table, lookups and inserts take effect in
+  the order they arrived, so each lookup sees exactly the inserts of its table
+  that arrived before it (what it would see if every burst ran alone, one
+  after the other). A turn launches up to three steps on one stream, in this
+  order: the lookups whose table has no waiting insert; the flush of the
+  waiting inserts; the lookups that arrived while an insert of their table was
+  waiting (held until that flush). An insert that arrives for a table with a
+  held lookup ends the turn's admission and forces the flush, so that the held
+  lookup cannot see it; it starts the next group of waiting inserts.
 """
 
 from __future__ import annotations
@@ -48,6 +58,8 @@ class ServeConfig:
     footprint_bytes: int = 256 << 20
     insert_flush_keys: int = 32768    # coalesced inserts go out once this many keys wait ...
     insert_flush_s: float = 300e-6    # ... or the oldest has waited this long
+    lookup_hold_s: float = 100e-6     # ... or a lookup held behind them has waited this long
+    raw_fraction: float = 0.2         # share of lookup keys naming flows inserted earlier in the run
     seed: int = 7
 
 
@@ -59,6 +71,12 @@ class Stream:
     size: np.ndarray       # keys in the burst
     insert: np.ndarray     # True: insert of new flows
     offset: np.ndarray     # lookups: offset in the table's lookup pool; inserts: offset in the insert pool
+    # lookup keys that name flows inserted earlier in the run (read-after-write): key raw_pos of
+    # table raw_table's lookup pool is key raw_src of the insert pool, whose insert burst arrived
+    # before the lookup burst; sorted by table
+    raw_table: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    raw_pos: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    raw_src: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
 
 
 def draw_stream(cfg: ServeConfig) -> Stream:
@@ -83,28 +101,68 @@ def draw_stream(cfg: ServeConfig) -> Stream:
         sel = look & (table == t)
         s = size[sel]
         offset[sel] = np.cumsum(s) - s
-    return Stream(arrival, table, size, insert, offset)
+    raw = draw_read_after_write(cfg, rng, table, size, insert, offset)
+    return Stream(arrival, table, size, insert, offset, *raw)
+
+
+def draw_read_after_write(cfg: ServeConfig, rng, table, size, insert, offset):
+    """Each key of a lookup burst, with probability raw_fraction, names a flow
+    that an insert burst of the same table inserted earlier in the run
+    (uniform over all such flows so far); keys of a burst with no earlier
+    insert on its table are left as drawn. Returns (raw_table, raw_pos,
+    raw_src): the table, the position in that table's lookup pool and the
+    insert-pool index of every such key."""
+    out_t, out_p, out_s = [], [], []
+    if cfg.raw_fraction <= 0:
+        return (np.zeros(0, np.int64),) * 3
+    for t in range(cfg.n_tables):
+        bursts = np.flatnonzero(table == t)  # arrival order
+        starts, lens = [], []                # insert-pool ranges of the table's inserts so far
+        cum = np.zeros(1, np.int64)
+        for b in bursts:
+            if insert[b]:
+                starts.append(int(offset[b]))
+                lens.append(int(size[b]))
+                cum = np.concatenate([cum, [cum[-1] + int(size[b])]])
+                continue
+            if not starts:
+                continue
+            m = int(rng.binomial(int(size[b]), cfg.raw_fraction))
+            if m == 0:
+                continue
+            pos = offset[b] + rng.choice(int(size[b]), m, replace=False)
+            u = rng.integers(0, int(cum[-1]), m)
+            r = np.searchsorted(cum, u, side="right") - 1
+            src = np.asarray(starts, np.int64)[r] + (u - cum[r])
+            out_t.append(np.full(m, t, np.int64))
+            out_p.append(pos.astype(np.int64))
+            out_s.append(src.astype(np.int64))
+    if not out_t:
+        return (np.zeros(0, np.int64),) * 3
+    return np.concatenate(out_t), np.concatenate(out_p), np.concatenate(out_s)
 
 
 @dataclass
 class Turn:
-    """What one turn launches."""
+    """What one turn launches, in this order: ``lookups``, then the flush of
+    ``inserts``, then ``lookups_after``."""
     admitted: slice                 # bursts admitted this turn (arrival order)
-    lookups: np.ndarray             # lookup bursts to launch now
+    lookups: np.ndarray             # lookup bursts whose table has no waiting insert
     inserts: list = field(default_factory=list)  # insert bursts to launch now, in arrival order
     insert_first: int = 0           # insert-pool offset of inserts[0]
     insert_keys: int = 0            # keys in inserts (a contiguous range of the insert pool)
+    lookups_after: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))  # held behind inserts
     nbytes: int = 0                 # staging footprint the turn's bursts release when it completes
 
     @property
     def done(self) -> np.ndarray:
         """The bursts that complete with this turn."""
-        return np.concatenate([self.lookups, np.asarray(self.inserts, np.int64)])
+        return np.concatenate([self.lookups, np.asarray(self.inserts, np.int64), self.lookups_after])
 
 
 class TurnPlanner:
-    """Admission and write coalescing over a pre-drawn stream (module doc).
-    ``plan`` returns one of
+    """Admission, write coalescing and per-table ordering over a pre-drawn
+    stream (module doc). ``plan`` returns one of
       ("idle", None, wake)  nothing to do before host time ``wake``;
       ("block", None, 0)    the budget is full: wait for the oldest launch;
       ("none", None, 0)     bursts were admitted, nothing to launch yet;
@@ -118,30 +176,42 @@ class TurnPlanner:
         self.nxt = 0               # first burst not yet admitted
         self.pending: list = []    # admitted insert bursts not yet launched
         self.pending_keys = 0
+        self.pending_tables: dict = {}  # table -> waiting insert bursts
+        self.held: list = []       # admitted lookups waiting for the flush of their table's inserts
+        self.held_tables: set = set()
         self.flight_bytes = 0      # footprint admitted and not yet completed
 
     def finished(self) -> bool:
         """Every burst admitted and launched."""
-        return self.nxt >= self.n and not self.pending
+        return self.nxt >= self.n and not self.pending and not self.held
 
     def _flush_due(self, now: float) -> bool:
         st, cfg = self.st, self.cfg
-        return bool(self.pending) and (self.pending_keys >= cfg.insert_flush_keys or self.nxt >= self.n or
-                                       now - st.arrival[self.pending[0]] >= cfg.insert_flush_s)
+        if not self.pending:
+            return False
+        return bool(self.pending_keys >= cfg.insert_flush_keys or self.nxt >= self.n or
+                    now - st.arrival[self.pending[0]] >= cfg.insert_flush_s or
+                    (self.held and now - st.arrival[self.held[0]] >= cfg.lookup_hold_s))
+
+    def _wake(self, now: float) -> float:
+        st, cfg = self.st, self.cfg
+        wake = st.arrival[self.nxt] if self.nxt < self.n else now
+        if self.pending:
+            wake = min(wake, st.arrival[self.pending[0]] + cfg.insert_flush_s)
+        if self.held:
+            wake = min(wake, st.arrival[self.held[0]] + cfg.lookup_hold_s)
+        return float(wake)
 
     def plan(self, now: float, outstanding: bool):
         st, cfg = self.st, self.cfg
         arrived = self.nxt < self.n and st.arrival[self.nxt] <= now
         flush = self._flush_due(now)
         if not arrived and not flush:
-            wake = st.arrival[self.nxt] if self.nxt < self.n else now
-            if self.pending:
-                wake = min(wake, st.arrival[self.pending[0]] + cfg.insert_flush_s)
-            return "idle", None, float(wake)
+            return "idle", None, self._wake(now)
         sel = slice(self.nxt, self.nxt)
+        lookups = []
         if arrived:
             hi = int(np.searchsorted(st.arrival, now, side="right"))
-            hi = min(hi, self.nxt + self.max_jobs)
             room = cfg.footprint_bytes - self.flight_bytes
             fit = int(np.searchsorted(np.cumsum(self.foot[self.nxt:hi]), room, side="right"))
             if fit == 0:
@@ -151,23 +221,40 @@ class TurnPlanner:
                     return "block", None, 0.0
                 else:
                     fit = 1  # a burst larger than the budget goes alone
-            sel = slice(self.nxt, self.nxt + fit)
+            stop = self.nxt
+            for b in range(self.nxt, self.nxt + fit):
+                t = int(st.table[b])
+                if st.insert[b]:
+                    if t in self.held_tables:
+                        flush = True  # a held lookup of t must not see this insert: flush first
+                        break
+                    self.pending.append(b)
+                    self.pending_keys += int(st.size[b])
+                    self.pending_tables[t] = self.pending_tables.get(t, 0) + 1
+                else:
+                    if len(lookups) + len(self.held) >= self.max_jobs:
+                        flush = bool(self.pending)  # the job array is full
+                        break
+                    if t in self.pending_tables:
+                        self.held.append(b)
+                        self.held_tables.add(t)
+                    else:
+                        lookups.append(b)
+                stop = b + 1
+            sel = slice(self.nxt, stop)
             self.flight_bytes += int(self.foot[sel].sum())
-        idx = np.arange(sel.start, sel.stop)
-        lookups = idx[~st.insert[sel]]
-        for b in idx[st.insert[sel]]:
-            self.pending.append(int(b))
-            self.pending_keys += int(st.size[b])
-        self.nxt = sel.stop
+            self.nxt = stop
         flush = bool(self.pending) and (flush or self._flush_due(now))
-        if not lookups.shape[0] and not flush:
+        if not lookups and not flush:
             return "none", None, 0.0
-        turn = Turn(admitted=sel, lookups=lookups)
+        turn = Turn(admitted=sel, lookups=np.asarray(lookups, np.int64))
         if flush:
             turn.inserts = self.pending
             turn.insert_first = int(st.offset[self.pending[0]])
             turn.insert_keys = self.pending_keys
-            self.pending, self.pending_keys = [], 0
+            turn.lookups_after = np.asarray(self.held, np.int64)
+            self.pending, self.pending_keys, self.pending_tables = [], 0, {}
+            self.held, self.held_tables = [], set()
         turn.nbytes = int(self.foot[turn.done].sum())
         return "launch", turn, 0.0
 

@@ -1,5 +1,7 @@
 """Served form: continuous batching gives every burst the result it gets
-alone (needs a GB300)."""
+alone (needs a GB300). A fifth of the lookup keys name flows that earlier
+insert bursts of the same table add during the run, so a lookup launched
+before an earlier insert of its table, or after a later one, would show."""
 
 import pytest
 import torch
@@ -18,6 +20,8 @@ def test_served_results_equal_alone_results():
     rm = mixed.run("batched")
     ra = alone.run("plain")
     assert rm["bursts"] == ra["bursts"] > 50
+    assert rm["read_after_write_keys"] > 1000
+    assert rm["held_lookup_bursts"] > 0, "no lookup waited for an insert: the ordering rule went unexercised"
     assert mixed.check() == {"lookups_match_map": True, "inserts_all_inserted": True}
     assert alone.check() == {"lookups_match_map": True, "inserts_all_inserted": True}
     for pm, pa in zip(mixed.pools, alone.pools):
@@ -33,4 +37,8 @@ def test_served_results_equal_alone_results():
             continue
         v, f = mixed.tables[t].lookup(mixed.ins_keys[sel])
         assert bool(f.all()) and torch.equal(v, mixed.ins_vals[sel])
+    # the read-after-write keys are hits, in both arms
+    for t, p in enumerate(mixed.pools):
+        pos = torch.from_numpy(st.raw_pos[st.raw_table == t]).cuda()
+        assert bool(p["found"][pos].all()) and bool(alone.pools[t]["found"][pos].all())
     assert rm["latency_us"]["p50"] > 0
