@@ -103,7 +103,7 @@ typedef struct ckpp_stats {
 /* Bytes of device memory a table of this geometry needs (0 if the geometry is
  * invalid): a 256-byte header, then n_buckets buckets of 256 bytes. A bucket
  * is two 128-byte lines. Line 0 holds the fields a lookup reads first (8
- * 16-bit tags, the 64-bit filter, the busy / in_secondary / lock word and the
+ * 16-bit tags, the 64-bit filter, the busy / in_secondary / claimed / lock word and the
  * moved counter; Sec. 4.1, 4.3) with the keys and values of slots 0..3, or,
  * with CKPP_TIMERS, of slots 0..2 and the 8 16-bit expiries (Sec. 4.2). Line 1
  * holds the keys and values of the other slots. The keys and values of a
@@ -268,7 +268,7 @@ int ckpp_bulk_delete(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32
 /* Bulk insert for callers that cannot allocate device memory. No counterpart
  * in the paper: it is ckpp_bulk_insert with the same semantics, arguments and
  * status codes, minus the workspace. Its scratch is a fixed device array built
- * into libckpp.so (about 2 MB, enough for CKPP_NOALLOC_MAX_KEYS keys), which
+ * into libckpp.so (about 3 MB, enough for CKPP_NOALLOC_MAX_KEYS keys), which
  * every GPU that loads the library holds until the process exits. It suits
  * callers that own no allocator when they insert: a data-plane thread that must
  * never call cudaMalloc/cudaFree (cudaFree can stall the whole device), or a
@@ -287,6 +287,45 @@ int ckpp_bulk_delete(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32
  * Errors: CKPP_EINVAL, CKPP_ESTALE, CKPP_ECUDA. */
 int ckpp_bulk_insert_noalloc(ckpp_table* table, const ckpp_key* keys, const uint64_t* vals, uint64_t n,
                              uint32_t now, uint16_t ttl, uint8_t* status, ckpp_stream_t stream);
+
+/* ---- Hash sharding: one table split over several GPUs ---------------------
+ * Each rank owns the keys of its shard in a table of its own (the paper's
+ * private per-core tables, Sec. 2 and Sec. 5.3, with the keys partitioned by
+ * hash instead of by core). A bulk call over the whole table partitions its
+ * batch by owner (ckpp_shard_partition), sends each part to its owner (an
+ * all-to-all, outside this library), runs the owner's ordinary bulk call,
+ * sends the results back (a second all-to-all) and writes them in the
+ * caller's order (ckpp_shard_unpermute). The shard of a key is
+ *   ((H1 >> 16) & 0xFFFF) * n_shards >> 16,
+ * bits 16-31 of the primary hash, which neither the tag (bits 0-15) nor the
+ * primary bucket (bits 32-63) uses, so each shard's table sees uniform buckets
+ * and tags. H1 is the table's primary hash with the given seed. */
+#define CKPP_MAX_SHARDS 64
+
+/* Device workspace bytes of ckpp_shard_partition (0 if n or n_shards is out
+ * of range). */
+size_t ckpp_shard_workspace_bytes(uint64_t n, uint32_t n_shards);
+
+/* Stable partition of a batch by shard (n_shards in [1, CKPP_MAX_SHARDS]).
+ *   keys      [n] ckpp_key, 16-byte aligned;  vals [n] uint64 or NULL
+ *   out_order [n] uint32: original index of the key at each sorted position
+ *   out_keys  [n] ckpp_key (16-byte aligned), out_vals [n] uint64 (NULL iff
+ *             vals is NULL): keys and values in sorted order, i.e. shard 0's
+ *             keys first, each shard's keys in batch order
+ *   out_counts [n_shards] uint64: keys per shard
+ *   workspace: ckpp_shard_workspace_bytes(n, n_shards) device bytes.
+ * All device pointers, caller-owned; asynchronous on `stream`.
+ * Errors: CKPP_EINVAL, CKPP_ECUDA. */
+int ckpp_shard_partition(const ckpp_key* keys, const uint64_t* vals, uint64_t n, uint64_t seed, uint32_t n_shards,
+                         uint32_t* out_order, ckpp_key* out_keys, uint64_t* out_vals, uint64_t* out_counts,
+                         void* workspace, size_t workspace_bytes, ckpp_stream_t stream);
+
+/* Write results that arrive in sorted order back to the caller's order:
+ * out[order[j]] = in[j] for j < n, for a uint64 array (in_u64/out_u64, both
+ * or neither) and a uint8 array (in_u8/out_u8, both or neither). Device
+ * pointers, caller-owned. Errors: CKPP_EINVAL, CKPP_ECUDA. */
+int ckpp_shard_unpermute(const uint32_t* order, uint64_t n, const uint64_t* in_u64, const uint8_t* in_u8,
+                         uint64_t* out_u64, uint8_t* out_u8, ckpp_stream_t stream);
 
 /* Expiration scan (Sec. 4.2): delete every dead entry of every bucket, with
  * moved-counter upkeep, and record `now` as the last scan time. If

@@ -85,6 +85,9 @@ def _load():
         "ckpp_sync_status": (C.c_int, [vp, vp]),
         "ckpp_get_geometry": (C.c_int, [vp, gp]),
         "ckpp_get_last_scan": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int)]),
+        "ckpp_shard_workspace_bytes": (sz, [u64, u32]),
+        "ckpp_shard_partition": (C.c_int, [vp, vp, u64, u64, u32, vp, vp, vp, vp, vp, sz, vp]),
+        "ckpp_shard_unpermute": (C.c_int, [vp, u64, vp, vp, vp, vp, vp]),
         "ckpp_error_string": (C.c_char_p, [C.c_int]),
         "ckpp_abi_version": (C.c_int, []),
     }
@@ -101,8 +104,9 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_sync_status", "ckpp_get_geometry", "ckpp_get_last_scan", "ckpp_error_string",
             "ckpp_abi_version", "ckpp_bulk_insert_noalloc", "ckpp_bulk_lookup_variant", "ckpp_batch_bytes",
             "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup", "ckpp_batch_insert",
-            "ckpp_batch_delete")
+            "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute")
 NOALLOC_MAX_KEYS = 65536
+MAX_SHARDS = 64
 
 
 def library():
@@ -318,3 +322,35 @@ def ckpp_get_last_scan(handle: int) -> tuple[int, bool]:
 
 def ckpp_abi_version() -> int:
     return int(_lib.ckpp_abi_version())
+
+
+def ckpp_shard_workspace_bytes(n: int, n_shards: int) -> int:
+    return int(_lib.ckpp_shard_workspace_bytes(n, n_shards))
+
+
+def ckpp_shard_partition(keys: torch.Tensor, vals: torch.Tensor | None, seed: int, n_shards: int,
+                         out_order: torch.Tensor, out_keys: torch.Tensor, out_vals: torch.Tensor | None,
+                         out_counts: torch.Tensor, workspace: torch.Tensor, stream=None):
+    n = keys.shape[0]
+    _dev(keys, "keys", torch.uint8)
+    _dev(out_order, "out_order", (torch.int32, torch.uint32))
+    _dev(out_keys, "out_keys", torch.uint8)
+    _dev(out_counts, "out_counts", (torch.int64, torch.uint64))
+    _dev(workspace, "workspace", torch.uint8)
+    for t, name in ((vals, "vals"), (out_vals, "out_vals")):
+        if t is not None:
+            _dev(t, name, (torch.int64, torch.uint64))
+    _check(_lib.ckpp_shard_partition(_ptr(keys), _ptr(vals), n, seed & (2**64 - 1), n_shards, _ptr(out_order),
+                                     _ptr(out_keys), _ptr(out_vals), _ptr(out_counts), _ptr(workspace),
+                                     workspace.numel(), _stream(stream)), "ckpp_shard_partition")
+
+
+def ckpp_shard_unpermute(order: torch.Tensor, in_u64: torch.Tensor | None, in_u8: torch.Tensor | None,
+                         out_u64: torch.Tensor | None, out_u8: torch.Tensor | None, stream=None):
+    n = order.shape[0]
+    _dev(order, "order", (torch.int32, torch.uint32))
+    for t, name in ((in_u64, "in_u64"), (out_u64, "out_u64"), (in_u8, "in_u8"), (out_u8, "out_u8")):
+        if t is not None:
+            _dev(t, name)
+    _check(_lib.ckpp_shard_unpermute(_ptr(order), n, _ptr(in_u64), _ptr(in_u8), _ptr(out_u64), _ptr(out_u8),
+                                     _stream(stream)), "ckpp_shard_unpermute")

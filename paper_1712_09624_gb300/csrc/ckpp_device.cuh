@@ -16,7 +16,8 @@
 // Line 0, bytes [0, 128):
 //   0..15    tag[8]     16-bit tags derived from the primary hash (Sec. 4.3)
 //   16..23   bloom      64-bit filter of this bucket's displaced keys (Sec. 4.1)
-//   24..27   ctrl       bits 0-7 busy, bits 8-15 in_secondary, bit 31 insert lock
+//   24..27   ctrl       bits 0-7 busy, bits 8-15 in_secondary, bits 16-23 claimed
+//                       (set only inside an insert call), bit 31 insert lock
 //   28..31   moved      moved counter (Sec. 4.1)
 //   tables without timers:          tables with timers (Sec. 4.2):
 //   32..95   key[0..3]              32..47   expiry[8] (u16 each)
@@ -48,6 +49,7 @@ constexpr uint32_t kAliveWindow = 1024;   // Sec. 4.2
 constexpr uint32_t kMaxStale = 64512;     // Sec. 4.2: 65536 - 1024
 constexpr uint32_t kBusyMask = 0xFFu;
 constexpr uint32_t kInsecShift = 8;
+constexpr uint32_t kClaimShift = 16;  // a slot claimed by an insert, not yet published
 constexpr uint32_t kLockBit = 0x80000000u;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint64_t kMaxBatch = 1ull << 30;

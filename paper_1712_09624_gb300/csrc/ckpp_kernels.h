@@ -43,6 +43,8 @@ struct Workspace {
   uint32_t* slot_of;    // [n] set position of each batch key
   uint32_t* pending;    // [n] leaders left for the displacement pass
   uint32_t* retry;      // [n] leaders a displacement pass passes on to the next
+  unsigned long long* claim;  // [n] per key: (bucket << 32) | the ctrl bits its publication flips, or 0
+                              // (the slot phase 1 claimed for it; written by phase 1 for every key)
   unsigned long long* fixup;  // [fix_cap] (table << 32 | bucket) whose moved counter fell to 0 off-lock
   uint32_t m_mask;      // m - 1 (m a power of two >= 2n)
   uint32_t fix_cap;

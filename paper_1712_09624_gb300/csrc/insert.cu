@@ -6,10 +6,13 @@
 //             workspace: each key learns the lowest (leader) and highest batch
 //             index of its group, which gives the batch the result of inserting
 //             the keys one by one in index order.
-//   phase1  - per leader: lock its two buckets, update in place if the key is
-//             stored (alive or dead), else take the lowest free or dead slot of
-//             the primary, else of the secondary; leaders with two full buckets
-//             are queued for phase 2.
+//   phase1  - per leader, lock-free: update in place if the key is stored
+//             (alive; a dead entry is revived), else claim the lowest free
+//             or dead slot of the primary, else of the secondary, with a CAS
+//             on the bucket's ctrl word, and write the entry into the
+//             claimed slot; leaders with two full buckets are queued for the
+//             displacement passes.
+//   publish - per key: the slot phase 1 claimed becomes busy (one atomic).
 //   move1   - per queued leader: the cuckoo paths of length one. Read the
 //             entries of b1, then of b2, and the buckets they can move to; the
 //             first entry whose other bucket has a free or dead slot moves
@@ -89,49 +92,143 @@ __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint3
 }
 
 // --------------------------------------------------------------- phase 1
-// Per leader. Lock the primary bucket first. With its lock held, its filter is
-// exact about this key (Sec. 4.1: a key stored in its secondary has both bits
-// set in its primary's filter, set under the primary's lock; phase 1 moves no
-// entry and the batch holds each key once). If the key is in the primary it is
-// updated there; if the filter rules out the secondary and the primary has a
-// free or dead slot, the key is placed there. Otherwise the secondary is
-// locked too -- directly when its index is higher (locks are taken in index
-// order), else by a single non-waiting attempt, and failing that both are
-// released and taken again in order -- and both buckets are searched.
+// Per leader, without locks. A key that is stored (alive or dead, Sec. 4.2) is
+// found in its primary bucket, or in its secondary when the primary's filter
+// says it may be there (Sec. 4.1: a key stored in its secondary has both bits
+// set in its primary's filter; phase 1 moves no entry and the batch holds each
+// key once, so the tests are exact). A live entry is updated in place. Any
+// other key claims the lowest claimable slot of its primary, else of its
+// secondary (Sec. 2), else waits for the displacement passes.
+//
+// A claim is a CAS on the bucket's ctrl word that sets the slot's claimed bit
+// (and clears its busy and in_secondary bits: a dead entry held there is
+// evicted, with moved-counter upkeep on its own primary). A slot is claimable
+// if it is neither busy nor claimed, or busy with a dead entry and not
+// claimed. The owner then writes the entry; the slot stays invisible to every
+// reader, whose searches look at busy slots only, until insert_publish (the
+// next kernel) flips its claimed bit to busy. A failed CAS returns the current
+// word, and the claimable slots are recomputed from it. Reviving a key's own
+// dead entry claims its slot in the same way (busy stays set), so a revival
+// and a reuse of that dead slot by another key cannot both succeed. Storing a
+// key in its secondary sets its two bits in the primary's filter and counts
+// it in the primary's moved counter, with relaxed atomics: no filter is reset
+// during phase 1 (resets of counters that reach zero here are deferred to the
+// fixup pass). Nothing in phase 1 waits on another thread, and nothing needs
+// a fence: the kernel boundary orders every write before the publication.
+constexpr int kClaimAttempts = 64;  // CAS retries on one bucket (at most 16 claims can change its word)
 
-// Both buckets locked (c1/s1, c2/s2 their ctrl words and snapshots): update
-// the key where it is stored, else place it in the lowest free or dead slot of
-// the primary, else of the secondary, else queue it for the displacement
-// passes. Returns the status, or 0 if queued.
-__device__ uint8_t phase1_both(const TableView& t, uint32_t tid, const Key& k, uint64_t v, const Addr& a,
-                               uint32_t now, uint32_t expiry, const Workspace& ws, uint64_t i, uint32_t& c1,
-                               const Snap& s1, uint32_t& c2, const Snap& s2) {
-  uint32_t b = a.b1;
-  const Snap* sb = &s1;
-  int slot = find_key(t, a.b1, c1, s1, k, a.tag);
-  if (slot < 0) {
-    b = a.b2;
-    sb = &s2;
-    slot = find_key(t, a.b2, c2, s2, k, a.tag);
+__device__ __forceinline__ uint32_t claim_bit(uint32_t s) { return 1u << (kClaimShift + s); }
+
+// Slots of a bucket (ctrl word c, snapshot s) that an insertion may claim.
+__device__ __forceinline__ uint32_t claimable(const TableView& t, uint32_t c, const Snap& s, uint32_t now) {
+  return free_mask(t, c, s, now) & ~(c >> kClaimShift) & kBusyMask;
+}
+
+// Claim the lowest claimable slot of bucket b. c: the word the snapshot s saw.
+// Returns the slot (prev receives the word the CAS replaced), -1 if nothing is
+// claimable, -2 after kClaimAttempts failed CASes.
+__device__ int claim_slot(const TableView& t, uint32_t b, uint32_t c, const Snap& s, uint32_t now, uint32_t& prev) {
+  uint32_t* cp = ctrl_ptr(t, b);
+  for (int i = 0; i < kClaimAttempts; ++i) {
+    const uint32_t f = claimable(t, c, s, now);
+    if (!f) return -1;
+    const uint32_t sl = __ffs(f) - 1;
+    const uint32_t want = (c | claim_bit(sl)) & ~((1u << sl) | (1u << (kInsecShift + sl)));
+    const uint32_t got = atomicCAS(cp, c, want);
+    if (got == c) {
+      prev = c;
+      return (int)sl;
+    }
+    c = got;
   }
-  if (slot >= 0) {
-    const bool was_alive = !t.timers || alive16(snap_expiry(*sb, slot), now);
+  return -2;
+}
+
+// Claim the slot of the key's own dead entry (slot sl of bucket b, busy in c).
+// Returns 1 on success, 0 if another key took the slot first (the entry is
+// gone), -2 after kClaimAttempts failed CASes.
+__device__ int claim_revival(const TableView& t, uint32_t b, uint32_t sl, uint32_t c) {
+  uint32_t* cp = ctrl_ptr(t, b);
+  for (int i = 0; i < kClaimAttempts; ++i) {
+    if (!((c >> sl) & 1u) || ((c >> (kClaimShift + sl)) & 1u)) return 0;
+    const uint32_t got = atomicCAS(cp, c, c | claim_bit(sl));
+    if (got == c) return 1;
+    c = got;
+  }
+  return -2;
+}
+
+// A dead entry evicted by a claim (prev: the word before it): if it sat in its
+// secondary bucket, its primary's moved counter drops (Sec. 4.1); a counter
+// that reaches zero is queued for the filter reset of the fixup pass.
+__device__ __forceinline__ void evict_claimed(const TableView& t, uint32_t tid, uint32_t b, uint32_t sl,
+                                             uint32_t prev, const Workspace& ws) {
+  if (((prev >> sl) & 1u) && ((prev >> (kInsecShift + sl)) & 1u)) {
+    Key k;
+    ld128_cg(key_ptr(t, b, sl), k.k0, k.k1);
+    const Addr e = address_of(k, t.nb, t.seed);
+    if (atomicSub(moved_ptr(t, e.b1), 1u) == 1u) push_fixup(ws, tid, e.b1);
+  }
+}
+
+struct P1Result {
+  uint8_t status;           // 0: queued for the displacement passes
+  unsigned long long rec;   // the claim to publish, or 0
+};
+
+// The key's stored entry in bucket b (snapshot s, word c), if any: a live one
+// is updated in place (UPDATED), a dead one revived through a claim
+// (INSERTED, Sec. 4.2). Returns false if the key is not there (or its dead
+// entry was just taken by another key).
+__device__ bool update_stored(const TableView& t, uint32_t b, uint32_t c, const Snap& s, const Key& k,
+                              const Addr& a, uint64_t v, uint32_t now, uint32_t expiry, P1Result& r) {
+  const int slot = find_key(t, b, c, s, k, a.tag);
+  if (slot < 0) return false;
+  if (!t.timers || alive16(snap_expiry(s, slot), now)) {
     st64_cg(value_ptr(t, b, slot), v);
     if (t.timers) set_expiry(t, b, slot, expiry);
-    return was_alive ? kStUpdated : kStInserted;
+    r.status = kStUpdated;
+    return true;
   }
-  const uint32_t f1 = free_mask(t, c1, s1, now);
-  const uint32_t f2 = f1 ? 0u : free_mask(t, c2, s2, now);
-  if (f1 || f2) {
-    b = f1 ? a.b1 : a.b2;
-    uint32_t& cb = f1 ? c1 : c2;
-    slot = __ffs(f1 ? f1 : f2) - 1;
-    if ((cb >> slot) & 1u) evict_entry(t, tid, b, slot, cb, ws);
-    place_entry(t, b, slot, k, v, a, expiry, cb);
-    return kStInserted;
+  const int got = claim_revival(t, b, (uint32_t)slot, c);
+  if (got == 0) return false;
+  if (got < 0) {
+    r.status = kStBusy;
+    return true;
   }
-  ws.pending[atomicAdd(ws.counters + 0, 1u)] = (uint32_t)i;
-  return 0;
+  st64_cg(value_ptr(t, b, slot), v);
+  set_expiry(t, b, slot, expiry);
+  r.status = kStInserted;
+  r.rec = ((unsigned long long)b << 32) | claim_bit(slot);
+  return true;
+}
+
+// Claim a slot of bucket b for the new key and write its entry there.
+// Returns false if b has nothing claimable.
+__device__ bool place_new(const TableView& t, uint32_t tid, uint32_t b, uint32_t c, const Snap& s, const Key& k,
+                          const Addr& a, uint64_t v, uint32_t now, uint32_t expiry, const Workspace& ws,
+                          P1Result& r) {
+  uint32_t prev = 0;
+  const int sl = claim_slot(t, b, c, s, now, prev);
+  if (sl == -1) return false;
+  if (sl < 0) {
+    r.status = kStBusy;
+    return true;
+  }
+  evict_claimed(t, tid, b, (uint32_t)sl, prev, ws);
+  st128_cg(key_ptr(t, b, sl), k.k0, k.k1);
+  st64_cg(value_ptr(t, b, sl), v);
+  st16_cg(tag_ptr(t, b, sl), a.tag);
+  if (t.timers) st16_cg(expiry_ptr(t, b, sl), expiry);
+  uint32_t flip = claim_bit(sl) | (1u << sl);
+  if (b == a.b2) {  // Sec. 4.1: displaced to the secondary
+    flip |= 1u << (kInsecShift + sl);
+    atomicOr(reinterpret_cast<unsigned long long*>(bloom_ptr(t, a.b1)), (unsigned long long)a.bits);
+    atomicAdd(moved_ptr(t, a.b1), 1u);
+  }
+  r.status = kStInserted;
+  r.rec = ((unsigned long long)b << 32) | flip;
+  return true;
 }
 
 __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
@@ -142,13 +239,13 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
   pdl_release();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  // The leader test's set words and the primary's lock are independent round
-  // trips: the words are requested before the lock and tested after it, so
-  // the two overlap. A key that is not its group's leader releases the lock
-  // untouched.
+  P1Result r{0, 0ull};
+  // The leader test's set words and the primary's snapshot are independent
+  // round trips; both are requested before either is used.
   const uint32_t pos = ws.slot_of[i];
   const uint32_t first = *ws.first_at(pos), last = *ws.last_at(pos);
   if (!ts.valid(i)) {
+    ws.claim[i] = 0ull;
     if (first == (uint32_t)i) status[i] = kStNoTable;
     return;
   }
@@ -156,62 +253,52 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
   const uint32_t tid = ts.id(i);
   const Key k = load_key(keys, i);
   const Addr a = address_of(k, t.nb, t.seed);
-  uint32_t c1, c2;
-  const bool locked = lock_bucket(t, a.b1, c1);
-  if (first != (uint32_t)i) {
-    if (locked) unlock_bucket(t, a.b1, c1);
-    return;
-  }
-  if (!locked) {
-    status[i] = kStBusy;
-    latch_error(t, kErrLockTimeout);
-    return;
-  }
   Snap s1, s2;
   snap_bucket(t, a.b1, s1);
+  if (first != (uint32_t)i) {
+    ws.claim[i] = 0ull;
+    return;
+  }
   const uint64_t v = vals[last];
-  const int slot = find_key(t, a.b1, c1, s1, k, a.tag);
-  if (slot >= 0) {
-    const bool was_alive = !t.timers || alive16(snap_expiry(s1, slot), now);
-    st64_cg(value_ptr(t, a.b1, slot), v);
-    if (t.timers) set_expiry(t, a.b1, slot, expiry);
-    unlock_bucket(t, a.b1, c1);
-    status[i] = was_alive ? kStUpdated : kStInserted;
+  const uint32_t c1 = (uint32_t)s1.w[3];
+  bool done = update_stored(t, a.b1, c1, s1, k, a, v, now, expiry, r);
+  bool have2 = false;
+  uint32_t c2 = 0;
+  if (!done && (s1.w[2] & a.bits) == a.bits) {  // the filter allows the secondary
+    snap_bucket(t, a.b2, s2);
+    have2 = true;
+    c2 = (uint32_t)s2.w[3];
+    done = update_stored(t, a.b2, c2, s2, k, a, v, now, expiry, r);
+  }
+  if (!done) done = place_new(t, tid, a.b1, c1, s1, k, a, v, now, expiry, ws, r);
+  if (!done) {
+    if (!have2) {
+      snap_bucket(t, a.b2, s2);
+      c2 = (uint32_t)s2.w[3];
+    }
+    done = place_new(t, tid, a.b2, c2, s2, k, a, v, now, expiry, ws, r);
+  }
+  ws.claim[i] = r.rec;
+  if (!done) {
+    ws.pending[atomicAdd(ws.counters + 0, 1u)] = (uint32_t)i;
     return;
   }
-  if ((s1.w[2] & a.bits) != a.bits) {  // the filter rules the secondary out
-    const uint32_t f1 = free_mask(t, c1, s1, now);
-    if (f1) {
-      const uint32_t sl = __ffs(f1) - 1;
-      if ((c1 >> sl) & 1u) evict_entry(t, tid, a.b1, sl, c1, ws);
-      place_entry(t, a.b1, sl, k, v, a, expiry, c1);
-      unlock_bucket(t, a.b1, c1);
-      status[i] = kStInserted;
-      return;
-    }
-  }
-  // The secondary is needed as well.
-  bool held;
-  if (a.b2 > a.b1) {
-    held = lock_bucket(t, a.b2, c2);
-    if (!held) unlock_bucket(t, a.b1, c1);
-  } else {
-    held = try_lock_bucket(t, a.b2, c2);
-    if (!held) {
-      unlock_bucket(t, a.b1, c1);
-      held = lock_pair(t, a.b1, a.b2, c1, c2);
-      if (held) snap_bucket(t, a.b1, s1);
-    }
-  }
-  if (!held) {
-    status[i] = kStBusy;
-    latch_error(t, kErrLockTimeout);
-    return;
-  }
-  snap_bucket(t, a.b2, s2);
-  const uint8_t st = phase1_both(t, tid, k, v, a, now, expiry, ws, i, c1, s1, c2, s2);
-  unlock_pair(t, a.b1, a.b2, c1, c2);
-  if (st) status[i] = st;
+  if (r.status == kStBusy) latch_error(t, kErrLockTimeout);
+  status[i] = r.status;
+}
+
+// Publication of phase 1's claims: each claimed slot's claimed bit is cleared
+// and its busy (and in_secondary) bits set, in one atomic XOR per key. From
+// here on the new entries are visible to every search.
+__global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t n, Workspace ws) {
+  pdl_wait();
+  pdl_release();
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long r = ws.claim[i];
+  if (!r) return;
+  const TableView t = ts.of(i);
+  atomicXor(ctrl_ptr(t, (uint32_t)(r >> 32)), (uint32_t)r);
 }
 
 // --------------------------------------------------------------- phase 2
@@ -713,6 +800,8 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
   cudaError_t e = launch_dedup(ts, keys, n, ws, s);
   if (e != cudaSuccess) return e;
   e = launch_chained(insert_phase1, grid_for(n, kThreads), kThreads, s, ts, keys, vals, n, now, expiry, status, ws);
+  if (e != cudaSuccess) return e;
+  e = launch_chained(insert_publish, grid_for(n, kThreads), kThreads, s, ts, n, ws);
   if (e != cudaSuccess) return e;
   // lists: phase 1 -> pending [0] -> move1 -> retry [3] -> grid search ->
   // pending [5] -> block search -> retry [6] -> last search

@@ -3,16 +3,24 @@
 // counter and Bloom filter upkeep of Sec. 4.1.
 //
 // Concurrency rules of the insert kernels (one table, one batch at a time):
-//  * a bucket's busy / in_secondary bits, tags, expiries, keys and values change only
-//    while its lock bit (ctrl bit 31) is held; the new ctrl word is published
-//    by the unlocking exchange;
-//  * Bloom bits of bucket p are set only while p's lock is held, so a filter
-//    reset done under p's lock cannot erase a concurrent insertion's bits;
+//  * phase 1 takes no lock: a key claims a free or dead slot with a CAS on the
+//    bucket's ctrl word (claimed bits 16-23), writes its entry into the
+//    claimed slot, and the next kernel publishes the claim (claimed -> busy);
+//    searches look at busy slots only, so a claimed slot is invisible until
+//    then. In-place updates touch live entries, which no claim can take;
+//  * in the displacement passes (after publication) a bucket's busy /
+//    in_secondary bits, tags, expiries, keys and values change only while its
+//    lock bit (ctrl bit 31) is held; the new ctrl word is published by the
+//    unlocking exchange;
+//  * Bloom bits of bucket p are set in phase 1 (no reset runs there) or under
+//    p's lock, and a filter is reset only under p's lock or after the batch,
+//    so a reset cannot erase a concurrent insertion's bits;
 //  * a moved counter may be decremented without its bucket's lock (when a dead
 //    entry is overwritten elsewhere); a decrement that reaches zero off-lock
 //    queues the bucket for a reset pass that runs after the batch.
-// Every wait is bounded: a lock not taken after kLockSpins tries returns false
-// and the caller reports CKPP_ST_BUSY and latches kErrLockTimeout.
+// Every wait is bounded: a lock not taken after kLockSpins tries (or a claim
+// whose CAS keeps failing) gives up; the caller reports CKPP_ST_BUSY and
+// latches kErrLockTimeout.
 #pragma once
 
 #include "ckpp_kernels.h"
@@ -56,41 +64,8 @@ __device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint
   return false;
 }
 
-// One attempt, no wait: safe to call while holding locks in any order.
-__device__ __forceinline__ bool try_lock_bucket(const TableView& t, uint32_t b, uint32_t& ctrl) {
-  const uint32_t old = or_acquire(ctrl_ptr(t, b), kLockBit);
-  if (old & kLockBit) return false;
-  ctrl = old;
-  return true;
-}
-
 __device__ __forceinline__ void unlock_bucket(const TableView& t, uint32_t b, uint32_t ctrl) {
   exch_release(ctrl_ptr(t, b), ctrl & ~kLockBit);
-}
-
-// Lock two distinct buckets in index order (no lock cycles). cx/cy receive the
-// ctrl words of x and y.
-__device__ __forceinline__ bool lock_pair(const TableView& t, uint32_t x, uint32_t y, uint32_t& cx, uint32_t& cy) {
-  const uint32_t lo = x < y ? x : y, hi = x < y ? y : x;
-  uint32_t clo, chi;
-  if (!lock_bucket(t, lo, clo)) return false;
-  if (!lock_bucket(t, hi, chi)) {
-    unlock_bucket(t, lo, clo);
-    return false;
-  }
-  cx = (x == lo) ? clo : chi;
-  cy = (x == lo) ? chi : clo;
-  return true;
-}
-
-__device__ __forceinline__ void unlock_pair(const TableView& t, uint32_t x, uint32_t y, uint32_t cx, uint32_t cy) {
-  if (x < y) {
-    unlock_bucket(t, y, cy);
-    unlock_bucket(t, x, cx);
-  } else {
-    unlock_bucket(t, x, cx);
-    unlock_bucket(t, y, cy);
-  }
 }
 
 // Coherent snapshot of a bucket: its first sector and (with timers) the 8 expiries.

@@ -98,7 +98,7 @@ class Decoded:
         if self.magic != 0x50504B43:
             bad.append("bad magic")
         if (self.ctrl & 0x7FFF0000).any() or (self.ctrl & 0x80000000).any():
-            bad.append("lock bit or unused ctrl bits set")
+            bad.append("lock bit, claimed bits or unused ctrl bits set")
         if (self.insec & ~self.busy).any():
             bad.append("in_secondary set on an empty slot")
         occ = self.occupied()
