@@ -175,8 +175,10 @@ def profiled_traffic():
     return float(d["traffic_bytes_per_launch"])
 
 
+# ncu's unit spellings -> bytes, or microseconds for times
 _UNIT_SCALE = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
-               "nsecond": 1e-3, "usecond": 1.0, "msecond": 1e3, "second": 1e6}
+               "nsecond": 1e-3, "usecond": 1.0, "msecond": 1e3, "second": 1e6,
+               "ns": 1e-3, "us": 1.0, "ms": 1e3, "s": 1e6}
 
 
 def record_traffic(csv_path: str):

@@ -93,7 +93,7 @@ def test_traffic_record_and_read(tmp_path):
     name = "void ckpp::<unnamed>::lookup_kernel<0, 0, 0, 0>(ckpp::TableView)"
     head = '"ID","Process ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
     rows = [("0", "dram__bytes_read.sum", "Gbyte", "2.5"), ("0", "dram__bytes_write.sum", "Mbyte", "1,500.5"),
-            ("0", "gpu__time_duration.sum", "usecond", "400.0"), ("1", "dram__bytes_read.sum", "Gbyte", "9.0")]
+            ("0", "gpu__time_duration.sum", "ns", "400000"), ("1", "dram__bytes_read.sum", "Gbyte", "9.0")]
     csv_path = tmp_path / "t.csv"
     csv_path.write_text("==PROF== noise\n" + head + "".join(f'"{i}","1","{name}","{m}","{u}","{v}"\n'
                                                            for i, m, u, v in rows))
