@@ -814,7 +814,7 @@ def run_batched(args):
                    "table_bytes": int(sum(t.buf.numel() for t in tables)), "build_s": round(build_s, 1)},
         "tuning": {"threads_per_key": best[0], "group_depth": best[1], "blocks_per_sm": best[2],
                    "keys_per_warp": best[3],
-                   "candidates_ms": {f"G{gd}_K{kp}_B{b}": round(v * 1e3, 4) for (t, gd, b, kp), v in tune.items()}},
+                   "candidates_ms": {f"T{t}_G{gd}_B{b}": round(v * 1e3, 4) for (t, gd, b, kp), v in tune.items()}},
         "plain_per_table_eager": {"value": round(total / t_eager / 1e9, 4), "ms_per_step": round(t_eager * 1e3, 3)},
         "plain_per_table_graph": ({"value": round(total / t_graph / 1e9, 4), "ms_per_step": round(t_graph * 1e3, 3)}
                                   if t_graph else {"error": graph_error}),

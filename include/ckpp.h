@@ -180,13 +180,14 @@ typedef struct ckpp_lookup_job {
   uint32_t table;       /* index into the batch's table list; jobs naming no table are skipped */
 } ckpp_lookup_job;
 
-/* Kernel configuration. threads_per_key: 4 (the only value): a key's 128-byte
- * bucket line is fetched by 8 lanes of 16 bytes, four lines per warp
- * instruction, one line request each. group_depth: 1 or 2 keys owned per
- * lane, i.e. up to 32 or 64 line requests a warp has in flight. blocks_per_sm:
- * 1..4 persistent blocks of 512 threads per SM. keys_per_warp: 8, 16 or 32
- * lanes of a warp that own keys per iteration (0 means 32). A NULL tuning is
- * {4, 1, 2, 32}. */
+/* Kernel configuration. threads_per_key: 1, 2 or 4 lanes of a warp per key
+ * in one iteration, so 32 / threads_per_key lanes own keys and every lane
+ * helps fetch their bucket lines (each 128-byte line is copied by 8 lanes of
+ * 16 bytes, four lines per warp instruction, one line request each).
+ * keys_per_warp: 0 (derived) or 32 / threads_per_key. group_depth: 1 or 2
+ * keys owned per owning lane, i.e. up to 32 / threads_per_key x group_depth
+ * line requests a warp has in flight. blocks_per_sm: 1..4 persistent blocks
+ * of 512 threads per SM. A NULL tuning is {1, 1, 2, 32}. */
 typedef struct ckpp_batch_tuning {
   uint32_t threads_per_key;
   uint32_t group_depth;
@@ -251,6 +252,26 @@ int ckpp_batch_lookup(ckpp_batch* batch, const ckpp_lookup_job* d_jobs, uint32_t
 int ckpp_bulk_insert(ckpp_table* table, const ckpp_key* keys, const uint64_t* vals, uint64_t n,
                      uint32_t now, uint16_t ttl, uint8_t* status, void* workspace, size_t workspace_bytes,
                      ckpp_stream_t stream);
+
+/* How insert calls (ckpp_bulk_insert, ckpp_batch_insert, the no-alloc insert)
+ * launch their work; no counterpart in the paper, the results are the same
+ * either way. An insert call is a chain of dependent kernels (duplicate
+ * resolution, the slot claims, their publication, the one-move pass, three
+ * cuckoo-path searches, the filter fixup); a small batch spends most of that
+ * chain's time starting and draining its kernels, so a batch of at most
+ * 131072 keys runs instead as one cooperative launch whose stages are
+ * separated by grid-wide barriers (two launches in all, with the workspace
+ * clear). Modes:
+ *   CKPP_INSERT_LAUNCH_AUTO    by batch size (the default);
+ *   CKPP_INSERT_LAUNCH_CHAIN   always the chain;
+ *   CKPP_INSERT_LAUNCH_SINGLE  always one launch (a device without
+ *                              cooperative launch uses the chain).
+ * The mode is process-wide; set it while no insert call is being issued.
+ * Returns the previous mode, or CKPP_EINVAL for an unknown one. */
+#define CKPP_INSERT_LAUNCH_AUTO 0
+#define CKPP_INSERT_LAUNCH_CHAIN 1
+#define CKPP_INSERT_LAUNCH_SINGLE 2
+int ckpp_set_insert_launch(int mode);
 
 /* Batched delete (Sec. 4.1: deleting a key stored in its secondary bucket
  * decrements the primary's moved counter and resets the filter at zero). The

@@ -88,6 +88,7 @@ def _load():
         "ckpp_shard_workspace_bytes": (sz, [u64, u32]),
         "ckpp_shard_partition": (C.c_int, [vp, vp, u64, u64, u32, vp, vp, vp, vp, vp, sz, vp]),
         "ckpp_shard_unpermute": (C.c_int, [vp, u64, vp, vp, vp, vp, vp]),
+        "ckpp_set_insert_launch": (C.c_int, [C.c_int]),
         "ckpp_error_string": (C.c_char_p, [C.c_int]),
         "ckpp_abi_version": (C.c_int, []),
     }
@@ -104,7 +105,9 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_sync_status", "ckpp_get_geometry", "ckpp_get_last_scan", "ckpp_error_string",
             "ckpp_abi_version", "ckpp_bulk_insert_noalloc", "ckpp_bulk_lookup_variant", "ckpp_batch_bytes",
             "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup", "ckpp_batch_insert",
-            "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute")
+            "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute",
+            "ckpp_set_insert_launch")
+INSERT_LAUNCH_AUTO, INSERT_LAUNCH_CHAIN, INSERT_LAUNCH_SINGLE = 0, 1, 2
 NOALLOC_MAX_KEYS = 65536
 MAX_SHARDS = 64
 
@@ -294,14 +297,15 @@ def ckpp_batch_delete(handle: int, keys: torch.Tensor, table_ids: torch.Tensor, 
 def ckpp_batch_lookup(handle: int, d_jobs: torch.Tensor, max_jobs: int, d_n_jobs: torch.Tensor | None = None,
                       now: int = 0, tuning: tuple | None = None, stream=None):
     """d_jobs: device uint8 tensor holding max_jobs ckpp_lookup_job records.
-    tuning: (threads_per_key, group_depth, blocks_per_sm[, keys_per_warp])."""
+    tuning: (threads_per_key, group_depth, blocks_per_sm[, keys_per_warp]); threads_per_key 1, 2 or 4,
+    keys_per_warp 0 or 32 / threads_per_key."""
     _dev(d_jobs, "d_jobs", torch.uint8)
     if d_jobs.numel() < max_jobs * JOB_BYTES:
         raise ValueError("d_jobs holds fewer than max_jobs jobs")
     if d_n_jobs is not None:
         _dev(d_n_jobs, "d_n_jobs", (torch.int32, torch.uint32))
     tn = None if tuning is None else C.byref(
-        ckpp_batch_tuning(tuning[0], tuning[1], tuning[2], tuning[3] if len(tuning) > 3 else 32))
+        ckpp_batch_tuning(tuning[0], tuning[1], tuning[2], tuning[3] if len(tuning) > 3 else 0))
     _check(_lib.ckpp_batch_lookup(handle, _ptr(d_jobs), max_jobs, _ptr(d_n_jobs), now, tn, _stream(stream)),
            "ckpp_batch_lookup")
 
@@ -354,3 +358,11 @@ def ckpp_shard_unpermute(order: torch.Tensor, in_u64: torch.Tensor | None, in_u8
             _dev(t, name)
     _check(_lib.ckpp_shard_unpermute(_ptr(order), n, _ptr(in_u64), _ptr(in_u8), _ptr(out_u64), _ptr(out_u8),
                                      _stream(stream)), "ckpp_shard_unpermute")
+
+
+def ckpp_set_insert_launch(mode: int) -> int:
+    """Process-wide launch mode of insert calls (INSERT_LAUNCH_*); returns the previous one."""
+    rc = _lib.ckpp_set_insert_launch(mode)
+    if rc < 0:
+        raise CkppError(rc, "ckpp_set_insert_launch")
+    return rc

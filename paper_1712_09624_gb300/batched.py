@@ -6,10 +6,11 @@ table's batch of keys and its output buffers), and launches the persistent
 kernel over all jobs (``ckpp_batch_lookup``), eagerly or as a captured CUDA
 graph that is replayed after the job array is rewritten.
 
-``autotune`` times every kernel configuration (group depth, keys per warp,
-persistent blocks per SM; threads per key is 4, the lanes that read one
-128-byte bucket line) on the current jobs with CUDA events and keeps the
-fastest; results are cached per (device, job-count, key-count) signature.
+``autotune`` times every kernel configuration (threads per key: 1, 2 or 4
+lanes of a warp per key, i.e. 32, 16 or 8 keys per warp iteration; group
+depth; persistent blocks per SM) on the current jobs with CUDA events and
+keeps the fastest; results are cached per (device, job-count, key-count)
+signature.
 """
 
 from __future__ import annotations
@@ -22,9 +23,8 @@ from . import _ckpp as K
 JOB_DTYPE = np.dtype([("keys", "<u8"), ("out_vals", "<u8"), ("out_found", "<u8"), ("n", "<u4"), ("table", "<u4")])
 assert JOB_DTYPE.itemsize == K.JOB_BYTES
 
-THREADS_PER_KEY = 4
+THREADS_PER_KEY = [1, 2, 4]   # lanes of a warp per key; keys per warp iteration = 32 / threads_per_key
 GROUP_DEPTHS = [1, 2]
-KEYS_PER_WARP = [8, 16, 32]
 BLOCKS_PER_SM = [1, 2, 3, 4]  # blocks of 512 threads
 
 _tune_cache: dict[tuple, tuple[int, int, int, int]] = {}
@@ -41,7 +41,7 @@ class BatchedLookup:
         self.handle = K.ckpp_batch_create([t.handle for t in self.tables], self.desc, stream)
         self.jobs = torch.zeros(self.max_jobs * K.JOB_BYTES, dtype=torch.uint8, device=self.device)
         self.n_jobs = torch.zeros(1, dtype=torch.int32, device=self.device)
-        self.tuning: tuple[int, int, int, int] = (THREADS_PER_KEY, 1, 2, 32)
+        self.tuning: tuple[int, int, int, int] = (1, 1, 2, 32)
         self.graph = None
         self._keep = []
 
@@ -115,15 +115,15 @@ def time_launch(batch: BatchedLookup, tuning, reps: int = 5, now: int = 0) -> fl
 
 def autotune(batch: BatchedLookup, total_keys: int, now: int = 0,
              reps: int = 5) -> tuple[tuple[int, int, int, int], dict]:
-    """Pick group depth, keys per warp and blocks per SM by timing every
+    """Pick threads per key, group depth and blocks per SM by timing every
     configuration on the batch's current jobs. Returns (best, {config: seconds})
     with configs (threads_per_key, group_depth, blocks_per_sm, keys_per_warp)."""
     sig = (batch.device.index, batch.n_active, int(np.log2(max(total_keys, 1))))
     results = {}
-    for g in GROUP_DEPTHS:
-        for kpw in KEYS_PER_WARP:
+    for tpk in THREADS_PER_KEY:
+        for g in GROUP_DEPTHS:
             for bps in BLOCKS_PER_SM:
-                cfg = (THREADS_PER_KEY, g, bps, kpw)
+                cfg = (tpk, g, bps, 32 // tpk)
                 results[cfg] = time_launch(batch, cfg, reps, now)
     best = min(results, key=results.get)
     _tune_cache[sig] = best

@@ -235,11 +235,12 @@ int ckpp_batch_delete(ckpp_batch* b, const ckpp_key* keys, const uint32_t* table
 int ckpp_batch_lookup(ckpp_batch* b, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,
                       uint32_t now, const ckpp_batch_tuning* tuning, ckpp_stream_t stream) {
   if (!b || max_jobs > kBatchMaxJobs || (max_jobs && !d_jobs)) return CKPP_EINVAL;
-  ckpp_batch_tuning tn = tuning ? *tuning : ckpp_batch_tuning{4, 1, 2, 32};
-  const uint32_t T = tn.threads_per_key, G = tn.group_depth, P = tn.keys_per_warp ? tn.keys_per_warp : 32;
-  if (T != 4 || !(G == 1 || G == 2) || !(P == 8 || P == 16 || P == 32) || tn.blocks_per_sm < 1 ||
-      tn.blocks_per_sm > 4)
+  ckpp_batch_tuning tn = tuning ? *tuning : ckpp_batch_tuning{1, 1, 2, 32};
+  const uint32_t T = tn.threads_per_key, G = tn.group_depth;
+  if (!(T == 1 || T == 2 || T == 4) || !(G == 1 || G == 2) || tn.blocks_per_sm < 1 || tn.blocks_per_sm > 4)
     return CKPP_EINVAL;
+  const uint32_t P = 32 / T;  // lanes that own keys in a warp iteration
+  if (tn.keys_per_warp != 0 && tn.keys_per_warp != P) return CKPP_EINVAL;
   for (ckpp_table* t : b->tables)
     if (int rc = time_check(t, now)) return rc;
   if (!max_jobs) return CKPP_OK;
@@ -247,6 +248,11 @@ int ckpp_batch_lookup(ckpp_batch* b, const ckpp_lookup_job* d_jobs, uint32_t max
                                        (int)T, (int)G, (int)P, b->any_timers, tn.blocks_per_sm * (uint32_t)b->sms,
                                        b->ctrl,
                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ckpp_set_insert_launch(int mode) {
+  const int prev = set_insert_launch(mode);
+  return prev < 0 ? CKPP_EINVAL : prev;
 }
 
 int ckpp_sync_status(ckpp_table* t, ckpp_stream_t stream) {

@@ -17,12 +17,15 @@
 // The last warp to finish resets the counter for the next launch, so
 // launches that use one batch descriptor must not overlap on the GPU.
 // Tuning (picked by the autotuner):
-//   threads per key  4: a key's 128-byte bucket line is fetched by 8 lanes of
-//                    16 bytes, four lines per warp instruction; fixed by the
-//                    line size (the value is part of the interface);
-//   group depth      1 or 2 keys owned per lane, i.e. up to 32 or 64 line
-//                    requests a warp has in flight;
-//   keys per warp    8, 16 or 32 lanes that own keys in a warp iteration;
+//   threads per key  1, 2 or 4 lanes of the warp per key in an iteration:
+//                    32 / threads_per_key lanes own keys, and all 32 lanes
+//                    fetch their bucket lines (8 lanes of 16 bytes per
+//                    128-byte line, four lines per warp instruction); more
+//                    lanes per key means fewer keys and fewer registers'
+//                    worth of probes per warp, for small jobs;
+//   group depth      1 or 2 keys owned per owning lane, i.e. up to
+//                    32 / threads_per_key x group_depth line requests a warp
+//                    has in flight;
 //   blocks per SM of the persistent grid.
 // Every configuration runs the same method and returns the same results.
 #include "probe.cuh"
@@ -233,7 +236,8 @@ cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, co
                                   int keys_per_warp, bool any_timers, uint32_t blocks, unsigned long long* ctrl,
                                   cudaStream_t s) {
   const BatchJob* j = static_cast<const BatchJob*>(jobs);
-  if (threads_per_key != 4 || (keys_per_warp != 8 && keys_per_warp != 16 && keys_per_warp != 32))
+  if (!(threads_per_key == 1 || threads_per_key == 2 || threads_per_key == 4) ||
+      keys_per_warp * threads_per_key != 32)
     return cudaErrorInvalidValue;
   const uint32_t kpw = (uint32_t)keys_per_warp;
   switch (group_depth * 2 + (any_timers ? 1 : 0)) {

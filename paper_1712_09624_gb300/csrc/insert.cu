@@ -52,12 +52,7 @@ __device__ __forceinline__ Key load_key(const uint8_t* keys, uint64_t i) {
 
 // ---------------------------------------------------------------- dedup
 // Equal keys bound for different tables are different keys.
-__global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restrict__ keys, uint64_t n, TableSet ts,
-                                                         Workspace ws) {
-  pdl_wait();
-  pdl_release();
-  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ void dedup_one(const uint8_t* __restrict__ keys, const TableSet& ts, const Workspace& ws, uint64_t i) {
   const Key k = load_key(keys, i);
   const uint32_t tid = ts.id(i);
   uint32_t pos = (uint32_t)(hash_key(k, 0x51ED270B27A2B5E3ull ^ tid) >> 16) & ws.m_mask;
@@ -82,6 +77,14 @@ __global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restri
     }
     pos = (pos + 1) & ws.m_mask;
   }
+}
+
+__global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restrict__ keys, uint64_t n, TableSet ts,
+                                                         Workspace ws) {
+  pdl_wait();
+  pdl_release();
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < n) dedup_one(keys, ts, ws, i);
 }
 
 __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint32_t& last) {
@@ -231,14 +234,9 @@ __device__ bool place_new(const TableView& t, uint32_t tid, uint32_t b, uint32_t
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
-                                                          const uint64_t* __restrict__ vals, uint64_t n,
-                                                          uint32_t now, uint32_t expiry, uint8_t* __restrict__ status,
-                                                          Workspace ws) {
-  pdl_wait();
-  pdl_release();
-  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ void phase1_one(const TableSet& ts, const uint8_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                           uint32_t now, uint32_t expiry, uint8_t* __restrict__ status, const Workspace& ws,
+                           uint64_t i) {
   P1Result r{0, 0ull};
   // The leader test's set words and the primary's snapshot are independent
   // round trips; both are requested before either is used.
@@ -287,18 +285,31 @@ __global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uin
   status[i] = r.status;
 }
 
-// Publication of phase 1's claims: each claimed slot's claimed bit is cleared
-// and its busy (and in_secondary) bits set, in one atomic XOR per key. From
-// here on the new entries are visible to every search.
-__global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t n, Workspace ws) {
+__global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
+                                                          const uint64_t* __restrict__ vals, uint64_t n,
+                                                          uint32_t now, uint32_t expiry, uint8_t* __restrict__ status,
+                                                          Workspace ws) {
   pdl_wait();
   pdl_release();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i < n) phase1_one(ts, keys, vals, now, expiry, status, ws, i);
+}
+
+// Publication of phase 1's claims: each claimed slot's claimed bit is cleared
+// and its busy (and in_secondary) bits set, in one atomic XOR per key. From
+// here on the new entries are visible to every search.
+__device__ __forceinline__ void publish_one(const TableSet& ts, const Workspace& ws, uint64_t i) {
   const unsigned long long r = ws.claim[i];
   if (!r) return;
   const TableView t = ts.of(i);
   atomicXor(ctrl_ptr(t, (uint32_t)(r >> 32)), (uint32_t)r);
+}
+
+__global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t n, Workspace ws) {
+  pdl_wait();
+  pdl_release();
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < n) publish_one(ts, ws, i);
 }
 
 // --------------------------------------------------------------- phase 2
@@ -544,15 +555,13 @@ __device__ int execute_path(const TableView& t, uint32_t tid, const uint32_t (&p
 // round trips per root); the first entry whose other bucket has a free or dead
 // slot gives a cuckoo path of length one, executed under locks. Keys without
 // one, or whose path went stale, are appended to `next`.
-__global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint8_t* __restrict__ keys,
-                                                         const uint64_t* __restrict__ vals, uint32_t now,
-                                                         uint32_t expiry, uint8_t* __restrict__ status, Workspace ws,
-                                                         const uint32_t* list, const uint32_t* count_ptr,
-                                                         uint32_t* next, uint32_t* next_count) {
-  pdl_wait();
-  pdl_release();
+// worker / workers: this thread's index among the threads sharing the pass.
+__device__ void move1_range(const TableSet& ts, const uint8_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                            uint32_t now, uint32_t expiry, uint8_t* __restrict__ status, const Workspace& ws,
+                            const uint32_t* list, const uint32_t* count_ptr, uint32_t* next, uint32_t* next_count,
+                            uint32_t worker, uint32_t workers) {
   const uint32_t count = ld32_cg(count_ptr);
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+  for (uint32_t j = worker; j < count; j += workers) {
     const uint32_t i = list[j];
     const TableView t = ts.of(i);
     const Key k = load_key(keys, i);
@@ -610,33 +619,33 @@ __global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint
   }
 }
 
-// Displacement pass over `list` (count in *count). Keys that find no path
-// are appended to `retry` (when given) for a second, low-contention pass;
-// otherwise they are FULL.
-template <int kThreadsPerBlock, int kBfsNodes, int kBfsDepth>
-__global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, const uint8_t* __restrict__ keys,
-                                                                  const uint64_t* __restrict__ vals, uint32_t now,
-                                                                  uint32_t expiry, uint8_t* __restrict__ status,
-                                                                  Workspace ws, const uint32_t* list,
-                                                                  const uint32_t* count_ptr, uint32_t* retry,
-                                                                  uint32_t* retry_count, uint32_t max_keys) {
+__global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint8_t* __restrict__ keys,
+                                                         const uint64_t* __restrict__ vals, uint32_t now,
+                                                         uint32_t expiry, uint8_t* __restrict__ status, Workspace ws,
+                                                         const uint32_t* list, const uint32_t* count_ptr,
+                                                         uint32_t* next, uint32_t* next_count) {
   pdl_wait();
   pdl_release();
-  constexpr bool kHashed = SeenSet<kBfsNodes>::kHashed;
-  static_assert(kThreadsPerBlock * (kBfsNodes * sizeof(Node) + (kHashed ? SeenSet<kBfsNodes>::kSize * 4 : 0)) <=
-                    48 * 1024,
-                "BFS state exceeds 48 KB");
+  move1_range(ts, keys, vals, now, expiry, status, ws, list, count_ptr, next, next_count,
+              blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// Displacement pass over `list` (count in *count). Keys that find no path
+// are appended to `retry` (when given) for a second, low-contention pass;
+// otherwise they are FULL. q: this thread's search queue; seen: its visited
+// set (searches of 512 nodes and more), or nullptr.
+template <int kBfsNodes, int kBfsDepth>
+__device__ void phase2_range(const TableSet& ts, const uint8_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                             uint32_t now, uint32_t expiry, uint8_t* __restrict__ status, const Workspace& ws,
+                             const uint32_t* list, const uint32_t* count_ptr, uint32_t* retry, uint32_t* retry_count,
+                             uint32_t max_keys, const Queue& q, uint32_t* seen, uint32_t worker, uint32_t workers) {
   static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
-  __shared__ Node queues[kBfsNodes][kThreadsPerBlock];
-  const Queue q{&queues[0][threadIdx.x], kThreadsPerBlock};
-  uint32_t* seen = SeenStorage<kHashed, kThreadsPerBlock, SeenSet<kBfsNodes>::kSize>::get();
   const uint32_t listed = ld32_cg(count_ptr);
   const uint32_t count = min(listed, max_keys);
   // A later pass searches wider but alone; when many keys reach it the table
   // is full rather than contended, and those beyond max_keys are FULL at once.
-  for (uint32_t j = count + blockIdx.x * blockDim.x + threadIdx.x; j < listed; j += gridDim.x * blockDim.x)
-    status[list[j]] = kStFull;
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+  for (uint32_t j = count + worker; j < listed; j += workers) status[list[j]] = kStFull;
+  for (uint32_t j = worker; j < count; j += workers) {
     const uint32_t i = list[j];
     const TableView t = ts.of(i);
     const uint32_t tid = ts.id(i);
@@ -669,16 +678,35 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
   }
 }
 
+template <int kThreadsPerBlock, int kBfsNodes, int kBfsDepth>
+__global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, const uint8_t* __restrict__ keys,
+                                                                  const uint64_t* __restrict__ vals, uint32_t now,
+                                                                  uint32_t expiry, uint8_t* __restrict__ status,
+                                                                  Workspace ws, const uint32_t* list,
+                                                                  const uint32_t* count_ptr, uint32_t* retry,
+                                                                  uint32_t* retry_count, uint32_t max_keys) {
+  pdl_wait();
+  pdl_release();
+  constexpr bool kHashed = SeenSet<kBfsNodes>::kHashed;
+  static_assert(kThreadsPerBlock * (kBfsNodes * sizeof(Node) + (kHashed ? SeenSet<kBfsNodes>::kSize * 4 : 0)) <=
+                    48 * 1024,
+                "BFS state exceeds 48 KB");
+  __shared__ Node queues[kBfsNodes][kThreadsPerBlock];
+  const Queue q{&queues[0][threadIdx.x], kThreadsPerBlock};
+  uint32_t* seen = SeenStorage<kHashed, kThreadsPerBlock, SeenSet<kBfsNodes>::kSize>::get();
+  phase2_range<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, count_ptr, retry, retry_count,
+                                     max_keys, q, seen, blockIdx.x * blockDim.x + threadIdx.x,
+                                     gridDim.x * blockDim.x);
+}
+
 // ----------------------------------------------------- fixup and finish
 // The two parts touch disjoint words (filters of the fixup list's buckets;
 // status bytes of non-leader keys), so one launch runs both: every thread
 // takes its share of the fixup list, and thread i < n finishes key i.
-__global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uint64_t n, uint8_t* __restrict__ status,
-                                                                Workspace ws) {
-  pdl_wait();
-  pdl_release();
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+__device__ void fixup_finish_range(const TableSet& ts, uint64_t n, uint8_t* __restrict__ status, const Workspace& ws,
+                                   uint64_t worker, uint64_t workers) {
+  const uint64_t stride = workers;
+  const uint64_t i = worker;
   if (ld32_cg(ws.counters + 2)) {  // the list overflowed: scan every bucket of every table
     for (uint32_t tb = 0; tb < ts.n_tables; ++tb) {
       const TableView t = ts.table(tb);
@@ -694,11 +722,134 @@ __global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uin
       if (ld32_cg(moved_ptr(t, b)) == 0u) st64_cg(bloom_ptr(t, b), 0ull);
     }
   }
-  if (i >= n) return;
-  const uint32_t leader = *ws.first_at(ws.slot_of[i]);
-  if (leader == (uint32_t)i) return;
-  const uint8_t st = status[leader];
-  status[i] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;  // FULL, BUSY, NO_TABLE copy through
+  for (uint64_t j = i; j < n; j += stride) {
+    const uint32_t leader = ld32_cg(ws.first_at(ws.slot_of[j]));
+    if (leader == (uint32_t)j) continue;
+    const uint8_t st = status[leader];
+    status[j] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;  // FULL, BUSY, NO_TABLE copy through
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uint64_t n, uint8_t* __restrict__ status,
+                                                                Workspace ws) {
+  pdl_wait();
+  pdl_release();
+  fixup_finish_range(ts, n, status, ws, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+                     (uint64_t)gridDim.x * blockDim.x);
+}
+
+// --------------------------------------------------- single-launch insert
+// The whole insert call of a small batch in one cooperative launch: the
+// stages of the chain above (dedup, phase 1, publication, the one-move pass,
+// the three search passes, fixup and finish) run in order, separated by a
+// grid barrier instead of kernel boundaries. A small batch spends most of a
+// chain's time in the chain's nine dependent launches (each one's start and
+// drain); here it pays two (the workspace clear and this kernel). All blocks
+// are resident at once (cooperative launch, grid sized by the occupancy the
+// kernel reaches), so the barrier cannot wait on a block that has not
+// started. Search queues live in 48 KB of dynamic shared memory per block: the
+// grid pass runs on 64 threads of every block (96 nodes each), the second pass
+// on one warp of each of the first 8 blocks (192 nodes), the last on one thread
+// of each of the next 16 blocks (2048 nodes and the visited set).
+constexpr int kSingleThreads = 256;
+constexpr size_t kSingleSmem = 48 * 1024;
+constexpr int kBarrierSpins = 1 << 22;  // bounded wait at a barrier (about a second or more)
+
+static_assert(96 * 64 * sizeof(Node) <= kSingleSmem, "grid pass queues exceed the shared memory");
+static_assert(192 * 32 * sizeof(Node) <= kSingleSmem, "second pass queues exceed the shared memory");
+static_assert(2048 * sizeof(Node) + SeenSet<2048>::kSize * 4 <= kSingleSmem, "last pass state exceeds the shared memory");
+
+__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier over gridDim.x resident blocks. count and gen are two
+// words of the workspace's zeroed counters: every block reads the generation,
+// then arrives on the count; the last to arrive resets the count and advances
+// the generation (release), and the others wait for it (acquire). Returns
+// false if the wait gave up after kBarrierSpins polls.
+__device__ bool grid_barrier(uint32_t* count, uint32_t* gen) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");  // this block's writes before the arrival
+    const uint32_t g = ld_acquire32(gen);
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
+    } else {
+      for (int spin = 0; ld_acquire32(gen) == g; ++spin) {
+        if (spin >= kBarrierSpins) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");  // the other blocks' writes after it
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(kSingleThreads, 2) insert_single_launch(TableSet ts, const uint8_t* __restrict__ keys,
+                                                                         const uint64_t* __restrict__ vals, uint64_t n,
+                                                                         uint32_t now, uint32_t expiry,
+                                                                         uint8_t* __restrict__ status, Workspace ws) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* bar_count = ws.counters + 8;
+  uint32_t* bar_gen = ws.counters + 9;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t threads = (uint64_t)gridDim.x * blockDim.x;
+  bool ok = true;
+  for (uint64_t i = tid; i < n; i += threads) dedup_one(keys, ts, ws, i);
+  ok &= grid_barrier(bar_count, bar_gen);
+  for (uint64_t i = tid; i < n; i += threads) phase1_one(ts, keys, vals, now, expiry, status, ws, i);
+  ok &= grid_barrier(bar_count, bar_gen);
+  for (uint64_t i = tid; i < n; i += threads) publish_one(ts, ws, i);
+  ok &= grid_barrier(bar_count, bar_gen);
+  // lists as in the chain: pending [0] -> one move -> retry [3] -> grid search -> pending [5] ->
+  // second pass -> retry [6] -> last pass. A pass whose list is empty is skipped with its barrier;
+  // every block reads the same count (final before the barrier), so all skip alike.
+  if (ld32_cg(ws.counters + 0)) {
+    move1_range(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 0, ws.retry, ws.counters + 3,
+                (uint32_t)tid, (uint32_t)threads);
+    ok &= grid_barrier(bar_count, bar_gen);
+  }
+  Node* nodes = reinterpret_cast<Node*>(smem);
+  if (ld32_cg(ws.counters + 3)) {
+    if (threadIdx.x < 64) {
+      const Queue q{nodes + threadIdx.x, 64};
+      phase2_range<96, 4>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 3, ws.pending,
+                          ws.counters + 5, 0xFFFFFFFFu, q, nullptr, blockIdx.x * 64 + threadIdx.x, gridDim.x * 64);
+    }
+    ok &= grid_barrier(bar_count, bar_gen);
+  }
+  if (ld32_cg(ws.counters + 5)) {
+    if (blockIdx.x < kSecondPassBlocks && threadIdx.x < 32) {
+      const Queue q{nodes + threadIdx.x, 32};
+      phase2_range<192, 5>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 5, ws.retry,
+                           ws.counters + 6, kSecondPassKeys, q, nullptr, blockIdx.x * 32 + threadIdx.x,
+                           kSecondPassBlocks * 32);
+    }
+    ok &= grid_barrier(bar_count, bar_gen);
+  }
+  if (ld32_cg(ws.counters + 6)) {
+    if (blockIdx.x >= kSecondPassBlocks && blockIdx.x < kSecondPassBlocks + kLastPassBlocks && threadIdx.x == 0) {
+      const Queue q{nodes, 1};
+      uint32_t* seen = reinterpret_cast<uint32_t*>(smem + 2048 * sizeof(Node));
+      phase2_range<2048, 6>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 6, (uint32_t*)nullptr,
+                            (uint32_t*)nullptr, kLastPassKeys, q, seen, blockIdx.x - kSecondPassBlocks,
+                            kLastPassBlocks);
+    }
+    ok &= grid_barrier(bar_count, bar_gen);
+  }
+  fixup_finish_range(ts, n, status, ws, tid, threads);
+  if (!ok && threadIdx.x == 0) latch_error(ts.table(0), kErrLockTimeout);
 }
 
 // ------------------------------------------------------- workspace reset
@@ -795,8 +946,70 @@ cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, co
   return launch_chained(dedup_kernel, grid_for(n, kThreads), kThreads, s, keys, n, ts, ws);
 }
 
+namespace {
+
+std::atomic<int> g_insert_launch{kInsertLaunchAuto};
+constexpr uint64_t kSingleLaunchMaxKeys = 1u << 17;  // auto: batches up to this size take one launch
+
+// Blocks per SM the single-launch kernel reaches (queried once per device; 0 if
+// it cannot run, or the device has too few SMs for its search passes).
+int single_launch_blocks_per_sm() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];  // 0 unknown, -1 cannot run, else blocks per SM
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 0;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v) return v > 0 ? v : 0;
+  int coop = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_single_launch, kSingleThreads, kSingleSmem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  v = (coop && per_sm > 0 && (uint64_t)device_sm_count() * (per_sm < 2 ? per_sm : 2) >=
+                                 kSecondPassBlocks + kLastPassBlocks)
+          ? (per_sm < 2 ? per_sm : 2)
+          : -1;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v > 0 ? v : 0;
+}
+
+cudaError_t launch_single(const TableSet& ts, const uint8_t* keys, const uint64_t* vals, uint64_t n, uint32_t now,
+                          uint32_t expiry, uint8_t* status, const Workspace& ws, cudaStream_t s, int per_sm) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  // one thread per key up to the resident limit, and at least the blocks the search passes use
+  const uint64_t want = (n + kSingleThreads - 1) / kSingleThreads;
+  const uint64_t lo = kSecondPassBlocks + kLastPassBlocks, hi = (uint64_t)device_sm_count() * per_sm;
+  cfg.gridDim = dim3((unsigned)(want < lo ? lo : (want > hi ? hi : want)));
+  cfg.blockDim = dim3(kSingleThreads);
+  cfg.dynamicSmemBytes = kSingleSmem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, insert_single_launch, ts, keys, vals, n, now, expiry, status, ws);
+}
+
+}  // namespace
+
+int set_insert_launch(int mode) {
+  if (mode != kInsertLaunchAuto && mode != kInsertLaunchChain && mode != kInsertLaunchSingle) return -1;
+  return g_insert_launch.exchange(mode);
+}
+
 cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_t* vals, uint64_t n, uint32_t now,
                           uint32_t expiry, uint8_t* status, const Workspace& ws, cudaStream_t s) {
+  const int mode = g_insert_launch.load(std::memory_order_relaxed);
+  if (mode != kInsertLaunchChain && (mode == kInsertLaunchSingle || n <= kSingleLaunchMaxKeys)) {
+    const int per_sm = single_launch_blocks_per_sm();
+    if (per_sm > 0) return launch_single(ts, keys, vals, n, now, expiry, status, ws, s, per_sm);
+  }
   cudaError_t e = launch_dedup(ts, keys, n, ws, s);
   if (e != cudaSuccess) return e;
   e = launch_chained(insert_phase1, grid_for(n, kThreads), kThreads, s, ts, keys, vals, n, now, expiry, status, ws);

@@ -66,3 +66,15 @@ def test_host_only_calls(K):
     assert lib.ckpp_create(ctypes.byref(h), ctypes.byref(g), None, 0, None) == K.CKPP_EINVAL
     assert lib.ckpp_destroy(None) == K.CKPP_EINVAL
     assert lib.ckpp_bulk_lookup(None, None, 0, None, None, 0, 0, None) == K.CKPP_EINVAL
+
+
+def test_insert_launch_mode_is_host_state(K):
+    """The insert launch mode is a host-side setting: unknown modes are
+    rejected and a set returns the previous mode (no GPU needed)."""
+    prev = K.ckpp_set_insert_launch(K.INSERT_LAUNCH_CHAIN)
+    try:
+        assert K.ckpp_set_insert_launch(K.INSERT_LAUNCH_SINGLE) == K.INSERT_LAUNCH_CHAIN
+        assert K.library().ckpp_set_insert_launch(7) == K.CKPP_EINVAL
+        assert K.ckpp_set_insert_launch(K.INSERT_LAUNCH_AUTO) == K.INSERT_LAUNCH_SINGLE
+    finally:
+        K.ckpp_set_insert_launch(prev)

@@ -84,7 +84,7 @@ def batch_setup():
     return BatchedLookup(tables, max_jobs=64), tables, qs
 
 
-@pytest.mark.parametrize("tuning", [(4, 1, 2, 32), (4, 2, 1, 32), (4, 2, 2, 8), (4, 1, 3, 16), (4, 1, 1, 8)])
+@pytest.mark.parametrize("tuning", [(1, 1, 2, 32), (1, 2, 1, 32), (4, 2, 2, 8), (2, 1, 3, 16), (4, 1, 1, 0)])
 def test_batched_equals_plain_per_table(batch_setup, tuning):
     batch, tables, qs = batch_setup
     ref = plain_results(tables, qs)
@@ -92,6 +92,38 @@ def test_batched_equals_plain_per_table(batch_setup, tuning):
              torch.full((k.shape[0],), 9, dtype=torch.uint8, device="cuda")) for _, k in qs]
     batch.set_jobs([(ti, k, ov, of) for (ti, k), (ov, of) in zip(qs, outs)])
     batch.launch(20, tuning)
+    torch.cuda.synchronize()
+    for (rv, rf), (ov, of) in zip(ref, outs):
+        assert torch.equal(rv, ov) and torch.equal(rf, of)
+
+
+def test_batched_rejects_inconsistent_tuning(batch_setup):
+    """threads_per_key is 1, 2 or 4 lanes per key; keys_per_warp, when given,
+    must be 32 / threads_per_key."""
+    from paper_1712_09624_gb300 import _ckpp as K
+    batch, _, _ = batch_setup
+    for bad in [(3, 1, 2, 0), (4, 1, 2, 32), (1, 1, 2, 8), (1, 3, 2, 0), (1, 1, 5, 0), (8, 1, 2, 4)]:
+        with pytest.raises(K.CkppError) as e:
+            batch.launch(20, bad)
+        assert e.value.code == K.CKPP_EINVAL, bad
+
+
+def test_autotune_searches_threads_per_key(batch_setup):
+    """The autotuner times every (threads per key, group depth, blocks per SM)
+    and keeps the fastest; the kept tuning still gives the plain results."""
+    from paper_1712_09624_gb300.batched import autotune
+    batch, tables, qs = batch_setup
+    outs = [(torch.zeros(k.shape[0], dtype=torch.int64, device="cuda"),
+             torch.zeros(k.shape[0], dtype=torch.uint8, device="cuda")) for _, k in qs]
+    batch.set_jobs([(ti, k, ov, of) for (ti, k), (ov, of) in zip(qs, outs)])
+    best, results = autotune(batch, sum(k.shape[0] for _, k in qs), now=20, reps=1)
+    assert {c[0] for c in results} == {1, 2, 4} and len(results) == 3 * 2 * 4
+    assert all(c[3] * c[0] == 32 for c in results) and best == min(results, key=results.get)
+    ref = plain_results(tables, qs)
+    for ov, of in outs:
+        ov.zero_()
+        of.zero_()
+    batch.launch(20)
     torch.cuda.synchronize()
     for (rv, rf), (ov, of) in zip(ref, outs):
         assert torch.equal(rv, ov) and torch.equal(rf, of)
@@ -146,7 +178,7 @@ def test_batched_max_jobs_mostly_tiny_and_empty():
              torch.full((k.shape[0],), 9, dtype=torch.uint8, device="cuda")) for _, k in qs]
     batch = BatchedLookup(tables, max_jobs=n_jobs)
     batch.set_jobs([(ti, k, ov, of) for (ti, k), (ov, of) in zip(qs, outs)])
-    for tuning in [(4, 1, 2, 32), (4, 2, 1, 8)]:
+    for tuning in [(1, 1, 2, 32), (4, 2, 1, 8)]:
         for ov, of in outs:
             ov.fill_(-7)
             of.fill_(9)

@@ -25,6 +25,17 @@ def K():
     return _ckpp
 
 
+@pytest.fixture(params=["chain", "single"])
+def insert_launch(request):
+    """Runs a test with every insert call as the kernel chain, then as one
+    cooperative launch (ckpp_set_insert_launch), restoring the mode after."""
+    from paper_1712_09624_gb300 import _ckpp
+    mode = {"chain": _ckpp.INSERT_LAUNCH_CHAIN, "single": _ckpp.INSERT_LAUNCH_SINGLE}[request.param]
+    prev = _ckpp.ckpp_set_insert_launch(mode)
+    yield request.param
+    _ckpp.ckpp_set_insert_launch(prev)
+
+
 def FT(*a, **kw):
     from paper_1712_09624_gb300.table import FlowTable
     return FlowTable(*a, **kw)
@@ -228,11 +239,11 @@ def run_stream(seed, nb, timers, n_batches, max_batch, pool_factor, max_lf=0.9):
 
 
 @pytest.mark.parametrize("seed,nb,timers", [(11, 256, False), (12, 1000, False), (13, 256, True), (14, 777, True)])
-def test_mutation_stream_parity(seed, nb, timers):
+def test_mutation_stream_parity(seed, nb, timers, insert_launch):
     run_stream(seed, nb, timers, n_batches=60, max_batch=700, pool_factor=1.3)
 
 
-def test_in_batch_duplicates_follow_index_order():
+def test_in_batch_duplicates_follow_index_order(insert_launch):
     """Sequential semantics inside a batch: the last occurrence's value wins, the
     first occurrence reports INSERTED (or UPDATED), later ones UPDATED; for a
     delete the first occurrence reports DELETED, later ones NOT_FOUND."""
@@ -251,7 +262,7 @@ def test_in_batch_duplicates_follow_index_order():
     assert download(g).check() == []
 
 
-def test_near_full_tiny_table_stays_consistent(K):
+def test_near_full_tiny_table_stays_consistent(K, insert_launch):
     """Filling past capacity: FULL keys are absent, every other key is present,
     and the table keeps its invariants (a cuckoo path search is bounded, so the
     FULL set may differ from the sequential oracle's near capacity)."""
@@ -272,7 +283,7 @@ def test_near_full_tiny_table_stays_consistent(K):
 
 
 @pytest.mark.parametrize("timers", [False, True])
-def test_single_batch_fill_to_lf095(timers):
+def test_single_batch_fill_to_lf095(timers, insert_launch):
     """One batch taking an empty table to LF 0.95 (heavy concurrent cuckoo
     displacement): every key INSERTED, invariants hold, the live set is exact."""
     nb = 1 << 16
@@ -290,7 +301,7 @@ def test_single_batch_fill_to_lf095(timers):
     assert fd.cpu().numpy().all() and (np_vals(v) == f.values).all()
 
 
-def test_two_bucket_table():
+def test_two_bucket_table(insert_launch):
     """The smallest table (2 buckets): every key's buckets are {0, 1}."""
     keys = W.make_keys(32, 62, 16)
     vals = np.arange(16, dtype=np.uint64)
