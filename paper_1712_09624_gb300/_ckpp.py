@@ -107,7 +107,7 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup", "ckpp_batch_insert",
             "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute",
             "ckpp_set_insert_launch")
-INSERT_LAUNCH_AUTO, INSERT_LAUNCH_CHAIN, INSERT_LAUNCH_SINGLE = 0, 1, 2
+INSERT_LAUNCH_CHAIN, INSERT_LAUNCH_SINGLE = 0, 1
 NOALLOC_MAX_KEYS = 65536
 MAX_SHARDS = 64
 

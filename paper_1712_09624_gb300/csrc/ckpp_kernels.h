@@ -96,10 +96,9 @@ cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, 
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws,
                          cudaStream_t s);
 
-// An insert call runs as a chain of kernels or, for small batches, as one
-// cooperative launch (insert.cu); the mode picks: auto (by batch size), the
-// chain always, or the single launch whenever the device can run it.
-constexpr int kInsertLaunchAuto = 0, kInsertLaunchChain = 1, kInsertLaunchSingle = 2;
+// An insert call runs as a chain of kernels (the default) or as one
+// cooperative launch (insert.cu), whichever mode the caller picks.
+constexpr int kInsertLaunchChain = 0, kInsertLaunchSingle = 1;
 int set_insert_launch(int mode);  // returns the previous mode, or -1 for an unknown mode
 
 cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_t* vals, uint64_t n,

@@ -753,7 +753,9 @@ __global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uin
 // of each of the next 16 blocks (2048 nodes and the visited set).
 constexpr int kSingleThreads = 256;
 constexpr size_t kSingleSmem = 48 * 1024;
-constexpr int kBarrierSpins = 1 << 22;  // bounded wait at a barrier (about a second or more)
+// Bounded wait at a barrier: about 2-4 s of polls (each a load and a 64 ns sleep), longer than
+// the bounded lock waits a stage may contain, so a barrier gives up only if a block never arrives.
+constexpr int kBarrierSpins = 1 << 22;
 
 static_assert(96 * 64 * sizeof(Node) <= kSingleSmem, "grid pass queues exceed the shared memory");
 static_assert(192 * 32 * sizeof(Node) <= kSingleSmem, "second pass queues exceed the shared memory");
@@ -948,8 +950,7 @@ cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, co
 
 namespace {
 
-std::atomic<int> g_insert_launch{kInsertLaunchAuto};
-constexpr uint64_t kSingleLaunchMaxKeys = 1u << 17;  // auto: batches up to this size take one launch
+std::atomic<int> g_insert_launch{kInsertLaunchChain};
 
 // Blocks per SM the single-launch kernel reaches (queried once per device; 0 if
 // it cannot run, or the device has too few SMs for its search passes).
@@ -999,14 +1000,14 @@ cudaError_t launch_single(const TableSet& ts, const uint8_t* keys, const uint64_
 }  // namespace
 
 int set_insert_launch(int mode) {
-  if (mode != kInsertLaunchAuto && mode != kInsertLaunchChain && mode != kInsertLaunchSingle) return -1;
+  if (mode != kInsertLaunchChain && mode != kInsertLaunchSingle) return -1;
   return g_insert_launch.exchange(mode);
 }
 
 cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_t* vals, uint64_t n, uint32_t now,
                           uint32_t expiry, uint8_t* status, const Workspace& ws, cudaStream_t s) {
   const int mode = g_insert_launch.load(std::memory_order_relaxed);
-  if (mode != kInsertLaunchChain && (mode == kInsertLaunchSingle || n <= kSingleLaunchMaxKeys)) {
+  if (mode == kInsertLaunchSingle) {
     const int per_sm = single_launch_blocks_per_sm();
     if (per_sm > 0) return launch_single(ts, keys, vals, n, now, expiry, status, ws, s, per_sm);
   }

@@ -75,6 +75,6 @@ def test_insert_launch_mode_is_host_state(K):
     try:
         assert K.ckpp_set_insert_launch(K.INSERT_LAUNCH_SINGLE) == K.INSERT_LAUNCH_CHAIN
         assert K.library().ckpp_set_insert_launch(7) == K.CKPP_EINVAL
-        assert K.ckpp_set_insert_launch(K.INSERT_LAUNCH_AUTO) == K.INSERT_LAUNCH_SINGLE
+        assert K.ckpp_set_insert_launch(K.INSERT_LAUNCH_CHAIN) == K.INSERT_LAUNCH_SINGLE
     finally:
         K.ckpp_set_insert_launch(prev)

@@ -301,6 +301,40 @@ def test_single_batch_fill_to_lf095(timers, insert_launch):
     assert fd.cpu().numpy().all() and (np_vals(v) == f.values).all()
 
 
+def test_stuck_lock_gives_up_with_busy(K, insert_launch):
+    """Failure detection without a fault: the test sets the lock bit of every
+    bucket in the table's bytes, a lock nobody will release. Keys with a free
+    slot are placed by the lock-free claims of phase 1 as usual; keys that need
+    a cuckoo path wait for a path lock, give up after the bounded wait, and
+    report BUSY; the device error word latches and ckpp_sync_status returns
+    EBUSY once, then clears. With the bits cleared again the table holds
+    exactly the INSERTED keys and keeps its invariants."""
+    nb = 64
+    g = FT(nb, seed=71)
+    keys = W.make_keys(71, 95, int(0.96 * nb * 8))
+    first = int(0.85 * nb * 8)
+    st0 = g.insert(keys[:first], np.arange(first, dtype=np.uint64)).cpu().numpy()
+    assert (st0 == K.ST_INSERTED).all()
+    assert g.sync_status() == K.CKPP_OK
+    lock_bytes = torch.from_numpy(256 + np.arange(nb) * 256 + 27).cuda()  # ctrl bit 31 of every bucket
+    g.buf[lock_bytes] |= 0x80
+    rest = keys[first:]
+    st = g.insert(rest, np.arange(rest.shape[0], dtype=np.uint64) + 10_000).cpu().numpy()
+    assert set(np.unique(st)) <= {K.ST_INSERTED, K.ST_BUSY, K.ST_FULL}
+    assert (st == K.ST_BUSY).sum() > 0 and (st == K.ST_INSERTED).sum() > 0
+    assert g.sync_status() == K.CKPP_EBUSY
+    assert g.sync_status() == K.CKPP_OK  # read and cleared
+    g.buf[lock_bytes] &= 0x7F
+    d = download(g)
+    assert d.check() == []
+    v, f = g.lookup(rest)
+    f = f.cpu().numpy()
+    assert (f == (st == K.ST_INSERTED)).all()
+    assert (np_vals(v)[f] == (np.arange(rest.shape[0], dtype=np.uint64) + 10_000)[f]).all()
+    _, f0 = g.lookup(keys[:first])
+    assert f0.cpu().numpy().all()
+
+
 def test_two_bucket_table(insert_launch):
     """The smallest table (2 buckets): every key's buckets are {0, 1}."""
     keys = W.make_keys(32, 62, 16)
