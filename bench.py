@@ -922,7 +922,8 @@ def run_served(args):
             "config": {"workload": "served form: 64 ports, Poisson bursts of 32..4096 keys, 2 G lookups/s offered, "
                                    "256 tables / 500M slots, 10% inserts", "duration_s": cfg.duration_s,
                        "footprint_budget_bytes": cfg.footprint_bytes, "insert_flush_keys": cfg.insert_flush_keys,
-                       "insert_flush_us": round(cfg.insert_flush_s * 1e6, 1)},
+                       "insert_flush_us": round(cfg.insert_flush_s * 1e6, 1),
+                       "lookup_hold_us": round(cfg.lookup_hold_s * 1e6, 1), "raw_fraction": cfg.raw_fraction},
             "batched": b, "plain_per_burst": out.get("plain")}
 
 

@@ -133,6 +133,22 @@ int ckpp_create(ckpp_table** out, const ckpp_geometry* geometry, void* dev_buf, 
  * caller must not reuse dev_buf before the table's queued work has finished. */
 int ckpp_destroy(ckpp_table* table);
 
+/* Open a table whose bytes already sit in dev_buf: a buffer a table was
+ * created in, or a copy of one (checkpoint and resume: a table is its buffer,
+ * so saving it is one device-to-host copy of ckpp_required_bytes bytes, taken
+ * while no call on the table is running, and restoring it is the copy back
+ * plus this call; no counterpart in the paper). Reads the 256-byte header on
+ * `stream` and synchronises it, checks the magic, the ABI version and the
+ * geometry (8 slots, known flags, n_buckets in range, bytes at least the
+ * geometry's size), and returns a handle over the buffer without touching the
+ * buckets; the latched device error word is kept. `now` restarts the
+ * staleness clock of a timers table (Sec. 4.2: a timed call more than 64512
+ * units after it returns CKPP_ESTALE): pass the time of the table's last expire
+ * scan, or an earlier one. dev_buf must stay untouched by the caller and
+ * outlive the handle, as for ckpp_create. Errors: CKPP_EINVAL (NULL,
+ * misaligned, too small, not a table of this ABI version), CKPP_ECUDA. */
+int ckpp_attach(ckpp_table** out, void* dev_buf, size_t bytes, uint32_t now, ckpp_stream_t stream);
+
 /* Batched lookup (Sec. 2, Sec. 4.1 and Fig. 4): for every key i, read the primary
  * bucket, compare tags, confirm the full key against the matching slot's key;
  * on a miss test the two Bloom bits of the primary's filter and read the

@@ -68,6 +68,7 @@ def _load():
         "ckpp_workspace_bytes": (sz, [u64]),
         "ckpp_create": (C.c_int, [C.POINTER(vp), gp, vp, sz, vp]),
         "ckpp_destroy": (C.c_int, [vp]),
+        "ckpp_attach": (C.c_int, [C.POINTER(vp), vp, sz, u32, vp]),
         "ckpp_bulk_lookup": (C.c_int, [vp, vp, u64, vp, vp, u32, u16, vp]),
         "ckpp_bulk_insert": (C.c_int, [vp, vp, vp, u64, u32, u16, vp, vp, sz, vp]),
         "ckpp_bulk_delete": (C.c_int, [vp, vp, u64, u32, vp, vp, sz, vp]),
@@ -106,7 +107,7 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_abi_version", "ckpp_bulk_insert_noalloc", "ckpp_bulk_lookup_variant", "ckpp_batch_bytes",
             "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup", "ckpp_batch_insert",
             "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute",
-            "ckpp_set_insert_launch")
+            "ckpp_set_insert_launch", "ckpp_attach")
 INSERT_LAUNCH_CHAIN, INSERT_LAUNCH_SINGLE = 0, 1
 NOALLOC_MAX_KEYS = 65536
 MAX_SHARDS = 64
@@ -366,3 +367,12 @@ def ckpp_set_insert_launch(mode: int) -> int:
     if rc < 0:
         raise CkppError(rc, "ckpp_set_insert_launch")
     return rc
+
+
+def ckpp_attach(buf: torch.Tensor, now: int = 0, stream=None) -> int:
+    """Handle over a table whose bytes already sit in buf (a uint8 CUDA tensor):
+    checkpoint and resume, see include/ckpp.h."""
+    _dev(buf, "buf", torch.uint8)
+    h = C.c_void_p()
+    _check(_lib.ckpp_attach(C.byref(h), _ptr(buf), buf.numel(), now, _stream(stream)), "ckpp_attach")
+    return h.value

@@ -48,6 +48,40 @@ int ckpp_create(ckpp_table** out, const ckpp_geometry* geometry, void* dev_buf, 
   return CKPP_OK;
 }
 
+int ckpp_attach(ckpp_table** out, void* dev_buf, size_t bytes, uint32_t now, ckpp_stream_t stream) {
+  if (!out || !dev_buf || !aligned(dev_buf, kAlign) || bytes < kHeaderBytes) return CKPP_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t hdr[kHeaderBytes];
+  if (cudaMemcpyAsync(hdr, dev_buf, kHeaderBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CKPP_ECUDA;
+  uint32_t magic, abi, slots, flags;
+  uint64_t nb, seed;
+  std::memcpy(&magic, hdr + kHdrMagic, 4);
+  std::memcpy(&abi, hdr + kHdrAbi, 4);
+  std::memcpy(&nb, hdr + kHdrBuckets, 8);
+  std::memcpy(&slots, hdr + kHdrSlots, 4);
+  std::memcpy(&flags, hdr + kHdrFlags, 4);
+  std::memcpy(&seed, hdr + kHdrSeed, 8);
+  ckpp_geometry g{nb, slots, flags, seed};
+  if (magic != kMagic || abi != kAbiVersion || !geometry_ok(&g) || bytes < table_bytes(&g)) return CKPP_EINVAL;
+  ckpp_table* t = new (std::nothrow) ckpp_table;
+  if (!t) return CKPP_EINVAL;
+  std::memset(t, 0, sizeof *t);
+  t->geo = g;
+  t->base = static_cast<uint8_t*>(dev_buf);
+  t->bytes = table_bytes(&g);
+  t->view.buckets = t->base + kHeaderBytes;
+  t->view.err = reinterpret_cast<uint32_t*>(t->base + kHdrErr);
+  t->view.nb = nb;
+  t->view.seed = seed;
+  t->view.timers = (flags & CKPP_TIMERS) ? 1u : 0u;
+  t->have_epoch = t->view.timers ? 1 : 0;
+  t->last_scan = now;
+  *out = t;
+  return CKPP_OK;
+}
+
 int ckpp_destroy(ckpp_table* table) {
   if (!table) return CKPP_EINVAL;
   delete table;

@@ -66,13 +66,6 @@ constexpr uint32_t kErrLockTimeout = 1u;
 constexpr uint8_t kStInserted = 1, kStUpdated = 2, kStFull = 3, kStDeleted = 4, kStNotFound = 5, kStBusy = 6,
                   kStNoTable = 7;
 
-// bounded waits
-// A bucket lock is held for microseconds (one cuckoo path's moves); a waiter
-// gives up after about 0.2 s of polls with back-off (each poll an atomic and a
-// sleep of up to 1 us), far longer than any holder, and well inside the grid
-// barrier's bound of the single-launch insert.
-constexpr int kLockSpins = 1 << 17;
-
 struct TableView {
   uint8_t* buckets;
   uint32_t* err;

@@ -51,6 +51,12 @@ __device__ __forceinline__ void exch_release(uint32_t* p, uint32_t v) {
   asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
 }
 
+// A bucket lock is held for microseconds (one cuckoo path's moves); a waiter
+// gives up after about 0.2 s of polls with back-off (each poll an atomic and a
+// sleep of up to 1 us), far longer than any holder, and well inside the grid
+// barrier's bound of the single-launch insert.
+constexpr int kLockSpins = 1 << 17;
+
 __device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint32_t& ctrl) {
   uint32_t* c = ctrl_ptr(t, b);
   for (int i = 0; i < kLockSpins; ++i) {

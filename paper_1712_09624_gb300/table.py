@@ -100,6 +100,31 @@ class FlowTable:
     def sync_status(self, stream=None) -> int:
         return K.ckpp_sync_status(self.handle, stream)
 
+    def save(self, f, stream=None) -> None:
+        """Checkpoint: the table's geometry and its whole device buffer, copied to
+        host memory once the stream's queued work is done, written to f (a path
+        or a file object) with torch.save."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        s.synchronize()
+        torch.save({"n_buckets": self.n_buckets, "timers": self.timers, "seed": self.seed,
+                    "bytes": self.buf.cpu()}, f)
+
+    @classmethod
+    def load(cls, f, device=None, now: int = 0, stream=None) -> "FlowTable":
+        """Resume a table saved with save(): its bytes go to a new device buffer,
+        opened with ckpp_attach (which checks the header). now: the time of the
+        table's last expire scan (timers tables), from which the 64512-unit
+        staleness window runs again."""
+        d = torch.load(f)
+        t = cls.__new__(cls)
+        t.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        t.n_buckets, t.timers, t.seed = int(d["n_buckets"]), bool(d["timers"]), int(d["seed"])
+        t.geo = K.geometry(t.n_buckets, t.timers, t.seed)
+        t.buf = d["bytes"].to(t.device)
+        t._ws = None
+        t.handle = K.ckpp_attach(t.buf, now, stream)
+        return t
+
     def close(self):
         if getattr(self, "handle", None):
             K.ckpp_destroy(self.handle)

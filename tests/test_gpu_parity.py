@@ -335,6 +335,42 @@ def test_stuck_lock_gives_up_with_busy(K, insert_launch):
     assert f0.cpu().numpy().all()
 
 
+def test_checkpoint_and_resume(K, tmp_path):
+    """A table is its buffer: saved to a file and loaded into a new buffer
+    (ckpp_attach checks the header), it answers exactly as the original, takes
+    the same inserts with the same statuses, and keeps the staleness window of
+    Sec. 4.2 from the time given at load. Buffers that are not a table of this
+    ABI are refused."""
+    from paper_1712_09624_gb300.table import FlowTable
+    nb = 1 << 10
+    f = W.fill(81, int(0.8 * nb * 8))
+    a = FT(nb, timers=True, seed=81)
+    assert (a.insert(f.keys, f.values, 100, 800).cpu().numpy() == K.ST_INSERTED).all()
+    a.expire(150)
+    path = tmp_path / "table.pt"
+    a.save(path)
+    b = FlowTable.load(path, now=150)
+    assert (b.n_buckets, b.timers, b.seed) == (nb, True, 81)
+    q = W.lookup_batch(81, 5000, f, 0.4).keys
+    va, fa = a.lookup(q, 200)
+    vb, fb = b.lookup(q, 200)
+    assert torch.equal(fa, fb) and torch.equal(va, vb)
+    more = W.make_keys(81, 96, 500)
+    sa = a.insert(more, np.arange(500, dtype=np.uint64), 210, 600)
+    sb = b.insert(more, np.arange(500, dtype=np.uint64), 210, 600)
+    assert torch.equal(sa, sb)
+    assert download(a).live(220) == download(b).live(220)
+    with pytest.raises(K.CkppError):  # the staleness window runs from the time given at load
+        b.lookup(q, 150 + 64513)
+    junk = torch.zeros(256 + nb * 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(K.CkppError) as e:
+        K.ckpp_attach(junk)
+    assert e.value.code == K.CKPP_EINVAL
+    with pytest.raises(K.CkppError) as e:
+        K.ckpp_attach(b.buf[: 256 + (nb - 1) * 256])  # shorter than the geometry's size
+    assert e.value.code == K.CKPP_EINVAL
+
+
 def test_two_bucket_table(insert_launch):
     """The smallest table (2 buckets): every key's buckets are {0, 1}."""
     keys = W.make_keys(32, 62, 16)
