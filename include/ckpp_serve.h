@@ -1,0 +1,115 @@
+/*
+ * ckpp_serve.h -- host-side runtime of the served form (libckpp.so).
+ *
+ * The served form answers a stream of packet bursts, each a lookup of flows or
+ * an insert of new flows on one of many tables, the way the paper's per-core
+ * flow tables see traffic (Sec. 2: packets are processed in batches, and a
+ * flow's packets are looked up after the flow is inserted). The device work is
+ * the batched calls of ckpp.h; this header is the host policy that turns the
+ * arrival stream into launches: which bursts go out in which launch, and when.
+ *
+ * Everything here is plain host code: no CUDA call, no device memory, usable
+ * without a GPU. Pointers are host pointers owned by the caller.
+ *
+ * The turn planner. Called whenever the caller's loop is free to launch, it
+ * plans one turn:
+ *  - admission: every burst that has arrived by `now`, in arrival order, while
+ *    the staging footprint (bytes_per_key x keys) of the bursts admitted and not
+ *    yet completed stays within footprint_bytes; a burst that does not fit
+ *    waits, and a burst larger than the whole budget is admitted alone once
+ *    nothing else is outstanding;
+ *  - lookups: the admitted lookup bursts go out in this turn;
+ *  - write coalescing: admitted insert bursts wait and go out together (one
+ *    multi-table insert over a contiguous range of the caller's insert pool)
+ *    once insert_flush_keys keys wait, the oldest waited insert_flush_s, a
+ *    lookup held behind them waited lookup_hold_s, the stream ended, or the
+ *    waiting inserts hold budget that a newly arrived burst needs;
+ *  - per-table arrival order: on every table, lookups and inserts take effect
+ *    in arrival order, so each lookup sees exactly the inserts of its table
+ *    that arrived before it. A turn launches, in this order, the lookups whose
+ *    table has no waiting insert; the flush of the waiting inserts; the lookups
+ *    that arrived while an insert of their table was waiting (held until that
+ *    flush). An insert that arrives for a table with a held lookup ends the
+ *    turn's admission and forces the flush (the held lookup must not see it).
+ *    A lookup beyond max_jobs ends admission too, and forces the flush of any
+ *    waiting inserts.
+ */
+#ifndef CKPP_SERVE_H
+#define CKPP_SERVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ckpp_planner ckpp_planner;
+
+typedef struct ckpp_plan_config {
+  double insert_flush_s;       /* flush once the oldest waiting insert waited this long (s) */
+  double lookup_hold_s;        /* ... or a lookup held behind them waited this long (s) */
+  uint64_t insert_flush_keys;  /* ... or this many insert keys wait */
+  uint64_t footprint_bytes;    /* staging budget of admitted, uncompleted bursts */
+  uint64_t bytes_per_key;      /* staging footprint of one key (keys in, results out) */
+  uint32_t max_jobs;           /* lookup bursts per turn (both lookup launches together), >= 1 */
+} ckpp_plan_config;
+
+/* The stream, in arrival order (arrival nondecreasing; checked). n bursts:
+ *   arrival [n] seconds since the start;  table [n] target table (< 2^20)
+ *   size    [n] keys in the burst;        insert [n] 1 = insert of new flows, 0 = lookup
+ *   offset  [n] inserts: first key in the insert pool (inserts' ranges follow one another in
+ *               arrival order); lookups: the caller's own offset (passed through to staging)
+ * The arrays are borrowed, not copied: they must outlive the planner.
+ * Errors: CKPP_EINVAL (NULL pointer, n < 0, unsorted arrival, table out of range, bad config). */
+int ckpp_plan_create(const double* arrival, const uint32_t* table, const uint32_t* size, const uint8_t* insert,
+                     const int64_t* offset, int64_t n, const ckpp_plan_config* cfg, ckpp_planner** out);
+int ckpp_plan_destroy(ckpp_planner* p);
+
+#define CKPP_PLAN_IDLE 0    /* nothing to do before host time turn->wake */
+#define CKPP_PLAN_BLOCK 1   /* the budget is full: wait for the oldest outstanding turn */
+#define CKPP_PLAN_NONE 2    /* bursts were admitted, nothing to launch yet */
+#define CKPP_PLAN_LAUNCH 3  /* launch the turn */
+
+typedef struct ckpp_turn {
+  int32_t action;        /* CKPP_PLAN_* */
+  int32_t pad;
+  double wake;           /* IDLE: host time of the next arrival or flush deadline */
+  int64_t admitted_lo;   /* bursts admitted by this call: [admitted_lo, admitted_hi) */
+  int64_t admitted_hi;
+  int64_t n_lookups;     /* bursts written to lookups[] (first lookup launch) */
+  int64_t n_inserts;     /* bursts written to inserts[] (the flush; 0 = no flush) */
+  int64_t n_after;       /* bursts written to after[] (lookups held behind the flush) */
+  int64_t insert_first;  /* insert-pool offset of inserts[0] */
+  int64_t insert_keys;   /* keys of inserts[] (a contiguous range of the insert pool) */
+  int64_t nbytes;        /* footprint the turn's bursts release when it completes */
+} ckpp_turn;
+
+/* Plans one turn at host time `now`; `outstanding` != 0 when an earlier turn
+ * has not completed. lookups/inserts/after receive burst indices (ascending)
+ * and must each hold `cap` entries; cap >= n always suffices.
+ * Errors: CKPP_EINVAL (NULL pointer, cap too small for the turn: the planner's
+ * state is then unchanged). */
+int ckpp_plan_next(ckpp_planner* p, double now, int outstanding, ckpp_turn* turn, int64_t* lookups, int64_t* inserts,
+                   int64_t* after, int64_t cap);
+/* Reports a launched turn as completed: frees its footprint (turn->nbytes). */
+int ckpp_plan_complete(ckpp_planner* p, int64_t nbytes);
+/* The planner's state: insert keys waiting, footprint outstanding, and whether
+ * every burst has been admitted and launched. Any output pointer may be NULL. */
+int ckpp_plan_state(const ckpp_planner* p, int64_t* pending_keys, int64_t* flight_bytes, int* finished);
+
+/* Writes one ckpp_lookup_job (ckpp.h) per burst bursts[i]: keys at
+ * pool_keys[t] + 16 * offset[b], out_vals at pool_vals[t] + 8 * offset[b],
+ * out_found at pool_found[t] + offset[b], n = size[b], table = t, with
+ * t = table[b]. The pool addresses are the caller's (device) buffers, used as
+ * numbers only. jobs: host memory for n_bursts records (32 bytes each).
+ * Errors: CKPP_EINVAL (NULL pointer, n_bursts < 0). */
+int ckpp_serve_stage_jobs(const int64_t* bursts, int64_t n_bursts, const uint32_t* table, const int64_t* offset,
+                          const uint32_t* size, const uint64_t* pool_keys, const uint64_t* pool_vals,
+                          const uint64_t* pool_found, void* jobs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKPP_SERVE_H */

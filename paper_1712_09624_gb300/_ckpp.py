@@ -45,7 +45,20 @@ class ckpp_batch_tuning(C.Structure):
                 ("keys_per_warp", C.c_uint32)]
 
 
+class ckpp_plan_config(C.Structure):
+    _fields_ = [("insert_flush_s", C.c_double), ("lookup_hold_s", C.c_double), ("insert_flush_keys", C.c_uint64),
+                ("footprint_bytes", C.c_uint64), ("bytes_per_key", C.c_uint64), ("max_jobs", C.c_uint32)]
+
+
+class ckpp_turn(C.Structure):
+    _fields_ = [("action", C.c_int32), ("pad", C.c_int32), ("wake", C.c_double), ("admitted_lo", C.c_int64),
+                ("admitted_hi", C.c_int64), ("n_lookups", C.c_int64), ("n_inserts", C.c_int64),
+                ("n_after", C.c_int64), ("insert_first", C.c_int64), ("insert_keys", C.c_int64),
+                ("nbytes", C.c_int64)]
+
+
 LOOKUP_BLOOM, LOOKUP_OPTIMISTIC, LOOKUP_PESSIMISTIC = 0, 1, 2
+PLAN_IDLE, PLAN_BLOCK, PLAN_NONE, PLAN_LAUNCH = 0, 1, 2, 3
 BATCH_MAX_JOBS = 8192
 JOB_BYTES = C.sizeof(ckpp_lookup_job)
 
@@ -90,6 +103,13 @@ def _load():
         "ckpp_shard_partition": (C.c_int, [vp, vp, u64, u64, u32, vp, vp, vp, vp, vp, sz, vp]),
         "ckpp_shard_unpermute": (C.c_int, [vp, u64, vp, vp, vp, vp, vp]),
         "ckpp_set_insert_launch": (C.c_int, [C.c_int]),
+        # include/ckpp_serve.h (host code)
+        "ckpp_plan_create": (C.c_int, [vp, vp, vp, vp, vp, C.c_int64, C.POINTER(ckpp_plan_config), C.POINTER(vp)]),
+        "ckpp_plan_destroy": (C.c_int, [vp]),
+        "ckpp_plan_next": (C.c_int, [vp, C.c_double, C.c_int, C.POINTER(ckpp_turn), vp, vp, vp, C.c_int64]),
+        "ckpp_plan_complete": (C.c_int, [vp, C.c_int64]),
+        "ckpp_plan_state": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+        "ckpp_serve_stage_jobs": (C.c_int, [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
         "ckpp_error_string": (C.c_char_p, [C.c_int]),
         "ckpp_abi_version": (C.c_int, []),
     }
@@ -108,6 +128,8 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_batch_create", "ckpp_batch_destroy", "ckpp_batch_lookup", "ckpp_batch_insert",
             "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute",
             "ckpp_set_insert_launch", "ckpp_attach")
+SERVE_EXPORTED = ("ckpp_plan_create", "ckpp_plan_destroy", "ckpp_plan_next", "ckpp_plan_complete",
+                  "ckpp_plan_state", "ckpp_serve_stage_jobs")
 INSERT_LAUNCH_CHAIN, INSERT_LAUNCH_SINGLE = 0, 1
 NOALLOC_MAX_KEYS = 65536
 MAX_SHARDS = 64

@@ -1,6 +1,7 @@
-"""Build libckpp.so (the CUDA library behind include/ckpp.h) for sm_103a.
+"""Build libckpp.so (the CUDA library behind include/ckpp.h, and the served
+form's host runtime behind include/ckpp_serve.h) for sm_103a.
 
-Each ``csrc/*.cu`` file is compiled by nvcc in parallel into ``_build/`` and
+Each ``csrc/*.cu`` / ``csrc/*.cpp`` file is compiled by nvcc in parallel into ``_build/`` and
 linked into ``libckpp.so`` next to this file. A rebuild happens only when a
 source or header is newer than the library (or ``force``).
 """
@@ -20,6 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libckpp.so")
 WL_LIB = os.path.join(HERE, "libckpp_workload.so")
 HEADER = os.path.join(ROOT, "include", "ckpp.h")
+SERVE_HEADER = os.path.join(ROOT, "include", "ckpp_serve.h")
 WL_HEADER = os.path.join(ROOT, "include", "ckpp_workload.h")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -45,7 +47,7 @@ def _build_lib(lib: str, sources: list[str], headers: list[str], objdir: str, fo
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -70,8 +72,9 @@ def _build_lib(lib: str, sources: list[str], headers: list[str], objdir: str, fo
 def build(force: bool = False, verbose: bool = False) -> str:
     """Build libckpp.so (the method) and libckpp_workload.so (device-side
     synthetic traffic); returns the path of libckpp.so."""
-    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))) + [HEADER]
+    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))) + [HEADER,
+                                                                                                        SERVE_HEADER]
     wl_sources = sorted(glob.glob(os.path.join(CSRC, "workload", "*.cu")))
     with ThreadPoolExecutor(max_workers=2) as ex:
         f1 = ex.submit(_build_lib, LIB, sources, headers, BUILD, force, verbose)

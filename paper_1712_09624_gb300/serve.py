@@ -30,6 +30,7 @@ burst (``ckpp_bulk_lookup`` / ``ckpp_bulk_insert``) as bursts arrive.
 
 from __future__ import annotations
 
+import ctypes
 import time
 from collections import deque
 
@@ -118,18 +119,23 @@ class Service:
         planner = TurnPlanner(st, cfg, K.BATCH_MAX_JOBS)
         nxt = 0  # plain mode: first burst not yet launched
         lib = K.library()
-        job_dtype = np.dtype([("keys", "<u8"), ("out_vals", "<u8"), ("out_found", "<u8"), ("n", "<u4"),
-                              ("table", "<u4")])
         # a ring of pinned job buffers: the host fills one while earlier copies are still queued
         ring = [torch.zeros(K.BATCH_MAX_JOBS * K.JOB_BYTES, dtype=torch.uint8).pin_memory() for _ in range(8)]
-        ring_views = [r.numpy().view(job_dtype) for r in ring]
         ring_event = [None] * len(ring)
         slot = 0
-        pool_keys = np.array([p["keys"].data_ptr() for p in self.pools], np.uint64)
-        pool_vals = np.array([p["vals"].data_ptr() for p in self.pools], np.uint64)
-        pool_found = np.array([p["found"].data_ptr() for p in self.pools], np.uint64)
+        pools = [np.array([p[name].data_ptr() for p in self.pools], np.uint64) for name in ("keys", "vals", "found")]
+        stage_args = (np.ascontiguousarray(st.table, np.uint32), np.ascontiguousarray(st.offset, np.int64),
+                      np.ascontiguousarray(st.size, np.uint32), *pools)
+        stage_ptrs = tuple(a.ctypes.data for a in stage_args)
+        jobs_ptr = self.batch.jobs.data_ptr()
+        tuning = K.ckpp_batch_tuning(*self.batch.tuning, *([0] * (4 - len(self.batch.tuning))))
+        tuning_ref = ctypes.byref(tuning)
+        batch_h = self.batch.handle
         handles = [t.handle for t in self.tables]
         ws_small = torch.empty(K.ckpp_workspace_bytes(cfg.max_burst), dtype=torch.uint8, device=dev)
+        ins_keys, ins_vals = self.ins_keys.data_ptr(), self.ins_vals.data_ptr()
+        ins_tables, ins_status = self.ins_tables.data_ptr(), self.ins_status.data_ptr()
+        ins_ws, ins_ws_bytes = self.ins_ws.data_ptr(), self.ins_ws.numel()
         launches = flushes = held = 0
         starts, groups, gpu_busy = [], [], []
         torch.cuda.synchronize(dev)
@@ -173,14 +179,8 @@ class Service:
                 if nj:
                     if ring_event[slot] is not None:
                         ring_event[slot].synchronize()  # the copy that last read this buffer is done
-                    view = ring_views[slot]
-                    tb = st.table[look_idx]
-                    off = st.offset[look_idx].astype(np.uint64)
-                    view["keys"][:nj] = pool_keys[tb] + off * np.uint64(16)
-                    view["out_vals"][:nj] = pool_vals[tb] + off * np.uint64(8)
-                    view["out_found"][:nj] = pool_found[tb] + off
-                    view["n"][:nj] = st.size[look_idx]
-                    view["table"][:nj] = tb
+                    K._check(lib.ckpp_serve_stage_jobs(look_idx.ctypes.data, nj, *stage_ptrs, ring[slot].data_ptr()),
+                             "ckpp_serve_stage_jobs")
                     nbytes_jobs = nj * K.JOB_BYTES
                     self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
                 ev_start = torch.cuda.Event(enable_timing=True)
@@ -188,22 +188,21 @@ class Service:
                 # 1. lookups whose table has no waiting insert (the job count is known here: the
                 #    prefix scan is sized to it, no device count)
                 if n_first:
-                    K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs, n_first, None, 0, self.batch.tuning,
-                                        cuda)
+                    K._check(lib.ckpp_batch_lookup(batch_h, jobs_ptr, n_first, None, 0, tuning_ref, sh),
+                             "ckpp_batch_lookup")
                     launches += 1
                 # 2. the waiting inserts, one contiguous range of the insert pool
                 if turn.inserts:
                     first = turn.insert_first
-                    lib.ckpp_batch_insert(self.batch.handle, self.ins_keys[first:].data_ptr(),
-                                          self.ins_tables[first:].data_ptr(), self.ins_vals[first:].data_ptr(),
-                                          turn.insert_keys, 0, 0, self.ins_status[first:].data_ptr(),
-                                          self.ins_ws.data_ptr(), self.ins_ws.numel(), sh)
+                    K._check(lib.ckpp_batch_insert(batch_h, ins_keys + 16 * first, ins_tables + 4 * first,
+                                                   ins_vals + 8 * first, turn.insert_keys, 0, 0, ins_status + first,
+                                                   ins_ws, ins_ws_bytes, sh), "ckpp_batch_insert")
                     launches += 1
                     flushes += 1
                 # 3. lookups held behind those inserts
                 if nj > n_first:
-                    K.ckpp_batch_lookup(self.batch.handle, self.batch.jobs[n_first * K.JOB_BYTES:], nj - n_first,
-                                        None, 0, self.batch.tuning, cuda)
+                    K._check(lib.ckpp_batch_lookup(batch_h, jobs_ptr + n_first * K.JOB_BYTES, nj - n_first, None, 0,
+                                                   tuning_ref, sh), "ckpp_batch_lookup")
                     launches += 1
                     held += nj - n_first
                 ev = torch.cuda.Event(enable_timing=True)

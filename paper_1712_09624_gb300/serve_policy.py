@@ -1,8 +1,9 @@
 """Host policy of the served form: the request stream and the turn planner.
 
-Pure host code (numpy only), so that the admission and write-coalescing rules
-can be checked without a GPU; ``serve.py`` runs the planned turns on the
-device.
+Host code only, so that the admission and write-coalescing rules can be
+checked without a GPU: the stream is drawn with numpy and the planner is the
+native one of include/ckpp_serve.h (compiled into libckpp.so, no CUDA call);
+``serve.py`` runs the planned turns on the device.
 
 Request stream: packet bursts arrive from many ports (Poisson arrivals,
 uniform burst sizes); each burst targets one table and is either a lookup of
@@ -161,8 +162,9 @@ class Turn:
 
 
 class TurnPlanner:
-    """Admission, write coalescing and per-table ordering over a pre-drawn
-    stream (module doc). ``plan`` returns one of
+    """The served form's turn planner over a pre-drawn stream: the native
+    planner of include/ckpp_serve.h (host code, no GPU needed), whose rules the
+    module doc states. ``plan`` returns one of
       ("idle", None, wake)  nothing to do before host time ``wake``;
       ("block", None, 0)    the budget is full: wait for the oldest launch;
       ("none", None, 0)     bursts were admitted, nothing to launch yet;
@@ -170,93 +172,72 @@ class TurnPlanner:
     The caller reports each completed turn with ``complete(turn)``."""
 
     def __init__(self, stream: Stream, cfg: ServeConfig, max_jobs: int):
+        import ctypes as C
+
+        from . import _ckpp as K
+        self.K, self.C, self.lib = K, C, K.library()
         self.st, self.cfg, self.max_jobs = stream, cfg, max_jobs
-        self.n = stream.arrival.shape[0]
-        self.foot = stream.size.astype(np.int64) * KEY_BYTES_IO
-        self.nxt = 0               # first burst not yet admitted
-        self.pending: list = []    # admitted insert bursts not yet launched
-        self.pending_keys = 0
-        self.pending_tables: dict = {}  # table -> waiting insert bursts
-        self.held: list = []       # admitted lookups waiting for the flush of their table's inserts
-        self.held_tables: set = set()
-        self.flight_bytes = 0      # footprint admitted and not yet completed
+        self.n = n = stream.arrival.shape[0]
+        # the planner borrows these arrays: they live as long as it does
+        self._arrays = (np.ascontiguousarray(stream.arrival, np.float64),
+                        np.ascontiguousarray(stream.table, np.uint32),
+                        np.ascontiguousarray(stream.size, np.uint32),
+                        np.ascontiguousarray(stream.insert, np.uint8),
+                        np.ascontiguousarray(stream.offset, np.int64))
+        conf = K.ckpp_plan_config(cfg.insert_flush_s, cfg.lookup_hold_s, cfg.insert_flush_keys,
+                                  cfg.footprint_bytes, KEY_BYTES_IO, max_jobs)
+        self._h = C.c_void_p()
+        K._check(self.lib.ckpp_plan_create(*(a.ctypes.data for a in self._arrays), n, C.byref(conf),
+                                           C.byref(self._h)), "ckpp_plan_create")
+        self._out = np.empty((3, max(n, 1)), np.int64)
+        self._ptrs = tuple(int(self._out[i].ctypes.data) for i in range(3))
+        self._turn = K.ckpp_turn()
+        self._turn_ref = C.byref(self._turn)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.lib.ckpp_plan_destroy(h)
+            self._h = None
+
+    def _state(self):
+        C = self.C
+        pk, fb, fin = C.c_int64(), C.c_int64(), C.c_int()
+        self.K._check(self.lib.ckpp_plan_state(self._h, C.byref(pk), C.byref(fb), C.byref(fin)), "ckpp_plan_state")
+        return pk.value, fb.value, bool(fin.value)
+
+    @property
+    def pending_keys(self) -> int:
+        """Insert keys admitted and waiting for a flush."""
+        return self._state()[0]
+
+    @property
+    def flight_bytes(self) -> int:
+        """Footprint admitted and not yet completed."""
+        return self._state()[1]
 
     def finished(self) -> bool:
         """Every burst admitted and launched."""
-        return self.nxt >= self.n and not self.pending and not self.held
-
-    def _flush_due(self, now: float) -> bool:
-        st, cfg = self.st, self.cfg
-        if not self.pending:
-            return False
-        return bool(self.pending_keys >= cfg.insert_flush_keys or self.nxt >= self.n or
-                    now - st.arrival[self.pending[0]] >= cfg.insert_flush_s or
-                    (self.held and now - st.arrival[self.held[0]] >= cfg.lookup_hold_s))
-
-    def _wake(self, now: float) -> float:
-        st, cfg = self.st, self.cfg
-        wake = st.arrival[self.nxt] if self.nxt < self.n else now
-        if self.pending:
-            wake = min(wake, st.arrival[self.pending[0]] + cfg.insert_flush_s)
-        if self.held:
-            wake = min(wake, st.arrival[self.held[0]] + cfg.lookup_hold_s)
-        return float(wake)
+        return self._state()[2]
 
     def plan(self, now: float, outstanding: bool):
-        st, cfg = self.st, self.cfg
-        arrived = self.nxt < self.n and st.arrival[self.nxt] <= now
-        flush = self._flush_due(now)
-        if not arrived and not flush:
-            return "idle", None, self._wake(now)
-        sel = slice(self.nxt, self.nxt)
-        lookups = []
-        if arrived:
-            hi = int(np.searchsorted(st.arrival, now, side="right"))
-            room = cfg.footprint_bytes - self.flight_bytes
-            fit = int(np.searchsorted(np.cumsum(self.foot[self.nxt:hi]), room, side="right"))
-            if fit == 0:
-                if self.pending:
-                    flush = True  # waiting inserts hold the budget: send them
-                elif outstanding:
-                    return "block", None, 0.0
-                else:
-                    fit = 1  # a burst larger than the budget goes alone
-            stop = self.nxt
-            for b in range(self.nxt, self.nxt + fit):
-                t = int(st.table[b])
-                if st.insert[b]:
-                    if t in self.held_tables:
-                        flush = True  # a held lookup of t must not see this insert: flush first
-                        break
-                    self.pending.append(b)
-                    self.pending_keys += int(st.size[b])
-                    self.pending_tables[t] = self.pending_tables.get(t, 0) + 1
-                else:
-                    if len(lookups) + len(self.held) >= self.max_jobs:
-                        flush = bool(self.pending)  # the job array is full
-                        break
-                    if t in self.pending_tables:
-                        self.held.append(b)
-                        self.held_tables.add(t)
-                    else:
-                        lookups.append(b)
-                stop = b + 1
-            sel = slice(self.nxt, stop)
-            self.flight_bytes += int(self.foot[sel].sum())
-            self.nxt = stop
-        flush = bool(self.pending) and (flush or self._flush_due(now))
-        if not lookups and not flush:
+        K, t = self.K, self._turn
+        rc = self.lib.ckpp_plan_next(self._h, now, 1 if outstanding else 0, self._turn_ref, *self._ptrs,
+                                     self._out.shape[1])
+        if rc != K.CKPP_OK:
+            K._check(rc, "ckpp_plan_next")
+        a = t.action
+        if a == K.PLAN_IDLE:
+            return "idle", None, t.wake
+        if a == K.PLAN_BLOCK:
+            return "block", None, 0.0
+        if a == K.PLAN_NONE:
             return "none", None, 0.0
-        turn = Turn(admitted=sel, lookups=np.asarray(lookups, np.int64))
-        if flush:
-            turn.inserts = self.pending
-            turn.insert_first = int(st.offset[self.pending[0]])
-            turn.insert_keys = self.pending_keys
-            turn.lookups_after = np.asarray(self.held, np.int64)
-            self.pending, self.pending_keys, self.pending_tables = [], 0, {}
-            self.held, self.held_tables = [], set()
-        turn.nbytes = int(self.foot[turn.done].sum())
+        out = self._out
+        turn = Turn(admitted=slice(t.admitted_lo, t.admitted_hi), lookups=out[0, :t.n_lookups].copy(),
+                    inserts=out[1, :t.n_inserts].tolist(), insert_first=t.insert_first, insert_keys=t.insert_keys,
+                    lookups_after=out[2, :t.n_after].copy(), nbytes=t.nbytes)
         return "launch", turn, 0.0
 
     def complete(self, turn: Turn):
-        self.flight_bytes -= turn.nbytes
+        self.K._check(self.lib.ckpp_plan_complete(self._h, turn.nbytes), "ckpp_plan_complete")

@@ -37,6 +37,18 @@ def test_workload_library_exports(K):
         assert hasattr(lib, name)
 
 
+def test_serve_runtime_exports(K):
+    """include/ckpp_serve.h (the served form's host runtime) is exported by
+    libckpp.so and bound by name."""
+    text = open(os.path.join(ROOT, "include", "ckpp_serve.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = sorted(set(re.findall(r"\b(ckpp_[a-z_0-9]+)\s*\(", text)))
+    assert set(K.SERVE_EXPORTED) == set(names) and len(names) == 6
+    lib = ctypes.CDLL(K.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name)
+
+
 def test_every_declared_symbol_is_exported(K):
     names = declared_functions()
     assert len(names) >= 15

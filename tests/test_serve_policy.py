@@ -1,7 +1,8 @@
 """The served form's host policy (admission within the footprint budget, write
-coalescing, per-table arrival order) on CPU: the turn planner is driven by a
-simulated clock and a simulated in-order device, and every turn it plans is
-checked."""
+coalescing, per-table arrival order) on CPU: the native turn planner
+(include/ckpp_serve.h, host code) is driven by a simulated clock and a
+simulated in-order device, every turn it plans is checked, and it plans the
+same turns as the rules written out in plain Python."""
 
 from collections import deque
 from dataclasses import replace
@@ -9,21 +10,27 @@ from dataclasses import replace
 import numpy as np
 import pytest
 
-from paper_1712_09624_gb300.serve_policy import KEY_BYTES_IO, ServeConfig, TurnPlanner, draw_stream
+from paper_1712_09624_gb300.serve_policy import KEY_BYTES_IO, ServeConfig, Turn, TurnPlanner, draw_stream
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_1712_09624_gb300 import build
+    build.build()  # the planner is host code in libckpp.so
+
 
 SMALL = ServeConfig(n_tables=8, ports=8, min_burst=32, max_burst=1024, offered_lookups_per_s=50e6,
                     insert_fraction=0.2, duration_s=0.02, footprint_bytes=4 << 20, insert_flush_keys=8192,
                     insert_flush_s=200e-6, seed=3)
 
 
-def simulate(cfg, host_s=10e-6, dev_fixed_s=5e-6, dev_per_key_s=0.2e-9, max_jobs=4096):
+def simulate(cfg, host_s=10e-6, dev_fixed_s=5e-6, dev_per_key_s=0.2e-9, max_jobs=4096, planner=TurnPlanner):
     """Runs the planner to the end. The host spends host_s per launched turn;
     the device runs turns in launch order, each taking dev_fixed_s plus
     dev_per_key_s per key. Returns the stream, the launched turns as (launch
     time, turn, insert keys waiting before the planning call, footprint
     outstanding after it) and the largest footprint ever outstanding."""
     st = draw_stream(cfg)
-    pl = TurnPlanner(st, cfg, max_jobs)
+    pl = planner(st, cfg, max_jobs)
     now, dev_free = 0.0, 0.0
     outstanding = deque()  # (finish time, turn)
     launched, max_flight = [], 0
@@ -261,3 +268,152 @@ def test_order_check_catches_lookups_run_before_their_inserts():
                             lookups_after=np.zeros(0, np.int64)), a, b) for t, turn, a, b in launched]
     with pytest.raises(AssertionError):
         check_table_order(st, moved)
+
+
+class RefPlanner:
+    """The planner's rules written in plain Python, one burst at a time, as
+    the served form's host policy states them: the native planner must plan
+    the same turns."""
+
+    def __init__(self, stream, cfg, max_jobs):
+        self.st, self.cfg, self.max_jobs = stream, cfg, max_jobs
+        self.n = stream.arrival.shape[0]
+        self.foot = stream.size.astype(np.int64) * KEY_BYTES_IO
+        self.nxt = 0
+        self.pending, self.pending_keys, self.pending_tables = [], 0, set()
+        self.held, self.held_tables = [], set()
+        self.flight_bytes = 0
+
+    def finished(self):
+        return self.nxt >= self.n and not self.pending and not self.held
+
+    def _flush_due(self, now):
+        st, cfg = self.st, self.cfg
+        return bool(self.pending) and (self.pending_keys >= cfg.insert_flush_keys or self.nxt >= self.n or
+                                       now - st.arrival[self.pending[0]] >= cfg.insert_flush_s or
+                                       (bool(self.held) and now - st.arrival[self.held[0]] >= cfg.lookup_hold_s))
+
+    def _wake(self, now):
+        st, cfg = self.st, self.cfg
+        wake = st.arrival[self.nxt] if self.nxt < self.n else now
+        if self.pending:
+            wake = min(wake, st.arrival[self.pending[0]] + cfg.insert_flush_s)
+        if self.held:
+            wake = min(wake, st.arrival[self.held[0]] + cfg.lookup_hold_s)
+        return float(wake)
+
+    def plan(self, now, outstanding):
+        st, cfg = self.st, self.cfg
+        arrived = self.nxt < self.n and st.arrival[self.nxt] <= now
+        flush = self._flush_due(now)
+        if not arrived and not flush:
+            return "idle", None, self._wake(now)
+        lo = stop = self.nxt
+        lookups = []
+        if arrived:
+            hi = lo
+            while hi < self.n and st.arrival[hi] <= now:
+                hi += 1
+            room = cfg.footprint_bytes - self.flight_bytes
+            fit, acc = 0, 0
+            while lo + fit < hi and acc + self.foot[lo + fit] <= room:
+                acc += self.foot[lo + fit]
+                fit += 1
+            if fit == 0:
+                if self.pending:
+                    flush = True
+                elif outstanding:
+                    return "block", None, 0.0
+                else:
+                    fit = 1
+            for b in range(lo, lo + fit):
+                t = int(st.table[b])
+                if st.insert[b]:
+                    if t in self.held_tables:
+                        flush = True
+                        break
+                    self.pending.append(b)
+                    self.pending_keys += int(st.size[b])
+                    self.pending_tables.add(t)
+                else:
+                    if len(lookups) + len(self.held) >= self.max_jobs:
+                        flush = True
+                        break
+                    if t in self.pending_tables:
+                        self.held.append(b)
+                        self.held_tables.add(t)
+                    else:
+                        lookups.append(b)
+                stop = b + 1
+            self.flight_bytes += int(self.foot[lo:stop].sum())
+            self.nxt = stop
+        flush = bool(self.pending) and (flush or self._flush_due(now))
+        if not lookups and not flush:
+            return "none", None, 0.0
+        turn = Turn(admitted=slice(lo, stop), lookups=np.asarray(lookups, np.int64))
+        if flush:
+            turn.inserts, turn.insert_first = self.pending, int(st.offset[self.pending[0]])
+            turn.insert_keys, turn.lookups_after = self.pending_keys, np.asarray(self.held, np.int64)
+            self.pending, self.pending_keys, self.pending_tables = [], 0, set()
+            self.held, self.held_tables = [], set()
+        turn.nbytes = int(self.foot[turn.done].sum())
+        return "launch", turn, 0.0
+
+    def complete(self, turn):
+        self.flight_bytes -= turn.nbytes
+
+
+@pytest.mark.parametrize("variant", ["small", "two_tables", "few_jobs", "tiny_budget", "many_tables"])
+def test_native_planner_equals_plain_rules(variant):
+    cfg = {"small": SMALL,
+           "two_tables": replace(SMALL, n_tables=2, insert_fraction=0.5, lookup_hold_s=5e-4),
+           "few_jobs": SMALL,
+           "tiny_budget": replace(SMALL, footprint_bytes=60_000, duration_s=0.005),
+           "many_tables": replace(SMALL, n_tables=1024)}[variant]
+    max_jobs = 3 if variant == "few_jobs" else 4096
+    runs = [simulate(cfg, max_jobs=max_jobs, planner=cls) for cls in (TurnPlanner, RefPlanner)]
+    (st, a, _), (_, b, _) = runs
+    assert len(a) == len(b)
+    for (ta, x, pa, fa), (tb, y, pb, fb) in zip(a, b):
+        assert ta == tb and pa == pb and fa == fb
+        assert x.admitted == y.admitted and x.inserts == y.inserts
+        assert np.array_equal(x.lookups, y.lookups) and np.array_equal(x.lookups_after, y.lookups_after)
+        assert x.insert_first == y.insert_first and x.insert_keys == y.insert_keys and x.nbytes == y.nbytes
+    check_common(st, a)
+
+
+def test_native_planner_argument_errors():
+    """Unsorted arrivals and a table index out of range are refused at
+    creation; an output room too small for the turn is refused without
+    changing the planner's state."""
+    import ctypes as C
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    lib = K.library()
+    conf = K.ckpp_plan_config(1e-3, 1e-3, 100, 1 << 20, KEY_BYTES_IO, 16)
+    arrival = np.array([0.0, 2e-6, 1e-6])
+    table = np.array([0, 1, 2], np.uint32)
+    size = np.array([10, 10, 10], np.uint32)
+    insert = np.array([0, 1, 0], np.uint8)
+    offset = np.zeros(3, np.int64)
+    h = C.c_void_p()
+    args = lambda arr, tb: (arr.ctypes.data, tb.ctypes.data, size.ctypes.data, insert.ctypes.data,
+                            offset.ctypes.data, 3, C.byref(conf), C.byref(h))
+    assert lib.ckpp_plan_create(*args(arrival, table)) == K.CKPP_EINVAL
+    arrival = np.sort(arrival)
+    assert lib.ckpp_plan_create(*args(arrival, np.array([0, 1 << 20, 2], np.uint32))) == K.CKPP_EINVAL
+    assert lib.ckpp_plan_create(*args(arrival, table)) == K.CKPP_OK
+    try:
+        out = np.zeros((3, 3), np.int64)
+        turn = K.ckpp_turn()
+        ptrs = [out[i].ctypes.data for i in range(3)]
+        assert lib.ckpp_plan_next(h, 1.0, 0, C.byref(turn), *ptrs, 2) == K.CKPP_EINVAL  # three bursts arrived
+        assert lib.ckpp_plan_next(h, 1.0, 0, C.byref(turn), *ptrs, 3) == K.CKPP_OK
+        assert turn.action == K.PLAN_LAUNCH and (turn.admitted_lo, turn.admitted_hi) == (0, 3)
+        assert turn.n_lookups == 2 and turn.n_inserts == 1 and turn.insert_keys == 10  # the stream ended
+        assert lib.ckpp_plan_complete(h, turn.nbytes + 1) == K.CKPP_EINVAL
+        assert lib.ckpp_plan_complete(h, turn.nbytes) == K.CKPP_OK
+        fin = C.c_int()
+        assert lib.ckpp_plan_state(h, None, None, C.byref(fin)) == K.CKPP_OK and fin.value == 1
+    finally:
+        lib.ckpp_plan_destroy(h)
