@@ -17,8 +17,7 @@
 //             entries of b1, then of b2, and the buckets they can move to; the
 //             first entry whose other bucket has a free or dead slot moves
 //             there under the locks of the path, and the key takes its slot.
-//             No shared memory, so the pass runs at full occupancy; at load
-//             factor 0.9 it places nearly every queued key.
+//             At load factor 0.9 it places nearly every queued key.
 //   phase2  - per key move1 left: breadth-first search for a longer cuckoo
 //             path without locks (queue in shared memory), then lock every
 //             bucket of the path plus the key's primary, re-validate the path,
@@ -353,10 +352,11 @@ struct Queue {
 };
 
 // Breadth-first search over buckets from b1 and b2 (lock-free reads; the path
-// is re-validated under its locks). Expanding a bucket issues the key reads of
-// its 8 slots together, then the control-word (and expiry) reads of the 8
-// buckets those entries can move to, so one level of the search costs two
-// memory round trips; a child with a free or dead slot ends the search (the
+// is re-validated under its locks). Expanding a bucket issues the reads of its
+// control word and the keys of its 8 slots together (each entry's other bucket
+// takes one hash, chosen by its in_secondary bit), then the control-word (and
+// expiry) reads of the 8 buckets those entries can move to, so one level of
+// the search costs two memory round trips; a child with a free or dead slot ends the search (the
 // first such child in queue order, i.e. a shortest path). A bucket enters the
 // queue once: small searches test the queue itself, large ones an
 // open-addressing set of 2 x kBfsNodes bucket numbers (`seen`, shared memory).
@@ -414,16 +414,15 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue&
   for (int qi = 0; qi < nq && nq < kBfsNodes; ++qi) {
     const Node cur = q[qi];
     if (cur.depth >= kBfsDepth) continue;
+    const uint32_t cc = ld32_cg(ctrl_ptr(t, cur.bucket));
     uint64_t k0[kSlots], k1[kSlots];
 #pragma unroll
     for (uint32_t sl = 0; sl < kSlots; ++sl) ld128_cg(key_ptr(t, cur.bucket, sl), k0[sl], k1[sl]);
     uint32_t y[kSlots], cy[kSlots];
     uint64_t e0[kSlots], e1[kSlots];
 #pragma unroll
-    for (uint32_t sl = 0; sl < kSlots; ++sl) {
-      const Addr e = address_of(Key{k0[sl], k1[sl]}, t.nb, t.seed);
-      y[sl] = (e.b1 == cur.bucket) ? e.b2 : e.b1;
-    }
+    for (uint32_t sl = 0; sl < kSlots; ++sl)
+      y[sl] = other_bucket(Key{k0[sl], k1[sl]}, cur.bucket, (cc >> (kInsecShift + sl)) & 1u, t.nb, t.seed);
 #pragma unroll
     for (uint32_t sl = 0; sl < kSlots; ++sl) {
       cy[sl] = ld32_cg(ctrl_ptr(t, y[sl]));
@@ -550,11 +549,87 @@ __device__ int execute_path(const TableView& t, uint32_t tid, const uint32_t (&p
   return rc;
 }
 
+// A cuckoo path of length one, found by the one-move pass: the entry in slot
+// sx of root x (a root of key k: a.b1 or a.b2) moves to free (or dead) slot
+// hole of its other bucket y, and k takes slot sx. Under the locks of x, y and
+// (when x is k's secondary) k's primary, the path is valid if slot sx is busy
+// and its entry's other bucket, from the key and in_secondary bit read under
+// the locks (one hash, which also gives the filter bits of a move to the
+// secondary), is still y, and the hole is still free or dead. The entry's value,
+// tag and expiry are read in the same round trip as its key, and the tag is
+// copied. The moves are those of execute_path. 1 placed, 0 stale path, -1 lock
+// timeout.
+__device__ int execute_move1(const TableView& t, uint32_t tid, uint32_t x, uint32_t sx, uint32_t y, uint32_t hole,
+                             const Key& k, uint64_t v, const Addr& a, uint32_t now, uint32_t expiry,
+                             const Workspace& ws) {
+  uint32_t lk[3], cw[3];
+  int nl = 0;
+  // x and y are distinct and differ from a.b1 unless x == a.b1 (the search skips y in {b1, b2})
+  const uint32_t u0 = x < y ? x : y, u1 = x < y ? y : x;
+  if (x == a.b1) {
+    lk[0] = u0;
+    lk[1] = u1;
+    nl = 2;
+  } else {
+    const uint32_t p = a.b1;
+    lk[0] = p < u0 ? p : u0;
+    lk[1] = p < u0 ? u0 : (p < u1 ? p : u1);
+    lk[2] = p < u1 ? u1 : p;
+    nl = 3;
+  }
+  if (!lock_buckets<3>(t, lk, nl, cw)) return -1;
+  int ix = 0, iy = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < nl && lk[i] == x) ix = i;
+    if (i < nl && lk[i] == y) iy = i;
+  }
+  Key ek;
+  ld128_cg(key_ptr(t, x, sx), ek.k0, ek.k1);
+  const uint64_t ev = ld64_cg(value_ptr(t, x, sx));
+  const uint32_t etag = ld16_cg(tag_ptr(t, x, sx));
+  const uint32_t eexp = t.timers ? ld16_cg(expiry_ptr(t, x, sx)) : 0u;
+  const uint32_t hexp = t.timers ? ld16_cg(expiry_ptr(t, y, hole)) : 0u;
+  const bool insec = (cw[ix] >> (kInsecShift + sx)) & 1u;
+  // one hash: H1 gives the primary of an entry in its secondary, H2 the secondary (and filter
+  // bits) of an entry in its primary
+  const uint64_t h = hash_key(ek, insec ? t.seed : t.seed ^ kSeed2Xor);
+  const uint32_t o = reduce(h, t.nb);
+  const uint32_t other = (!insec && o == x) ? (x + 1 == (uint32_t)t.nb ? 0u : x + 1) : o;
+  const uint64_t bits = (1ull << (h & 63)) | (1ull << ((h >> 6) & 63));
+  bool ok = ((cw[ix] >> sx) & 1u) && other == y;
+  const bool end_busy = (cw[iy] >> hole) & 1u;
+  if (ok && end_busy) ok = t.timers && !alive16(hexp, now);
+  if (ok) {
+    if (end_busy) evict_entry(t, tid, y, hole, cw[iy], ws);
+    st128_cg(key_ptr(t, y, hole), ek.k0, ek.k1);
+    st64_cg(value_ptr(t, y, hole), ev);
+    st16_cg(tag_ptr(t, y, hole), etag);
+    if (t.timers) st16_cg(expiry_ptr(t, y, hole), eexp);
+    cw[iy] |= 1u << hole;
+    if (!insec) {  // Sec. 4.1: primary x -> secondary y: x's filter gets the entry's bits, its counter + 1
+      cw[iy] |= 1u << (kInsecShift + hole);
+      atomicOr(reinterpret_cast<unsigned long long*>(bloom_ptr(t, x)), (unsigned long long)bits);
+      atomicAdd(moved_ptr(t, x), 1u);
+    } else {  // secondary x -> primary y: y's counter - 1, its filter reset at zero (y is locked)
+      cw[iy] &= ~(1u << (kInsecShift + hole));
+      if (atomicSub(moved_ptr(t, y), 1u) == 1u) atomicExch(reinterpret_cast<unsigned long long*>(bloom_ptr(t, y)), 0ull);
+    }
+    cw[ix] &= ~((1u << sx) | (1u << (kInsecShift + sx)));
+    place_entry(t, x, sx, k, v, a, expiry, cw[ix]);
+  }
+  unlock_buckets<3>(t, lk, nl, cw);
+  return ok ? 1 : 0;
+}
+
 // One-move pass over `list` (count in *count_ptr): for each key, the entries
 // of b1 and then of b2 are read with the buckets they can move to (two memory
-// round trips per root); the first entry whose other bucket has a free or dead
-// slot gives a cuckoo path of length one, executed under locks. Keys without
-// one, or whose path went stale, are appended to `next`.
+// round trips per root: the root's keys and control word, then the control
+// words of the buckets its entries can move to; each entry's other bucket
+// takes one hash, chosen by its in_secondary bit); the first entry whose other
+// bucket has a free or dead slot gives a cuckoo path of length one, executed
+// under locks (execute_move1). Keys without one, or whose path went stale, are
+// appended to `next`. The key's value is requested before the search.
 // worker / workers: this thread's index among the threads sharing the pass.
 __device__ void move1_range(const TableSet& ts, const uint8_t* __restrict__ keys, const uint64_t* __restrict__ vals,
                             uint32_t now, uint32_t expiry, uint8_t* __restrict__ status, const Workspace& ws,
@@ -564,52 +639,50 @@ __device__ void move1_range(const TableSet& ts, const uint8_t* __restrict__ keys
   for (uint32_t j = worker; j < count; j += workers) {
     const uint32_t i = list[j];
     const TableView t = ts.of(i);
+    const uint64_t v = vals[*ws.last_at(ws.slot_of[i])];
     const Key k = load_key(keys, i);
     const Addr a = address_of(k, t.nb, t.seed);
-    uint32_t path[kPathBuckets], slot[kPathBuckets], hole = 0;
+    uint32_t x = 0, sx = 0, y = 0, hole = 0;
     bool found = false;
     for (int r = 0; r < 2 && !found; ++r) {
-      const uint32_t x = r ? a.b2 : a.b1;
-      uint32_t y[kSlots];
+      const uint32_t root = r ? a.b2 : a.b1;
+      const uint32_t cr = ld32_cg(ctrl_ptr(t, root));
+      uint64_t k0[kSlots], k1[kSlots];
 #pragma unroll
-      for (uint32_t sl = 0; sl < kSlots; ++sl) {
-        uint64_t k0, k1;
-        ld128_cg(key_ptr(t, x, sl), k0, k1);
-        const Addr e = address_of(Key{k0, k1}, t.nb, t.seed);
-        y[sl] = (e.b1 == x) ? e.b2 : e.b1;
-      }
+      for (uint32_t sl = 0; sl < kSlots; ++sl) ld128_cg(key_ptr(t, root, sl), k0[sl], k1[sl]);
+      uint32_t yy[kSlots];
+#pragma unroll
+      for (uint32_t sl = 0; sl < kSlots; ++sl)
+        yy[sl] = other_bucket(Key{k0[sl], k1[sl]}, root, (cr >> (kInsecShift + sl)) & 1u, t.nb, t.seed);
       uint32_t cy[kSlots];
       uint64_t e0[kSlots], e1[kSlots];
 #pragma unroll
       for (uint32_t sl = 0; sl < kSlots; ++sl) {
-        cy[sl] = ld32_cg(ctrl_ptr(t, y[sl]));
+        cy[sl] = ld32_cg(ctrl_ptr(t, yy[sl]));
         if (t.timers) {
-          ld128_cg(expiry_ptr(t, y[sl], 0), e0[sl], e1[sl]);
+          ld128_cg(expiry_ptr(t, yy[sl], 0), e0[sl], e1[sl]);
         } else {
           e0[sl] = e1[sl] = 0;
         }
       }
 #pragma unroll
       for (uint32_t sl = 0; sl < kSlots; ++sl) {
-        if (found || y[sl] == a.b1 || y[sl] == a.b2) continue;  // the roots have no room
+        if (found || yy[sl] == a.b1 || yy[sl] == a.b2) continue;  // the roots have no room
         Snap s;
         s.e0 = e0[sl];
         s.e1 = e1[sl];
         const uint32_t f = free_mask(t, cy[sl], s, now);
         if (f) {
-          path[0] = x;
-          path[1] = y[sl];
-          slot[0] = sl;
+          x = root;
+          sx = sl;
+          y = yy[sl];
           hole = __ffs(f) - 1;
           found = true;
         }
       }
     }
     int rc = 0;
-    if (found) {
-      const uint64_t v = vals[*ws.last_at(ws.slot_of[i])];
-      rc = execute_path(t, ts.id(i), path, slot, 1, hole, k, v, a, now, expiry, ws);
-    }
+    if (found) rc = execute_move1(t, ts.id(i), x, sx, y, hole, k, v, a, now, expiry, ws);
     if (rc == 0) {
       next[atomicAdd(next_count, 1u)] = i;
     } else {
@@ -1020,7 +1093,7 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
   // lists: phase 1 -> pending [0] -> move1 -> retry [3] -> grid search ->
   // pending [5] -> block search -> retry [6] -> last search
   const unsigned sms = (unsigned)device_sm_count();
-  e = launch_chained(insert_move1, sms * 8, kThreads, s, ts, keys, vals, now, expiry, status, ws,
+  e = launch_chained(insert_move1, sms * 16, kThreads, s, ts, keys, vals, now, expiry, status, ws,
                      (const uint32_t*)ws.pending, (const uint32_t*)(ws.counters + 0), ws.retry, ws.counters + 3);
   if (e != cudaSuccess) return e;
   e = launch_chained(insert_phase2<kP2Threads, 96, 4>, sms * 4, kP2Threads, s, ts, keys, vals, now, expiry, status,

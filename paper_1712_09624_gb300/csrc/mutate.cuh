@@ -51,6 +51,27 @@ __device__ __forceinline__ void exch_release(uint32_t* p, uint32_t v) {
   asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
 }
 
+// Relaxed forms for several lock words at once: the atomics of a group are
+// issued together, and one fence gives the group acquire (after) or release
+// (before) ordering.
+__device__ __forceinline__ uint32_t or_relaxed(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.relaxed.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void and_relaxed(uint32_t* p, uint32_t v) {
+  [[maybe_unused]] uint32_t old;
+  asm volatile("atom.relaxed.gpu.global.and.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void exch_relaxed(uint32_t* p, uint32_t v) {
+  [[maybe_unused]] uint32_t old;
+  asm volatile("atom.relaxed.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // A bucket lock is held for microseconds (one cuckoo path's moves); a waiter
 // gives up after about 0.2 s of polls with back-off (each poll an atomic and a
 // sleep of up to 1 us), far longer than any holder, and well inside the grid
@@ -72,6 +93,58 @@ __device__ __forceinline__ bool lock_bucket(const TableView& t, uint32_t b, uint
 
 __device__ __forceinline__ void unlock_bucket(const TableView& t, uint32_t b, uint32_t ctrl) {
   exch_release(ctrl_ptr(t, b), ctrl & ~kLockBit);
+}
+
+// Lock the n buckets b[0..n) (ascending, distinct), returning their words in
+// ctrl. First all lock bits are set at once; if any was held, the ones taken
+// are dropped again and the buckets are locked one by one in index order (a
+// global order, so waiters cannot deadlock). False if a wait gave up (nothing
+// is then held).
+template <int N>
+__device__ __forceinline__ bool lock_buckets(const TableView& t, const uint32_t (&b)[N], int n, uint32_t (&ctrl)[N]) {
+  bool all = true;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) ctrl[i] = or_relaxed(ctrl_ptr(t, b[i]), kLockBit);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) all &= !(ctrl[i] & kLockBit);
+  if (all) {
+    fence_acq_rel();  // acquire: the holders' writes before their release are seen from here on
+    return true;
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n && !(ctrl[i] & kLockBit)) and_relaxed(ctrl_ptr(t, b[i]), ~kLockBit);  // nothing written: drop it
+  for (int i = 0; i < n; ++i) {
+    if (!lock_bucket(t, b[i], ctrl[i])) {
+      for (int j = i - 1; j >= 0; --j) unlock_bucket(t, b[j], ctrl[j]);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Store the words ctrl[0..n) (lock bits cleared) into the locked buckets b,
+// after one release fence for all of them.
+template <int N>
+__device__ __forceinline__ void unlock_buckets(const TableView& t, const uint32_t (&b)[N], int n,
+                                               const uint32_t (&ctrl)[N]) {
+  fence_acq_rel();
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n) exch_relaxed(ctrl_ptr(t, b[i]), ctrl[i] & ~kLockBit);
+}
+
+// The bucket an entry of bucket x can move to, from one hash of its key e: its
+// primary if it lives in its secondary (in_secondary bit set), else its
+// secondary (Sec. 2; the same collapse rule as address_of when the two hashes
+// pick the same bucket). The bit selects the hash's seed, so lanes of a warp
+// with different bits run the same instructions.
+__device__ __forceinline__ uint32_t other_bucket(const Key& e, uint32_t x, bool insec, uint64_t nb, uint64_t seed) {
+  const uint32_t o = reduce(hash_key(e, insec ? seed : seed ^ kSeed2Xor), nb);
+  const uint32_t next = x + 1 == (uint32_t)nb ? 0u : x + 1;
+  return (!insec && o == x) ? next : o;
 }
 
 // Coherent snapshot of a bucket: its first sector and (with timers) the 8 expiries.
