@@ -414,10 +414,8 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue&
   for (int qi = 0; qi < nq && nq < kBfsNodes; ++qi) {
     const Node cur = q[qi];
     if (cur.depth >= kBfsDepth) continue;
-    const uint32_t cc = ld32_cg(ctrl_ptr(t, cur.bucket));
     uint64_t k0[kSlots], k1[kSlots];
-#pragma unroll
-    for (uint32_t sl = 0; sl < kSlots; ++sl) ld128_cg(key_ptr(t, cur.bucket, sl), k0[sl], k1[sl]);
+    const uint32_t cc = load_bucket_keys(t, cur.bucket, k0, k1);
     uint32_t y[kSlots], cy[kSlots];
     uint64_t e0[kSlots], e1[kSlots];
 #pragma unroll
@@ -554,11 +552,10 @@ __device__ int execute_path(const TableView& t, uint32_t tid, const uint32_t (&p
 // hole of its other bucket y, and k takes slot sx. Under the locks of x, y and
 // (when x is k's secondary) k's primary, the path is valid if slot sx is busy
 // and its entry's other bucket, from the key and in_secondary bit read under
-// the locks (one hash, which also gives the filter bits of a move to the
-// secondary), is still y, and the hole is still free or dead. The entry's value,
-// tag and expiry are read in the same round trip as its key, and the tag is
-// copied. The moves are those of execute_path. 1 placed, 0 stale path, -1 lock
-// timeout.
+// the locks, is still y, and the hole is still free or dead. The entry's value
+// and expiry are read in the same round trip as its key; its tag and filter
+// bits come from its two hashes. The moves are those of execute_path. 1
+// placed, 0 stale path, -1 lock timeout.
 __device__ int execute_move1(const TableView& t, uint32_t tid, uint32_t x, uint32_t sx, uint32_t y, uint32_t hole,
                              const Key& k, uint64_t v, const Addr& a, uint32_t now, uint32_t expiry,
                              const Workspace& ws) {
@@ -587,16 +584,16 @@ __device__ int execute_move1(const TableView& t, uint32_t tid, uint32_t x, uint3
   Key ek;
   ld128_cg(key_ptr(t, x, sx), ek.k0, ek.k1);
   const uint64_t ev = ld64_cg(value_ptr(t, x, sx));
-  const uint32_t etag = ld16_cg(tag_ptr(t, x, sx));
   const uint32_t eexp = t.timers ? ld16_cg(expiry_ptr(t, x, sx)) : 0u;
   const uint32_t hexp = t.timers ? ld16_cg(expiry_ptr(t, y, hole)) : 0u;
   const bool insec = (cw[ix] >> (kInsecShift + sx)) & 1u;
-  // one hash: H1 gives the primary of an entry in its secondary, H2 the secondary (and filter
-  // bits) of an entry in its primary
-  const uint64_t h = hash_key(ek, insec ? t.seed : t.seed ^ kSeed2Xor);
-  const uint32_t o = reduce(h, t.nb);
-  const uint32_t other = (!insec && o == x) ? (x + 1 == (uint32_t)t.nb ? 0u : x + 1) : o;
-  const uint64_t bits = (1ull << (h & 63)) | (1ull << ((h >> 6) & 63));
+  // H1 gives the entry's tag and the primary of an entry in its secondary, H2 the secondary
+  // (and filter bits) of an entry in its primary; hashing beats a fourth memory request
+  const uint64_t h1 = hash_key(ek, t.seed), h2 = hash_key(ek, t.seed ^ kSeed2Xor);
+  const uint32_t b2 = reduce(h2, t.nb);
+  const uint32_t other = insec ? reduce(h1, t.nb) : (b2 != x ? b2 : (x + 1 == (uint32_t)t.nb ? 0u : x + 1));
+  const uint32_t etag = (uint32_t)(h1 & 0xFFFF);
+  const uint64_t bits = (1ull << (h2 & 63)) | (1ull << ((h2 >> 6) & 63));
   bool ok = ((cw[ix] >> sx) & 1u) && other == y;
   const bool end_busy = (cw[iy] >> hole) & 1u;
   if (ok && end_busy) ok = t.timers && !alive16(hexp, now);
@@ -646,10 +643,8 @@ __device__ void move1_range(const TableSet& ts, const uint8_t* __restrict__ keys
     bool found = false;
     for (int r = 0; r < 2 && !found; ++r) {
       const uint32_t root = r ? a.b2 : a.b1;
-      const uint32_t cr = ld32_cg(ctrl_ptr(t, root));
       uint64_t k0[kSlots], k1[kSlots];
-#pragma unroll
-      for (uint32_t sl = 0; sl < kSlots; ++sl) ld128_cg(key_ptr(t, root, sl), k0[sl], k1[sl]);
+      const uint32_t cr = load_bucket_keys(t, root, k0, k1);
       uint32_t yy[kSlots];
 #pragma unroll
       for (uint32_t sl = 0; sl < kSlots; ++sl)

@@ -147,6 +147,35 @@ __device__ __forceinline__ uint32_t other_bucket(const Key& e, uint32_t x, bool 
   return (!insec && o == x) ? next : o;
 }
 
+// The control word and the 8 keys of bucket b, read one 32-byte sector per
+// request: the keys of two slots share a sector, so the 8 keys and the word
+// take 5 requests (6 with timers) instead of 9 (bucket layout in
+// ckpp_device.cuh).
+__device__ __forceinline__ uint32_t load_bucket_keys(const TableView& t, uint32_t b, uint64_t (&k0)[kSlots],
+                                                     uint64_t (&k1)[kSlots]) {
+  const uint8_t* p = bucket_ptr(t, b);
+  uint64_t h[4], s1[4], s2[4], s3[4], s4[4], s5[4] = {0, 0, 0, 0};
+  ld256_cg(p, h);
+  ld256_cg(p + 32, s1);
+  ld256_cg(p + 64, s2);
+  ld256_cg(p + 128, s3);
+  ld256_cg(p + 160, s4);
+  if (t.timers) ld256_cg(p + 192, s5);
+  if (!t.timers) {  // keys 0..3 at bytes 32..95, keys 4..7 at 128..191
+    k0[0] = s1[0], k1[0] = s1[1], k0[1] = s1[2], k1[1] = s1[3];
+    k0[2] = s2[0], k1[2] = s2[1], k0[3] = s2[2], k1[3] = s2[3];
+    k0[4] = s3[0], k1[4] = s3[1], k0[5] = s3[2], k1[5] = s3[3];
+    k0[6] = s4[0], k1[6] = s4[1], k0[7] = s4[2], k1[7] = s4[3];
+  } else {  // keys 0..2 at bytes 48..95, keys 3..7 at 128..207
+    k0[0] = s1[2], k1[0] = s1[3];
+    k0[1] = s2[0], k1[1] = s2[1], k0[2] = s2[2], k1[2] = s2[3];
+    k0[3] = s3[0], k1[3] = s3[1], k0[4] = s3[2], k1[4] = s3[3];
+    k0[5] = s4[0], k1[5] = s4[1], k0[6] = s4[2], k1[6] = s4[3];
+    k0[7] = s5[0], k1[7] = s5[1];
+  }
+  return (uint32_t)h[3];  // ctrl: bytes 24..27
+}
+
 // Coherent snapshot of a bucket: its first sector and (with timers) the 8 expiries.
 struct Snap {
   uint64_t w[4];
