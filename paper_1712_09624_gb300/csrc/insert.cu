@@ -56,14 +56,12 @@ __device__ void dedup_one(const uint8_t* __restrict__ keys, const TableSet& ts, 
   const uint32_t tid = ts.id(i);
   uint32_t pos = (uint32_t)(hash_key(k, 0x51ED270B27A2B5E3ull ^ tid) >> 16) & ws.m_mask;
   for (uint32_t probe = 0; probe <= ws.m_mask; ++probe) {
-    uint32_t cur = ld32_cg(ws.first_at(pos));
+    // the CAS claims a free position or returns the index of the key group holding it
+    const uint32_t cur = atomicCAS(ws.first_at(pos), kEmpty, (uint32_t)i);
     if (cur == kEmpty) {
-      cur = atomicCAS(ws.first_at(pos), kEmpty, (uint32_t)i);
-      if (cur == kEmpty) {
-        atomicMax(ws.last_at(pos), (uint32_t)i);
-        ws.slot_of[i] = pos;
-        return;
-      }
+      atomicMax(ws.last_at(pos), (uint32_t)i);
+      ws.slot_of[i] = pos;
+      return;
     }
     // A first-index word only ever holds batch indices of one key group, so
     // the key at index cur is that group's key even while atomicMin lowers cur.
@@ -86,12 +84,21 @@ __global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restri
   if (i < n) dedup_one(keys, ts, ws, i);
 }
 
+// The first and last batch index of position p's key group (one 8-byte read).
+__device__ __forceinline__ uint2 group_of(const Workspace& ws, uint32_t p) {
+  return *reinterpret_cast<const uint2*>(ws.first_at(p));
+}
+
 __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint32_t& last) {
-  const uint32_t pos = ws.slot_of[i];
-  if (*ws.first_at(pos) != (uint32_t)i) return false;
-  last = *ws.last_at(pos);
+  const uint2 g = group_of(ws, ws.slot_of[i]);
+  if (g.x != (uint32_t)i) return false;
+  last = g.y;
   return true;
 }
+
+// Status byte of a key that is not its group's first occurrence, until the
+// finishing pass copies its leader's outcome (never returned to the caller).
+constexpr uint8_t kStFollower = 0xFF;
 
 // --------------------------------------------------------------- phase 1
 // Per leader, without locks. A key that is stored (alive or dead, Sec. 4.2) is
@@ -239,11 +246,11 @@ __device__ void phase1_one(const TableSet& ts, const uint8_t* __restrict__ keys,
   P1Result r{0, 0ull};
   // The leader test's set words and the primary's snapshot are independent
   // round trips; both are requested before either is used.
-  const uint32_t pos = ws.slot_of[i];
-  const uint32_t first = *ws.first_at(pos), last = *ws.last_at(pos);
+  const uint2 g = group_of(ws, ws.slot_of[i]);
+  const uint32_t first = g.x, last = g.y;
   if (!ts.valid(i)) {
     ws.claim[i] = 0ull;
-    if (first == (uint32_t)i) status[i] = kStNoTable;
+    status[i] = first == (uint32_t)i ? kStNoTable : kStFollower;
     return;
   }
   const TableView t = ts.of(i);
@@ -254,6 +261,7 @@ __device__ void phase1_one(const TableSet& ts, const uint8_t* __restrict__ keys,
   snap_bucket(t, a.b1, s1);
   if (first != (uint32_t)i) {
     ws.claim[i] = 0ull;
+    status[i] = kStFollower;
     return;
   }
   const uint64_t v = vals[last];
@@ -791,8 +799,8 @@ __device__ void fixup_finish_range(const TableSet& ts, uint64_t n, uint8_t* __re
     }
   }
   for (uint64_t j = i; j < n; j += stride) {
+    if (status[j] != kStFollower) continue;  // a leader: its outcome is final
     const uint32_t leader = ld32_cg(ws.first_at(ws.slot_of[j]));
-    if (leader == (uint32_t)j) continue;
     const uint8_t st = status[leader];
     status[j] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;  // FULL, BUSY, NO_TABLE copy through
   }
