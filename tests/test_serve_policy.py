@@ -417,3 +417,33 @@ def test_native_planner_argument_errors():
         assert lib.ckpp_plan_state(h, None, None, C.byref(fin)) == K.CKPP_OK and fin.value == 1
     finally:
         lib.ckpp_plan_destroy(h)
+
+
+def test_stage_jobs_writes_one_job_record_per_burst():
+    """ckpp_serve_stage_jobs (host code) turns burst indices into the batched
+    lookup's job records: each job's key, value and flag pointers are its
+    table's pool addresses advanced to the burst's offset, with its size and
+    table."""
+    from paper_1712_09624_gb300 import _ckpp as K
+    lib = K.library()
+    rng = np.random.default_rng(5)
+    n_b, n_t = 500, 7
+    table = rng.integers(0, n_t, n_b).astype(np.uint32)
+    offset = rng.integers(0, 1 << 30, n_b).astype(np.int64)
+    size = rng.integers(0, 5000, n_b).astype(np.uint32)
+    pools = [rng.integers(1 << 40, 1 << 41, n_t).astype(np.uint64) * np.uint64(256) for _ in range(3)]
+    bursts = np.sort(rng.choice(n_b, 200, replace=False)).astype(np.int64)
+    jobs = np.zeros(bursts.shape[0], np.dtype([("keys", "<u8"), ("out_vals", "<u8"), ("out_found", "<u8"),
+                                                ("n", "<u4"), ("table", "<u4")]))
+    assert jobs.itemsize == K.JOB_BYTES
+    args = [a.ctypes.data for a in (table, offset, size, *pools)]
+    assert lib.ckpp_serve_stage_jobs(bursts.ctypes.data, bursts.shape[0], *args, jobs.ctypes.data) == K.CKPP_OK
+    t = table[bursts]
+    off = offset[bursts].astype(np.uint64)
+    assert (jobs["keys"] == pools[0][t] + np.uint64(16) * off).all()
+    assert (jobs["out_vals"] == pools[1][t] + np.uint64(8) * off).all()
+    assert (jobs["out_found"] == pools[2][t] + off).all()
+    assert (jobs["n"] == size[bursts]).all() and (jobs["table"] == t).all()
+    assert lib.ckpp_serve_stage_jobs(None, 0, *args, None) == K.CKPP_OK  # nothing to stage
+    assert lib.ckpp_serve_stage_jobs(bursts.ctypes.data, -1, *args, jobs.ctypes.data) == K.CKPP_EINVAL
+    assert lib.ckpp_serve_stage_jobs(bursts.ctypes.data, 1, *args[:-1], None, jobs.ctypes.data) == K.CKPP_EINVAL
