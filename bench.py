@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--mixed-batches", type=int, default=400, help="mixed: batches (time units) to run")
     p.add_argument("--serve-seconds", type=float, default=0.2, help="served: seconds of offered traffic")
     p.add_argument("--serve-modes", default="batched,plain", help="served: arms to run")
+    p.add_argument("--serve-max-inflight", type=int, default=None,
+                   help="served: turns queued on the device at most (0: no limit)")
     p.add_argument("--serve-flush-keys", type=int, default=None,
                    help="served: coalesced inserts go out once this many keys wait (default: the loop's own)")
     p.add_argument("--serve-flush-us", type=float, default=None,
@@ -908,6 +910,8 @@ def run_served(args):
         cfg.insert_flush_keys = args.serve_flush_keys
     if args.serve_flush_us is not None:
         cfg.insert_flush_s = args.serve_flush_us * 1e-6
+    if args.serve_max_inflight is not None:
+        cfg.max_inflight = args.serve_max_inflight
     out = {}
     for mode in args.serve_modes.split(","):
         svc = Service(cfg)
@@ -923,7 +927,8 @@ def run_served(args):
                                    "256 tables / 500M slots, 10% inserts", "duration_s": cfg.duration_s,
                        "footprint_budget_bytes": cfg.footprint_bytes, "insert_flush_keys": cfg.insert_flush_keys,
                        "insert_flush_us": round(cfg.insert_flush_s * 1e6, 1),
-                       "lookup_hold_us": round(cfg.lookup_hold_s * 1e6, 1), "raw_fraction": cfg.raw_fraction},
+                       "lookup_hold_us": round(cfg.lookup_hold_s * 1e6, 1), "raw_fraction": cfg.raw_fraction,
+                       "max_inflight_turns": cfg.max_inflight},
             "batched": b, "plain_per_burst": out.get("plain")}
 
 

@@ -8,8 +8,9 @@
  * the batched calls of ckpp.h; this header is the host policy that turns the
  * arrival stream into launches: which bursts go out in which launch, and when.
  *
- * Everything here is plain host code: no CUDA call, no device memory, usable
- * without a GPU. Pointers are host pointers owned by the caller.
+ * The planner and the job staging are plain host code: no CUDA call, no device
+ * memory, usable without a GPU; their pointers are host pointers owned by the
+ * caller. The serving loops at the end drive the device through ckpp.h.
  *
  * The turn planner. Called whenever the caller's loop is free to launch, it
  * plans one turn:
@@ -39,6 +40,8 @@
 
 #include <stddef.h>
 #include <stdint.h>
+
+#include "ckpp.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -107,6 +110,71 @@ int ckpp_plan_state(const ckpp_planner* p, int64_t* pending_keys, int64_t* fligh
 int ckpp_serve_stage_jobs(const int64_t* bursts, int64_t n_bursts, const uint32_t* table, const int64_t* offset,
                           const uint32_t* size, const uint64_t* pool_keys, const uint64_t* pool_vals,
                           const uint64_t* pool_found, void* jobs);
+
+/* ------------------------------------------------------------------------
+ * The serving loops. They run a whole stream in real time on the host, on one
+ * CUDA stream, and return when every burst has completed. Host time starts at
+ * the call; a burst is admitted once its arrival time has passed.
+ *
+ * ckpp_serve_run (continuous batching) asks the planner for a turn whenever it
+ * is free to launch and, without waiting for earlier turns, stages the turn's
+ * lookup jobs in a pinned ring buffer, copies them to the device job array and
+ * launches, in this order: ckpp_batch_lookup over the lookups whose table has
+ * no waiting insert; ckpp_batch_insert over the flushed inserts (one
+ * contiguous range of the insert pool, `now` 0, ttl 0); ckpp_batch_lookup over
+ * the lookups held behind them. A turn completes when an event recorded after
+ * its launches does; its bursts then release their footprint.
+ *
+ * ckpp_serve_run_plain (the comparison arm) launches one ckpp_bulk_lookup or
+ * ckpp_bulk_insert per burst on the burst's own table, in arrival order, as
+ * bursts arrive, with one event per group of bursts launched together.
+ *
+ * Lookup burst b of table t reads keys at pool_keys[t] + 16 * offset[b] and
+ * writes values at pool_vals[t] + 8 * offset[b] and flags at pool_found[t] +
+ * offset[b] (size[b] keys). Insert burst b uses keys [offset[b], offset[b] +
+ * size[b]) of the insert pool, their values, table indices (into the batch's
+ * tables, also the stream's table numbers) and status bytes.
+ *
+ * done_at [n] out: each burst's completion time, seconds since the call's
+ * start (its turn's event, on the device clock, offset by the start event).
+ * Errors: CKPP_EINVAL (NULL, sizes), any error of the calls it makes (the run
+ * stops there; work already queued still runs), CKPP_ECUDA. */
+typedef struct ckpp_serve_buffers {
+  const uint64_t* pool_keys;   /* host [n_tables]: device address of each table's lookup keys */
+  const uint64_t* pool_vals;   /* host [n_tables]: ... of its value outputs */
+  const uint64_t* pool_found;  /* host [n_tables]: ... of its found flags */
+  uint32_t n_tables;
+  uint32_t max_jobs;           /* jobs per batched lookup launch (<= CKPP_BATCH_MAX_JOBS) */
+  const ckpp_key* ins_keys;    /* device insert pool (arrival order) */
+  const uint32_t* ins_tables;  /* device table index per insert key */
+  const uint64_t* ins_vals;    /* device value per insert key */
+  uint8_t* ins_status;         /* device status per insert key (out) */
+  void* ins_workspace;         /* device workspace for the largest insert call */
+  size_t ins_workspace_bytes;
+  ckpp_lookup_job* d_jobs;     /* device job array of max_jobs records */
+  ckpp_lookup_job* h_jobs;     /* pinned host memory: ring_slots x max_jobs records */
+  uint32_t ring_slots;         /* >= 1 */
+  uint32_t max_inflight;       /* ckpp_serve_run: turns queued on the device at most (0: no limit); at the
+                                  limit the loop waits for the oldest, and arrivals gather meanwhile */
+} ckpp_serve_buffers;
+
+typedef struct ckpp_serve_stats {
+  double wall_s;          /* from the start to the last completion */
+  double gpu_busy_s;      /* sum over turns (groups) of the device time of their launches */
+  uint64_t turns;         /* turns launched (batched) or launch groups (plain) */
+  uint64_t launches;      /* library calls made */
+  uint64_t flushes;       /* insert calls (batched) */
+  uint64_t held;          /* lookup bursts launched behind a flush (batched) */
+  uint64_t admitted;      /* bursts admitted, summed over turns */
+} ckpp_serve_stats;
+
+int ckpp_serve_run(ckpp_planner* planner, ckpp_batch* batch, const ckpp_serve_buffers* buffers,
+                   const ckpp_batch_tuning* tuning, ckpp_stream_t stream, double* done_at, ckpp_serve_stats* stats);
+
+/* tables [n_tables]: the handle of each table (the stream's table numbers);
+ * the planner only lends the stream and is not advanced. */
+int ckpp_serve_run_plain(const ckpp_planner* planner, ckpp_table* const* tables, const ckpp_serve_buffers* buffers,
+                         ckpp_stream_t stream, double* done_at, ckpp_serve_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,19 @@ class ckpp_turn(C.Structure):
                 ("nbytes", C.c_int64)]
 
 
+class ckpp_serve_buffers(C.Structure):
+    _fields_ = [("pool_keys", C.c_void_p), ("pool_vals", C.c_void_p), ("pool_found", C.c_void_p),
+                ("n_tables", C.c_uint32), ("max_jobs", C.c_uint32), ("ins_keys", C.c_void_p),
+                ("ins_tables", C.c_void_p), ("ins_vals", C.c_void_p), ("ins_status", C.c_void_p),
+                ("ins_workspace", C.c_void_p), ("ins_workspace_bytes", C.c_size_t), ("d_jobs", C.c_void_p),
+                ("h_jobs", C.c_void_p), ("ring_slots", C.c_uint32), ("max_inflight", C.c_uint32)]
+
+
+class ckpp_serve_stats(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("gpu_busy_s", C.c_double), ("turns", C.c_uint64),
+                ("launches", C.c_uint64), ("flushes", C.c_uint64), ("held", C.c_uint64), ("admitted", C.c_uint64)]
+
+
 LOOKUP_BLOOM, LOOKUP_OPTIMISTIC, LOOKUP_PESSIMISTIC = 0, 1, 2
 PLAN_IDLE, PLAN_BLOCK, PLAN_NONE, PLAN_LAUNCH = 0, 1, 2, 3
 BATCH_MAX_JOBS = 8192
@@ -110,6 +123,10 @@ def _load():
         "ckpp_plan_complete": (C.c_int, [vp, C.c_int64]),
         "ckpp_plan_state": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
         "ckpp_serve_stage_jobs": (C.c_int, [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
+        "ckpp_serve_run": (C.c_int, [vp, vp, C.POINTER(ckpp_serve_buffers), C.POINTER(ckpp_batch_tuning), vp, vp,
+                                     C.POINTER(ckpp_serve_stats)]),
+        "ckpp_serve_run_plain": (C.c_int, [vp, vp, C.POINTER(ckpp_serve_buffers), vp, vp,
+                                           C.POINTER(ckpp_serve_stats)]),
         "ckpp_error_string": (C.c_char_p, [C.c_int]),
         "ckpp_abi_version": (C.c_int, []),
     }
@@ -129,7 +146,7 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute",
             "ckpp_set_insert_launch", "ckpp_attach")
 SERVE_EXPORTED = ("ckpp_plan_create", "ckpp_plan_destroy", "ckpp_plan_next", "ckpp_plan_complete",
-                  "ckpp_plan_state", "ckpp_serve_stage_jobs")
+                  "ckpp_plan_state", "ckpp_serve_stage_jobs", "ckpp_serve_run", "ckpp_serve_run_plain")
 INSERT_LAUNCH_CHAIN, INSERT_LAUNCH_SINGLE = 0, 1
 NOALLOC_MAX_KEYS = 65536
 MAX_SHARDS = 64

@@ -7,54 +7,12 @@
 // each flush by walking the flushed bursts, so a turn costs time in the
 // bursts it touches, not in the number of tables.
 
-#include <algorithm>
-#include <cstdint>
 #include <cstring>
 #include <new>
-#include <vector>
 
-#include "../../include/ckpp.h"
-#include "../../include/ckpp_serve.h"
+#include "serve_internal.h"
 
-namespace {
-
-constexpr uint32_t kMaxTables = 1u << 20;
-
-}  // namespace
-
-struct ckpp_planner {
-  const double* arrival;
-  const uint32_t* table;
-  const uint32_t* size;
-  const uint8_t* insert;
-  const int64_t* offset;
-  int64_t n;
-  ckpp_plan_config cfg;
-  int64_t nxt = 0;                 // first burst not yet admitted
-  std::vector<int64_t> pending;    // admitted insert bursts not yet launched
-  int64_t pending_keys = 0;
-  std::vector<int64_t> held;       // admitted lookups waiting for the flush
-  std::vector<uint8_t> pend_mask;  // per table: an insert waits
-  std::vector<uint8_t> held_mask;  // per table: a lookup is held
-  std::vector<int64_t> lookups;    // scratch: this turn's free lookups
-  int64_t flight_bytes = 0;        // footprint admitted and not yet completed
-
-  int64_t foot(int64_t b) const { return int64_t(size[b]) * int64_t(cfg.bytes_per_key); }
-
-  bool flush_due(double now) const {
-    if (pending.empty()) return false;
-    return uint64_t(pending_keys) >= cfg.insert_flush_keys || nxt >= n ||
-           now - arrival[pending.front()] >= cfg.insert_flush_s ||
-           (!held.empty() && now - arrival[held.front()] >= cfg.lookup_hold_s);
-  }
-
-  double wake(double now) const {
-    double w = nxt < n ? arrival[nxt] : now;
-    if (!pending.empty()) w = std::min(w, arrival[pending.front()] + cfg.insert_flush_s);
-    if (!held.empty()) w = std::min(w, arrival[held.front()] + cfg.lookup_hold_s);
-    return w;
-  }
-};
+using ckpp_serve::kMaxTables;
 
 extern "C" int ckpp_plan_create(const double* arrival, const uint32_t* table, const uint32_t* size,
                                 const uint8_t* insert, const int64_t* offset, int64_t n, const ckpp_plan_config* cfg,

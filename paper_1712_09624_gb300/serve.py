@@ -1,38 +1,36 @@
 """Served form: a continuous-batching request loop over device-resident tables.
 
 Packet bursts arrive from many ports (``serve_policy.draw_stream``). The loop
-runs in real time on the host:
+runs in real time on the host, as native code (``ckpp_serve_run`` of
+include/ckpp_serve.h):
 
-* it retires finished launches (CUDA event queries) and frees their staging
+* it retires finished turns (CUDA event queries) and frees their staging
   footprint;
-* it asks the turn planner (``serve_policy.TurnPlanner``: admission within an
-  HBM footprint budget, write coalescing) what to launch;
-* it launches that without waiting for the previous launch, all on one
-  stream, in the turn's order: the lookups whose table has no waiting insert
-  as one persistent ``ckpp_batch_lookup`` (one job per burst); when the
-  planner flushes them, the waiting inserts as one multi-table
-  ``ckpp_batch_insert`` (an insert call has a fixed cost of several dependent
-  kernels, so coalescing writes keeps that cost from every turn); then the
-  lookups that were held behind those inserts as a second batched lookup. The
-  next turn is queued while the current one runs.
+* it asks the turn planner (admission within an HBM footprint budget, write
+  coalescing, per-table arrival order) what to launch;
+* it launches that without waiting for the previous turn, all on one stream,
+  in the turn's order: the lookups whose table has no waiting insert as one
+  persistent ``ckpp_batch_lookup`` (one job per burst); when the planner
+  flushes them, the waiting inserts as one multi-table ``ckpp_batch_insert``
+  (an insert call has a fixed cost of several dependent kernels, so
+  coalescing writes keeps that cost from every turn); then the lookups that
+  were held behind those inserts as a second batched lookup.
 
 Each table applies its lookups and inserts in arrival order (the planner's
 rule), so every burst gets the result it gets when every burst runs alone in
 arrival order. Lookups read flows of the warm fill, unknown flows, and (a
 ``raw_fraction`` of their keys) flows inserted by earlier insert bursts of
 the same table during the run; the tests compare every result with that
-sequential answer. Per-burst latency is completion time (the launch's CUDA
-event, mapped to host time) minus arrival time.
+sequential answer. Per-burst latency is completion time (the turn's CUDA
+event on the device clock, from an event recorded at the start) minus arrival
+time.
 
 The comparison arm serves the same arrival stream with one plain launch per
-burst (``ckpp_bulk_lookup`` / ``ckpp_bulk_insert``) as bursts arrive.
+burst (``ckpp_bulk_lookup`` / ``ckpp_bulk_insert``) as bursts arrive
+(``ckpp_serve_run_plain``, also native).
 """
 
 from __future__ import annotations
-
-import ctypes
-import time
-from collections import deque
 
 import numpy as np
 import torch
@@ -110,151 +108,62 @@ class Service:
     # ------------------------------------------------------------------ runs
     def run(self, mode: str = "batched", warmup_fraction: float = 0.1) -> dict:
         """Serve the whole stream in real time; mode 'batched' (continuous
-        batching) or 'plain' (one launch per burst)."""
+        batching, ckpp_serve_run) or 'plain' (one launch per burst,
+        ckpp_serve_run_plain). Both loops are native host code driving the
+        device on the current stream."""
+        import ctypes as C
+
         cfg, st, dev = self.cfg, self.stream, self.device
         cuda = torch.cuda.current_stream(dev)
         n_bursts = st.arrival.shape[0]
-        done_at = np.full(n_bursts, np.nan)
-        in_flight = deque()  # (event, bursts it completes, turn or None)
         planner = TurnPlanner(st, cfg, K.BATCH_MAX_JOBS)
-        nxt = 0  # plain mode: first burst not yet launched
-        lib = K.library()
-        # a ring of pinned job buffers: the host fills one while earlier copies are still queued
-        ring = [torch.zeros(K.BATCH_MAX_JOBS * K.JOB_BYTES, dtype=torch.uint8).pin_memory() for _ in range(8)]
-        ring_event = [None] * len(ring)
-        slot = 0
+        ring_slots = 8
+        h_jobs = torch.zeros(ring_slots * K.BATCH_MAX_JOBS * K.JOB_BYTES, dtype=torch.uint8).pin_memory()
         pools = [np.array([p[name].data_ptr() for p in self.pools], np.uint64) for name in ("keys", "vals", "found")]
-        stage_args = (np.ascontiguousarray(st.table, np.uint32), np.ascontiguousarray(st.offset, np.int64),
-                      np.ascontiguousarray(st.size, np.uint32), *pools)
-        stage_ptrs = tuple(a.ctypes.data for a in stage_args)
-        jobs_ptr = self.batch.jobs.data_ptr()
-        tuning = K.ckpp_batch_tuning(*self.batch.tuning, *([0] * (4 - len(self.batch.tuning))))
-        tuning_ref = ctypes.byref(tuning)
-        batch_h = self.batch.handle
-        handles = [t.handle for t in self.tables]
-        ws_small = torch.empty(K.ckpp_workspace_bytes(cfg.max_burst), dtype=torch.uint8, device=dev)
-        ins_keys, ins_vals = self.ins_keys.data_ptr(), self.ins_vals.data_ptr()
-        ins_tables, ins_status = self.ins_tables.data_ptr(), self.ins_status.data_ptr()
-        ins_ws, ins_ws_bytes = self.ins_ws.data_ptr(), self.ins_ws.numel()
-        launches = flushes = held = 0
-        starts, groups, gpu_busy = [], [], []
+        buf = K.ckpp_serve_buffers(
+            pools[0].ctypes.data, pools[1].ctypes.data, pools[2].ctypes.data, cfg.n_tables, K.BATCH_MAX_JOBS,
+            self.ins_keys.data_ptr(), self.ins_tables.data_ptr(), self.ins_vals.data_ptr(),
+            self.ins_status.data_ptr(), self.ins_ws.data_ptr(), self.ins_ws.numel(), self.batch.jobs.data_ptr(),
+            h_jobs.data_ptr(), ring_slots, cfg.max_inflight)
+        done_at = np.full(n_bursts, np.nan)
+        stats = K.ckpp_serve_stats()
+        lib = K.library()
         torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        t0 = time.perf_counter()
-        e0.record(cuda)
-
-        def retire(block: bool):
-            while in_flight and (block or in_flight[0][0].query()):
-                ev, idx, turn = in_flight.popleft()
-                ev.synchronize()
-                done_at[idx] = ev_time(ev)
-                if turn is not None:
-                    planner.complete(turn)
-                if starts:
-                    gpu_busy.append(starts.pop(0).elapsed_time(ev) / 1e3)
-                block = False
-
-        def ev_time(ev):
-            return e0.elapsed_time(ev) / 1e3
-
-        sh = cuda.cuda_stream
-        while (not planner.finished() if mode == "batched" else nxt < n_bursts) or in_flight:
-            retire(False)
-            now = time.perf_counter() - t0
-            if mode == "batched":
-                action, turn, wake = planner.plan(now, bool(in_flight))
-                if action == "idle":
-                    if not in_flight:
-                        time.sleep(max(0.0, min(50e-6, wake - now)))
-                    continue
-                if action == "block":
-                    retire(True)
-                    continue
-                if action == "none":
-                    continue
-                look_idx = np.concatenate([turn.lookups, turn.lookups_after])
-                n_first = turn.lookups.shape[0]
-                nj = look_idx.shape[0]
-                # the turn's host work comes first, so that its launches go out back to back
-                if nj:
-                    if ring_event[slot] is not None:
-                        ring_event[slot].synchronize()  # the copy that last read this buffer is done
-                    K._check(lib.ckpp_serve_stage_jobs(look_idx.ctypes.data, nj, *stage_ptrs, ring[slot].data_ptr()),
-                             "ckpp_serve_stage_jobs")
-                    nbytes_jobs = nj * K.JOB_BYTES
-                    self.batch.jobs[:nbytes_jobs].copy_(ring[slot][:nbytes_jobs], non_blocking=True)
-                ev_start = torch.cuda.Event(enable_timing=True)
-                ev_start.record(cuda)
-                # 1. lookups whose table has no waiting insert (the job count is known here: the
-                #    prefix scan is sized to it, no device count)
-                if n_first:
-                    K._check(lib.ckpp_batch_lookup(batch_h, jobs_ptr, n_first, None, 0, tuning_ref, sh),
-                             "ckpp_batch_lookup")
-                    launches += 1
-                # 2. the waiting inserts, one contiguous range of the insert pool
-                if turn.inserts:
-                    first = turn.insert_first
-                    K._check(lib.ckpp_batch_insert(batch_h, ins_keys + 16 * first, ins_tables + 4 * first,
-                                                   ins_vals + 8 * first, turn.insert_keys, 0, 0, ins_status + first,
-                                                   ins_ws, ins_ws_bytes, sh), "ckpp_batch_insert")
-                    launches += 1
-                    flushes += 1
-                # 3. lookups held behind those inserts
-                if nj > n_first:
-                    K._check(lib.ckpp_batch_lookup(batch_h, jobs_ptr + n_first * K.JOB_BYTES, nj - n_first, None, 0,
-                                                   tuning_ref, sh), "ckpp_batch_lookup")
-                    launches += 1
-                    held += nj - n_first
-                ev = torch.cuda.Event(enable_timing=True)
-                ev.record(cuda)
-                if nj:
-                    ring_event[slot] = ev
-                    slot = (slot + 1) % len(ring)
-                in_flight.append((ev, turn.done, turn))
-                starts.append(ev_start)
-                groups.append(turn.admitted.stop - turn.admitted.start)
-            elif nxt < n_bursts and st.arrival[nxt] <= now:  # plain: one launch per burst, as it arrives
-                hi = int(np.searchsorted(st.arrival, now, side="right"))
-                for b in range(nxt, hi):
-                    t = int(st.table[b])
-                    n = int(st.size[b])
-                    off = int(st.offset[b])
-                    if st.insert[b]:
-                        lib.ckpp_bulk_insert(handles[t], self.ins_keys[off:].data_ptr(),
-                                             self.ins_vals[off:].data_ptr(), n, 0, 0,
-                                             self.ins_status[off:].data_ptr(), ws_small.data_ptr(),
-                                             ws_small.numel(), sh)
-                    else:
-                        p = self.pools[t]
-                        lib.ckpp_bulk_lookup(handles[t], p["keys"][off:].data_ptr(), n, p["vals"][off:].data_ptr(),
-                                             p["found"][off:].data_ptr(), 0, 0, sh)
-                    launches += 1
-                ev = torch.cuda.Event(enable_timing=True)
-                ev.record(cuda)
-                in_flight.append((ev, np.arange(nxt, hi), None))
-                nxt = hi
-            elif not in_flight and nxt < n_bursts:
-                time.sleep(max(0.0, min(50e-6, st.arrival[nxt] - now)))
-        retire(True)
-        wall = time.perf_counter() - t0
+        if mode == "batched":
+            tn = self.batch.tuning
+            tuning = K.ckpp_batch_tuning(tn[0], tn[1], tn[2], tn[3] if len(tn) > 3 else 0)
+            rc = lib.ckpp_serve_run(planner._h, self.batch.handle, C.byref(buf), C.byref(tuning), cuda.cuda_stream,
+                                    done_at.ctypes.data, C.byref(stats))
+            K._check(rc, "ckpp_serve_run")
+        else:
+            handles = (C.c_void_p * cfg.n_tables)(*[t.handle for t in self.tables])
+            rc = lib.ckpp_serve_run_plain(planner._h, handles, C.byref(buf), cuda.cuda_stream, done_at.ctypes.data,
+                                          C.byref(stats))
+            K._check(rc, "ckpp_serve_run_plain")
+        torch.cuda.synchronize(dev)
+        del pools, h_jobs
+        if np.isnan(done_at).any():
+            raise RuntimeError(f"{int(np.isnan(done_at).sum())} bursts were never completed")
+        wall = stats.wall_s
         lat = (done_at - st.arrival) * 1e6
         keep = st.arrival >= warmup_fraction * cfg.duration_s
         lk = ~st.insert
         served = int(st.size[lk].sum())
+        turns = int(stats.turns)
         return {
             "mode": mode, "bursts": int(n_bursts), "lookups": served, "inserts": int(st.size[st.insert].sum()),
             "offered_glookups": round(served / cfg.duration_s / 1e9, 3),
             "achieved_glookups": round(served / wall / 1e9, 3), "wall_s": round(wall, 4),
-            "launches": launches,
-            "groups": len(groups) if groups else None,
-            "bursts_per_group": round(float(np.mean(groups)), 1) if groups else None,
-            "gpu_busy_fraction": round(float(np.sum(gpu_busy)) / wall, 3) if gpu_busy else None,
-            "gpu_ms_per_group": round(float(np.mean(gpu_busy)) * 1e3, 4) if gpu_busy else None,
+            "launches": int(stats.launches),
+            "groups": turns,
+            "bursts_per_group": round(int(stats.admitted) / turns, 1) if turns else None,
+            "gpu_busy_fraction": round(stats.gpu_busy_s / wall, 3) if wall else None,
+            "gpu_ms_per_group": round(stats.gpu_busy_s / turns * 1e3, 4) if turns else None,
             "latency_us": percentiles(lat[keep]),
             "lookup_latency_us": percentiles(lat[keep & lk]),
             "insert_latency_us": percentiles(lat[keep & st.insert]),
-            "insert_flushes": flushes if mode == "batched" else None,
-            "held_lookup_bursts": held if mode == "batched" else None,
+            "insert_flushes": int(stats.flushes) if mode == "batched" else None,
+            "held_lookup_bursts": int(stats.held) if mode == "batched" else None,
             "read_after_write_keys": int(st.raw_pos.shape[0]),
         }
 

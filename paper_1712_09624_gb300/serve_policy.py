@@ -61,6 +61,7 @@ class ServeConfig:
     insert_flush_s: float = 300e-6    # ... or the oldest has waited this long
     lookup_hold_s: float = 100e-6     # ... or a lookup held behind them has waited this long
     raw_fraction: float = 0.2         # share of lookup keys naming flows inserted earlier in the run
+    max_inflight: int = 1             # turns queued on the device at most (0: no limit)
     seed: int = 7
 
 
