@@ -78,7 +78,7 @@ inline int prepare_workspace(uint64_t n, void* workspace, size_t bytes, cudaStre
   ws.fixup = reinterpret_cast<unsigned long long*>(w + L.off_fixup);
   ws.m_mask = (uint32_t)(L.m - 1);
   ws.fix_cap = L.fix_cap;
-  return launch_workspace_clear(ws, (uint32_t)(kAlign / 4), s) == cudaSuccess ? CKPP_OK : CKPP_ECUDA;
+  return launch_workspace_clear(ws, (uint32_t)(kAlign / 4), n, s) == cudaSuccess ? CKPP_OK : CKPP_ECUDA;
 }
 
 // Sec. 4.2: a timed call more than 64512 units after the last scan could see

@@ -40,7 +40,8 @@ struct Workspace {
   uint32_t* set;        // [2m] open-addressing set of batch keys; position p holds two words side by
                         // side (one line for both): the lowest batch index of the key (kEmpty when
                         // free) and the highest
-  uint32_t* slot_of;    // [n] set position of each batch key
+  uint32_t* slot_of;    // [n] set position of each batch key, | kDupBit when its key group has other
+                        // members (cleared to 0 with the set)
   uint32_t* pending;    // [n] leaders left for the displacement pass
   uint32_t* retry;      // [n] leaders a displacement pass passes on to the next
   unsigned long long* claim;  // [n] per key: (bucket << 32) | the ctrl bits its publication flips, or 0
@@ -91,7 +92,7 @@ cudaError_t launch_batched_lookup(const TableView* tables, uint32_t n_tables, co
 
 // Resets a carved workspace for a new batch: counter_words counters to 0, the
 // dedup set's first-index words to empty and last-index words to 0 (one launch).
-cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, cudaStream_t s);
+cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, uint64_t n, cudaStream_t s);
 
 cudaError_t launch_dedup(const TableSet& ts, const uint8_t* keys, uint64_t n, const Workspace& ws,
                          cudaStream_t s);
