@@ -21,6 +21,9 @@ One JSON line on rank 0. Beside the headline `value` it reports:
   mutations  bulk_insert / bulk_delete / expire throughput on the same table;
   small_config  the small configuration (2^17 buckets x 8, LF 0.9, 1M-key
              batch), L2-resident, against the measured L2 read bandwidth;
+  sharding   the device half of a hash-sharded lookup of the same batch over 8
+             shards (partition by owner, results back in the caller's order),
+             beside one local lookup;
   cpu_baseline  the CPU oracle's lookup rate on a bounded sample (rank 0, N=1).
 
 --impl reference times the CPU oracle itself (the reference arm of this
@@ -443,10 +446,62 @@ def run_ours(args, rank, world, local_rank):
         out["e2e"] = e2e_lookup(args, table, q, dev, stream)
         out["mutations"] = mutation_rates(table, dev, stream, ins_times, seed)
         out["small_config"] = small_config(args, dev, stream)
+        out["sharding"] = shard_side(args, keys, per_launch, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, fill, q, nb, seed)
         out["cpu_baseline_all_cores"] = cpu_baseline_share_nothing(args)
     return out
+
+
+def shard_side(args, keys, lookup_s, dev, stream, n_shards: int = 8, steps: int = 10):
+    """The device half of a hash-sharded lookup on the headline batch, as if
+    over 8 GPUs: partition the 16M keys by owner (ckpp_shard_partition: the
+    owner-sorted keys and the order) and put the results back in the caller's
+    order (ckpp_shard_unpermute of the 8-byte values and the flags). Timed by
+    CUDA events (mean of `steps` after 3 warm-ups) and set against one local
+    lookup of the same batch. The all-to-alls between the two are not
+    measured (one GPU); their volume is stated."""
+    import torch
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    n = keys.shape[0]
+    ws = torch.empty(K.ckpp_shard_workspace_bytes(n, n_shards), dtype=torch.uint8, device=dev)
+    pos = torch.empty(n, dtype=torch.int32, device=dev)
+    keys_s = torch.empty((n, 16), dtype=torch.uint8, device=dev)
+    counts = torch.empty(n_shards, dtype=torch.int64, device=dev)
+    vals_in = torch.arange(n, dtype=torch.int64, device=dev)
+    flags_in = torch.ones(n, dtype=torch.uint8, device=dev)
+    vals_out = torch.empty_like(vals_in)
+    flags_out = torch.empty_like(flags_in)
+
+    def part():
+        K.ckpp_shard_partition(keys, None, args.seed, n_shards, pos, keys_s, None, counts, ws, stream)
+
+    def unperm():
+        K.ckpp_shard_unpermute(pos, vals_in, flags_in, vals_out, flags_out, stream)
+
+    def time_of(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    tp, tu = time_of(part), time_of(unperm)
+    c = counts.cpu().numpy()
+    # unpermute gathers out[i] = in[pos[i]]: with vals_in = arange, vals_out is pos, a permutation, so every
+    # index appears once
+    ok = int(c.sum()) == n and bool(torch.bincount(vals_out, minlength=n).eq(1).all()) and bool(flags_out.all())
+    return {"n_shards": n_shards, "partition_us": round(tp * 1e6, 1), "unpermute_us": round(tu * 1e6, 1),
+            "local_lookup_us": round(lookup_s * 1e6, 1),
+            "device_overhead_vs_lookup": round((tp + tu) / lookup_s, 3),
+            "largest_shard_share": round(float(c.max()) / n, 5), "consistent": ok,
+            "all_to_all_bytes_per_key": {"keys_out": 16, "results_back": 9},
+            "note": "one GPU: the partition and unpermute kernels only; the two all-to-alls are not measured"}
 
 
 def l2_read_peak(dev, stream, mib: int = 48, passes: int = 20, steps: int = 10):

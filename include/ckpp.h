@@ -348,7 +348,8 @@ size_t ckpp_shard_workspace_bytes(uint64_t n, uint32_t n_shards);
 
 /* Stable partition of a batch by shard (n_shards in [1, CKPP_MAX_SHARDS]).
  *   keys      [n] ckpp_key, 16-byte aligned;  vals [n] uint64 or NULL
- *   out_order [n] uint32: original index of the key at each sorted position
+ *   out_pos   [n] uint32: the sorted position of each key of the batch (written
+ *             in batch order; ckpp_shard_unpermute reads it the same way)
  *   out_keys  [n] ckpp_key (16-byte aligned), out_vals [n] uint64 (NULL iff
  *             vals is NULL): keys and values in sorted order, i.e. shard 0's
  *             keys first, each shard's keys in batch order
@@ -357,14 +358,15 @@ size_t ckpp_shard_workspace_bytes(uint64_t n, uint32_t n_shards);
  * All device pointers, caller-owned; asynchronous on `stream`.
  * Errors: CKPP_EINVAL, CKPP_ECUDA. */
 int ckpp_shard_partition(const ckpp_key* keys, const uint64_t* vals, uint64_t n, uint64_t seed, uint32_t n_shards,
-                         uint32_t* out_order, ckpp_key* out_keys, uint64_t* out_vals, uint64_t* out_counts,
+                         uint32_t* out_pos, ckpp_key* out_keys, uint64_t* out_vals, uint64_t* out_counts,
                          void* workspace, size_t workspace_bytes, ckpp_stream_t stream);
 
-/* Write results that arrive in sorted order back to the caller's order:
- * out[order[j]] = in[j] for j < n, for a uint64 array (in_u64/out_u64, both
- * or neither) and a uint8 array (in_u8/out_u8, both or neither). Device
- * pointers, caller-owned. Errors: CKPP_EINVAL, CKPP_ECUDA. */
-int ckpp_shard_unpermute(const uint32_t* order, uint64_t n, const uint64_t* in_u64, const uint8_t* in_u8,
+/* Bring results that arrive in sorted order back to the caller's order:
+ * out[i] = in[pos[i]] for i < n (pos: ckpp_shard_partition's out_pos), for a
+ * uint64 array (in_u64/out_u64, both or neither) and a uint8 array
+ * (in_u8/out_u8, both or neither). The outputs are written in batch order.
+ * Device pointers, caller-owned. Errors: CKPP_EINVAL, CKPP_ECUDA. */
+int ckpp_shard_unpermute(const uint32_t* pos, uint64_t n, const uint64_t* in_u64, const uint8_t* in_u8,
                          uint64_t* out_u64, uint8_t* out_u8, ckpp_stream_t stream);
 
 /* Expiration scan (Sec. 4.2): delete every dead entry of every bucket, with

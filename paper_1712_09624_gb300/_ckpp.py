@@ -373,30 +373,30 @@ def ckpp_shard_workspace_bytes(n: int, n_shards: int) -> int:
 
 
 def ckpp_shard_partition(keys: torch.Tensor, vals: torch.Tensor | None, seed: int, n_shards: int,
-                         out_order: torch.Tensor, out_keys: torch.Tensor, out_vals: torch.Tensor | None,
+                         out_pos: torch.Tensor, out_keys: torch.Tensor, out_vals: torch.Tensor | None,
                          out_counts: torch.Tensor, workspace: torch.Tensor, stream=None):
     n = keys.shape[0]
     _dev(keys, "keys", torch.uint8)
-    _dev(out_order, "out_order", (torch.int32, torch.uint32))
+    _dev(out_pos, "out_pos", (torch.int32, torch.uint32))
     _dev(out_keys, "out_keys", torch.uint8)
     _dev(out_counts, "out_counts", (torch.int64, torch.uint64))
     _dev(workspace, "workspace", torch.uint8)
     for t, name in ((vals, "vals"), (out_vals, "out_vals")):
         if t is not None:
             _dev(t, name, (torch.int64, torch.uint64))
-    _check(_lib.ckpp_shard_partition(_ptr(keys), _ptr(vals), n, seed & (2**64 - 1), n_shards, _ptr(out_order),
+    _check(_lib.ckpp_shard_partition(_ptr(keys), _ptr(vals), n, seed & (2**64 - 1), n_shards, _ptr(out_pos),
                                      _ptr(out_keys), _ptr(out_vals), _ptr(out_counts), _ptr(workspace),
                                      workspace.numel(), _stream(stream)), "ckpp_shard_partition")
 
 
-def ckpp_shard_unpermute(order: torch.Tensor, in_u64: torch.Tensor | None, in_u8: torch.Tensor | None,
+def ckpp_shard_unpermute(pos: torch.Tensor, in_u64: torch.Tensor | None, in_u8: torch.Tensor | None,
                          out_u64: torch.Tensor | None, out_u8: torch.Tensor | None, stream=None):
-    n = order.shape[0]
-    _dev(order, "order", (torch.int32, torch.uint32))
+    n = pos.shape[0]
+    _dev(pos, "pos", (torch.int32, torch.uint32))
     for t, name in ((in_u64, "in_u64"), (out_u64, "out_u64"), (in_u8, "in_u8"), (out_u8, "out_u8")):
         if t is not None:
             _dev(t, name)
-    _check(_lib.ckpp_shard_unpermute(_ptr(order), n, _ptr(in_u64), _ptr(in_u8), _ptr(out_u64), _ptr(out_u8),
+    _check(_lib.ckpp_shard_unpermute(_ptr(pos), n, _ptr(in_u64), _ptr(in_u8), _ptr(out_u64), _ptr(out_u8),
                                      _stream(stream)), "ckpp_shard_unpermute")
 
 

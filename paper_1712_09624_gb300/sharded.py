@@ -42,7 +42,7 @@ class Routed:
     way back needs."""
     keys: torch.Tensor          # [m, 16] keys this rank owns, by source rank then batch index
     vals: torch.Tensor | None   # [m] values with them (inserts)
-    order: torch.Tensor         # [n] the partition's order of the caller's batch
+    order: torch.Tensor         # [n] the partition's record of the caller's batch, for the way back
     send_counts: list           # keys sent to each rank
     recv_counts: list           # keys received from each rank
 
@@ -51,7 +51,8 @@ class ShardRouter:
     """The two all-to-alls of a sharded bulk call (module doc). partitioner:
     ``partition(keys, vals, n_shards) -> (order, keys_sorted, vals_sorted,
     counts)`` and ``unpermute(order, sorted_results) -> results`` (a list of
-    1-D tensors, each in the caller's order)."""
+    1-D tensors, each in the caller's order); ``order`` is whatever record of
+    the permutation the partitioner hands back to its own unpermute."""
 
     def __init__(self, partitioner, group=None):
         self.part = partitioner
@@ -111,22 +112,22 @@ class DevicePartitioner:
             raise ValueError(f"cannot partition {n} keys into {n_shards} shards")
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(need, dtype=torch.uint8, device=dev)
-        order = torch.empty(n, dtype=torch.int32, device=dev)
+        pos = torch.empty(n, dtype=torch.int32, device=dev)  # each key's sorted position
         keys_s = torch.empty((n, 16), dtype=torch.uint8, device=dev)
         vals_s = None if vals is None else torch.empty(n, dtype=vals.dtype, device=dev)
         counts = torch.empty(n_shards, dtype=torch.int64, device=dev)
-        K.ckpp_shard_partition(keys, vals, self.seed, n_shards, order, keys_s, vals_s, counts, self._ws, self.stream)
-        return order, keys_s, vals_s, counts
+        K.ckpp_shard_partition(keys, vals, self.seed, n_shards, pos, keys_s, vals_s, counts, self._ws, self.stream)
+        return pos, keys_s, vals_s, counts
 
-    def unpermute(self, order: torch.Tensor, sorted_results: list) -> list:
+    def unpermute(self, pos: torch.Tensor, sorted_results: list) -> list:
         K = self.K
         out = []
         for r in sorted_results:
             o = torch.empty_like(r)
             if r.element_size() == 8:
-                K.ckpp_shard_unpermute(order, r, None, o, None, self.stream)
+                K.ckpp_shard_unpermute(pos, r, None, o, None, self.stream)
             elif r.element_size() == 1:
-                K.ckpp_shard_unpermute(order, None, r, None, o, self.stream)
+                K.ckpp_shard_unpermute(pos, None, r, None, o, self.stream)
             else:
                 raise TypeError(f"results of {r.element_size()}-byte elements cannot be unpermuted")
             out.append(o)

@@ -19,7 +19,8 @@ def expected_shards(keys: np.ndarray, seed: int, n_shards: int) -> np.ndarray:
     return ((((h1 >> np.uint64(16)) & np.uint64(0xFFFF)) * np.uint64(n_shards)) >> np.uint64(16)).astype(np.int64)
 
 
-@pytest.mark.parametrize("n,n_shards", [(100_003, 1), (100_003, 3), (257, 8), (1 << 18, 64), (1, 5)])
+@pytest.mark.parametrize("n,n_shards", [(100_003, 1), (100_003, 3), (257, 8), (1 << 18, 64), (1, 5),
+                                         (3_000_017, 13), ((1 << 22) + 5, 64)])
 def test_partition_is_a_stable_sort_by_shard(n, n_shards):
     from paper_1712_09624_gb300 import _ckpp as K
     seed = 17
@@ -28,21 +29,21 @@ def test_partition_is_a_stable_sort_by_shard(n, n_shards):
     vals_np = np.arange(n, dtype=np.int64) * 3 + 1
     keys = torch.from_numpy(keys_np).cuda()
     vals = torch.from_numpy(vals_np).cuda()
-    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    pos = torch.empty(n, dtype=torch.int32, device="cuda")
     ks = torch.empty_like(keys)
     vs = torch.empty_like(vals)
     counts = torch.empty(n_shards, dtype=torch.int64, device="cuda")
     ws = torch.empty(K.ckpp_shard_workspace_bytes(n, n_shards), dtype=torch.uint8, device="cuda")
-    K.ckpp_shard_partition(keys, vals, seed, n_shards, order, ks, vs, counts, ws)
+    K.ckpp_shard_partition(keys, vals, seed, n_shards, pos, ks, vs, counts, ws)
     shard = expected_shards(keys_np, seed, n_shards)
     want = np.argsort(shard, kind="stable")
-    assert (order.cpu().numpy() == want).all()
+    assert (pos.cpu().numpy()[want] == np.arange(n)).all()  # key want[j] sits at sorted position j
     assert (ks.cpu().numpy() == keys_np[want]).all() and (vs.cpu().numpy() == vals_np[want]).all()
     assert (counts.cpu().numpy() == np.bincount(shard, minlength=n_shards)).all()
     # unpermute: results in sorted order go back to the caller's order
     back64 = torch.empty_like(vs)
     back8 = torch.empty(n, dtype=torch.uint8, device="cuda")
-    K.ckpp_shard_unpermute(order, vs, (vs & 0xFF).to(torch.uint8), back64, back8)
+    K.ckpp_shard_unpermute(pos, vs, (vs & 0xFF).to(torch.uint8), back64, back8)
     assert torch.equal(back64, vals) and torch.equal(back8, (vals & 0xFF).to(torch.uint8))
 
 
