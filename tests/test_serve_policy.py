@@ -447,3 +447,27 @@ def test_stage_jobs_writes_one_job_record_per_burst():
     assert lib.ckpp_serve_stage_jobs(None, 0, *args, None) == K.CKPP_OK  # nothing to stage
     assert lib.ckpp_serve_stage_jobs(bursts.ctypes.data, -1, *args, jobs.ctypes.data) == K.CKPP_EINVAL
     assert lib.ckpp_serve_stage_jobs(bursts.ctypes.data, 1, *args[:-1], None, jobs.ctypes.data) == K.CKPP_EINVAL
+
+
+def test_serving_loops_refuse_bad_arguments_without_a_gpu():
+    """The native serving loops check their arguments before any CUDA call:
+    missing pointers and a buffer set whose tables do not cover the stream
+    are refused with CKPP_EINVAL."""
+    import ctypes as C
+
+    from paper_1712_09624_gb300 import _ckpp as K
+    lib = K.library()
+    stats = K.ckpp_serve_stats()
+    assert lib.ckpp_serve_run(None, None, None, None, None, None, C.byref(stats)) == K.CKPP_EINVAL
+    assert lib.ckpp_serve_run_plain(None, None, None, None, None, C.byref(stats)) == K.CKPP_EINVAL
+    st = draw_stream(replace(SMALL, duration_s=0.002))
+    pl = TurnPlanner(st, SMALL, 64)
+    pools = np.zeros(SMALL.n_tables, np.uint64)
+    done = np.zeros(st.arrival.shape[0])
+    # fewer tables than the stream names, and no job buffers
+    buf = K.ckpp_serve_buffers(pools.ctypes.data, pools.ctypes.data, pools.ctypes.data, 1, 64)
+    handles = (C.c_void_p * SMALL.n_tables)(*([1] * SMALL.n_tables))
+    assert lib.ckpp_serve_run_plain(pl._h, handles, C.byref(buf), None, done.ctypes.data,
+                                    C.byref(stats)) == K.CKPP_EINVAL
+    assert lib.ckpp_serve_run(pl._h, C.c_void_p(1), C.byref(buf), None, None, done.ctypes.data,
+                              C.byref(stats)) == K.CKPP_EINVAL
