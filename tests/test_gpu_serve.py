@@ -9,12 +9,14 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_alone_results():
+@pytest.mark.parametrize("max_inflight", [1, 0, 3])
+def test_served_results_equal_alone_results(max_inflight):
     from paper_1712_09624_gb300.serve import ServeConfig, Service
-    # 8 tables of 64K slots at LF 0.6; ~60K new flows arrive (10% of 0.6 M keys offered), well within capacity
+    # 8 tables of 64K slots at LF 0.6; ~60K new flows arrive (10% of 0.6 M keys offered), well within capacity;
+    # the pacing of the loop (turns queued on the device) changes the turns, never the results
     cfg = ServeConfig(n_tables=8, total_slots=1 << 19, warm_lf=0.6, ports=4, min_burst=32, max_burst=512,
                       offered_lookups_per_s=20e6, insert_fraction=0.1, neg_rate=0.2, duration_s=0.03,
-                      footprint_bytes=1 << 20, seed=11)
+                      footprint_bytes=1 << 20, seed=11, max_inflight=max_inflight)
     mixed = Service(cfg)
     alone = Service(cfg)
     rm = mixed.run("batched")
