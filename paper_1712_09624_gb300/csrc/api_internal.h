@@ -34,12 +34,14 @@ inline bool geometry_ok(const ckpp_geometry* g) {
 inline size_t table_bytes(const ckpp_geometry* g) { return kHeaderBytes + (size_t)g->n_buckets * kBucketBytes; }
 
 // Workspace of an n-key batch: counters | set[2m] (first and last index per
-// position, interleaved) | slot_of[n] | pending[n] | retry[n] | claim[n]
-// (8 bytes each) | fixup[fix_cap] (8 bytes each), each part 256-byte aligned.
+// position, interleaved) | slot_of[n] | dup[n] (bytes) | pending[n] | retry[n]
+// | claim[n] (8 bytes each) | fixup[fix_cap] (8 bytes each), each part
+// 256-byte aligned.
 struct WsLayout {
   uint64_t m = 0;
   uint32_t fix_cap = 0;
-  size_t off_set = 0, off_slot = 0, off_pending = 0, off_retry = 0, off_claim = 0, off_fixup = 0, total = 0;
+  size_t off_set = 0, off_slot = 0, off_dup = 0, off_pending = 0, off_retry = 0, off_claim = 0, off_fixup = 0,
+         total = 0;
 };
 
 constexpr WsLayout ws_layout(uint64_t n) {
@@ -53,6 +55,8 @@ constexpr WsLayout ws_layout(uint64_t n) {
   off = align_up(off + 8 * m, kAlign);
   L.off_slot = off;
   off = align_up(off + 4 * n, kAlign);
+  L.off_dup = off;
+  off = align_up(off + n, kAlign);
   L.off_pending = off;
   off = align_up(off + 4 * n, kAlign);
   L.off_retry = off;
@@ -72,6 +76,7 @@ inline int prepare_workspace(uint64_t n, void* workspace, size_t bytes, cudaStre
   ws.counters = reinterpret_cast<uint32_t*>(w);
   ws.set = reinterpret_cast<uint32_t*>(w + L.off_set);
   ws.slot_of = reinterpret_cast<uint32_t*>(w + L.off_slot);
+  ws.dup = w + L.off_dup;
   ws.pending = reinterpret_cast<uint32_t*>(w + L.off_pending);
   ws.retry = reinterpret_cast<uint32_t*>(w + L.off_retry);
   ws.claim = reinterpret_cast<unsigned long long*>(w + L.off_claim);

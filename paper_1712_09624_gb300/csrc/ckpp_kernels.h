@@ -40,8 +40,8 @@ struct Workspace {
   uint32_t* set;        // [2m] open-addressing set of batch keys; position p holds two words side by
                         // side (one line for both): the lowest batch index of the key (kEmpty when
                         // free) and the highest
-  uint32_t* slot_of;    // [n] set position of each batch key, | kDupBit when its key group has other
-                        // members (cleared to 0 with the set)
+  uint32_t* slot_of;    // [n] set position of each batch key
+  uint8_t* dup;         // [n] 1 when the key's group has other members (cleared to 0 with the set)
   uint32_t* pending;    // [n] leaders left for the displacement pass
   uint32_t* retry;      // [n] leaders a displacement pass passes on to the next
   unsigned long long* claim;  // [n] per key: (bucket << 32) | the ctrl bits its publication flips, or 0

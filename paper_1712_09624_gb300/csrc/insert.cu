@@ -44,8 +44,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPathAttempts = 16;
-// Flag in slot_of: the key's group has other members (set positions stay below 2^31).
-constexpr uint32_t kDupBit = 1u << 31;
 
 __device__ __forceinline__ Key load_key(const uint8_t* keys, uint64_t i) {
   uint64_t a, b;
@@ -64,7 +62,7 @@ __device__ void dedup_one(const uint8_t* __restrict__ keys, const TableSet& ts, 
     const uint32_t cur = atomicCAS(ws.first_at(pos), kEmpty, (uint32_t)i);
     if (cur == kEmpty) {
       atomicMax(ws.last_at(pos), (uint32_t)i);
-      atomicOr(&ws.slot_of[i], pos);  // a later occurrence may have flagged i already
+      ws.slot_of[i] = pos;
       return;
     }
     // A first-index word only ever holds batch indices of one key group, so
@@ -73,10 +71,11 @@ __device__ void dedup_one(const uint8_t* __restrict__ keys, const TableSet& ts, 
     if (o.k0 == k.k0 && o.k1 == k.k1 && ts.id(cur) == tid) {
       atomicMin(ws.first_at(pos), (uint32_t)i);
       atomicMax(ws.last_at(pos), (uint32_t)i);
+      ws.slot_of[i] = pos;
       // both occurrences are flagged: the first to claim the position learns of the
       // group only here (every later occurrence's CAS returns a member of it)
-      atomicOr(&ws.slot_of[i], pos | kDupBit);
-      atomicOr(&ws.slot_of[cur], kDupBit);
+      ws.dup[i] = 1;
+      ws.dup[cur] = 1;
       return;
     }
     pos = (pos + 1) & ws.m_mask;
@@ -94,9 +93,8 @@ __global__ void __launch_bounds__(kThreads) dedup_kernel(const uint8_t* __restri
 // The first and last batch index of key i's group: i itself for a key that
 // occurs once in the batch (no read of the set), else one 8-byte read.
 __device__ __forceinline__ uint2 group_of(const Workspace& ws, uint64_t i) {
-  const uint32_t so = ws.slot_of[i];
-  if (!(so & kDupBit)) return make_uint2((uint32_t)i, (uint32_t)i);
-  return *reinterpret_cast<const uint2*>(ws.first_at(so & ~kDupBit));
+  if (!ws.dup[i]) return make_uint2((uint32_t)i, (uint32_t)i);
+  return *reinterpret_cast<const uint2*>(ws.first_at(ws.slot_of[i]));
 }
 
 __device__ __forceinline__ bool is_leader(const Workspace& ws, uint64_t i, uint32_t& last) {
@@ -815,7 +813,7 @@ __device__ void fixup_finish_range(const TableSet& ts, uint64_t n, uint8_t* __re
   }
   for (uint64_t j = i; j < n; j += stride) {
     if (status[j] != kStFollower) continue;  // a leader: its outcome is final
-    const uint32_t leader = ld32_cg(ws.first_at(ws.slot_of[j] & ~kDupBit));
+    const uint32_t leader = ld32_cg(ws.first_at(ws.slot_of[j]));
     const uint8_t st = status[leader];
     status[j] = (st == kStInserted || st == kStUpdated) ? kStUpdated : st;  // FULL, BUSY, NO_TABLE copy through
   }
@@ -950,13 +948,13 @@ __global__ void __launch_bounds__(kSingleThreads, 2) insert_single_launch(TableS
 // vector holds two positions.
 __global__ void __launch_bounds__(kThreads) workspace_clear(uint32_t* __restrict__ counters, uint32_t counter_words,
                                                             uint4* __restrict__ set, uint64_t n_vec,
-                                                            uint4* __restrict__ slot_of, uint64_t slot_vec) {
+                                                            uint4* __restrict__ dup, uint64_t dup_vec) {
   pdl_release();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (tid < counter_words) counters[tid] = 0u;
   for (uint64_t j = tid; j < n_vec; j += stride) set[j] = make_uint4(kEmpty, 0u, kEmpty, 0u);
-  for (uint64_t j = tid; j < slot_vec; j += stride) slot_of[j] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint64_t j = tid; j < dup_vec; j += stride) dup[j] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 __global__ void __launch_bounds__(kThreads) delete_kernel(TableSet ts, const uint8_t* __restrict__ keys, uint64_t n,
@@ -1027,17 +1025,16 @@ cudaError_t launch_chained(void (*kernel)(Params...), unsigned grid, unsigned bl
 
 cudaError_t launch_workspace_clear(const Workspace& ws, uint32_t counter_words, uint64_t n, cudaStream_t s) {
   // m is a power of two >= 64 and the set is 256-byte aligned: 2m words clear
-  // as m / 2 whole 16-byte vectors; slot_of (256-byte aligned, its part of the
-  // layout rounded up to 256 bytes) clears as ceil(n / 4) vectors
+  // as m / 2 whole 16-byte vectors; dup (256-byte aligned, its part of the
+  // layout rounded up to 256 bytes) clears as ceil(n / 16) vectors
   const uint64_t n_vec = ((uint64_t)ws.m_mask + 1) / 2;
-  const uint64_t slot_vec = (n + 3) / 4;
+  const uint64_t dup_vec = (n + 15) / 16;
   uint64_t want = n_vec > counter_words ? n_vec : counter_words;
-  want = want > slot_vec ? want : slot_vec;
+  want = want > dup_vec ? want : dup_vec;
   const uint64_t blocks = (want + kThreads - 1) / kThreads;
   const uint64_t cap = 16ull * device_sm_count();
   workspace_clear<<<(unsigned)(blocks < cap ? blocks : cap), kThreads, 0, s>>>(
-      ws.counters, counter_words, reinterpret_cast<uint4*>(ws.set), n_vec, reinterpret_cast<uint4*>(ws.slot_of),
-      slot_vec);
+      ws.counters, counter_words, reinterpret_cast<uint4*>(ws.set), n_vec, reinterpret_cast<uint4*>(ws.dup), dup_vec);
   return cudaGetLastError();
 }
 
