@@ -670,30 +670,35 @@ __device__ void move1_range(const TableSet& ts, const uint8_t* __restrict__ keys
 #pragma unroll
       for (uint32_t sl = 0; sl < kSlots; ++sl)
         yy[sl] = other_bucket(Key{k0[sl], k1[sl]}, root, (cr >> (kInsecShift + sl)) & 1u, t.nb, t.seed);
-      uint32_t cy[kSlots];
-      uint64_t e0[kSlots], e1[kSlots];
+      // the buckets the entries can move to, four at a time: most keys find room among the
+      // first four, and each bucket read is a memory request of its own
+      for (uint32_t half = 0; half < kSlots && !found; half += kSlots / 2) {
+        uint32_t cy[kSlots / 2];
+        uint64_t e0[kSlots / 2], e1[kSlots / 2];
 #pragma unroll
-      for (uint32_t sl = 0; sl < kSlots; ++sl) {
-        cy[sl] = ld32_cg(ctrl_ptr(t, yy[sl]));
-        if (t.timers) {
-          ld128_cg(expiry_ptr(t, yy[sl], 0), e0[sl], e1[sl]);
-        } else {
-          e0[sl] = e1[sl] = 0;
+        for (uint32_t q = 0; q < kSlots / 2; ++q) {
+          cy[q] = ld32_cg(ctrl_ptr(t, yy[half + q]));
+          if (t.timers) {
+            ld128_cg(expiry_ptr(t, yy[half + q], 0), e0[q], e1[q]);
+          } else {
+            e0[q] = e1[q] = 0;
+          }
         }
-      }
 #pragma unroll
-      for (uint32_t sl = 0; sl < kSlots; ++sl) {
-        if (found || yy[sl] == a.b1 || yy[sl] == a.b2) continue;  // the roots have no room
-        Snap s;
-        s.e0 = e0[sl];
-        s.e1 = e1[sl];
-        const uint32_t f = free_mask(t, cy[sl], s, now);
-        if (f) {
-          x = root;
-          sx = sl;
-          y = yy[sl];
-          hole = __ffs(f) - 1;
-          found = true;
+        for (uint32_t q = 0; q < kSlots / 2; ++q) {
+          const uint32_t sl = half + q;
+          if (found || yy[sl] == a.b1 || yy[sl] == a.b2) continue;  // the roots have no room
+          Snap s;
+          s.e0 = e0[q];
+          s.e1 = e1[q];
+          const uint32_t f = free_mask(t, cy[q], s, now);
+          if (f) {
+            x = root;
+            sx = sl;
+            y = yy[sl];
+            hole = __ffs(f) - 1;
+            found = true;
+          }
         }
       }
     }
