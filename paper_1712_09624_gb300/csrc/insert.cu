@@ -44,6 +44,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPathAttempts = 16;
+// Buckets the one-move pass reads per round trip when looking for room for a root's entries.
+constexpr uint32_t kMoveGroup = 2;
 
 __device__ __forceinline__ Key load_key(const uint8_t* keys, uint64_t i) {
   uint64_t a, b;
@@ -670,23 +672,23 @@ __device__ void move1_range(const TableSet& ts, const uint8_t* __restrict__ keys
 #pragma unroll
       for (uint32_t sl = 0; sl < kSlots; ++sl)
         yy[sl] = other_bucket(Key{k0[sl], k1[sl]}, root, (cr >> (kInsecShift + sl)) & 1u, t.nb, t.seed);
-      // the buckets the entries can move to, four at a time: most keys find room among the
-      // first four, and each bucket read is a memory request of its own
-      for (uint32_t half = 0; half < kSlots && !found; half += kSlots / 2) {
-        uint32_t cy[kSlots / 2];
-        uint64_t e0[kSlots / 2], e1[kSlots / 2];
+      // the buckets the entries can move to, kMoveGroup at a time: most keys find room among the
+      // first ones, and each bucket read is a memory request of its own
+      for (uint32_t g = 0; g < kSlots && !found; g += kMoveGroup) {
+        uint32_t cy[kMoveGroup];
+        uint64_t e0[kMoveGroup], e1[kMoveGroup];
 #pragma unroll
-        for (uint32_t q = 0; q < kSlots / 2; ++q) {
-          cy[q] = ld32_cg(ctrl_ptr(t, yy[half + q]));
+        for (uint32_t q = 0; q < kMoveGroup; ++q) {
+          cy[q] = ld32_cg(ctrl_ptr(t, yy[g + q]));
           if (t.timers) {
-            ld128_cg(expiry_ptr(t, yy[half + q], 0), e0[q], e1[q]);
+            ld128_cg(expiry_ptr(t, yy[g + q], 0), e0[q], e1[q]);
           } else {
             e0[q] = e1[q] = 0;
           }
         }
 #pragma unroll
-        for (uint32_t q = 0; q < kSlots / 2; ++q) {
-          const uint32_t sl = half + q;
+        for (uint32_t q = 0; q < kMoveGroup; ++q) {
+          const uint32_t sl = g + q;
           if (found || yy[sl] == a.b1 || yy[sl] == a.b2) continue;  // the roots have no room
           Snap s;
           s.e0 = e0[q];
