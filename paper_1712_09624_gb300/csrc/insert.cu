@@ -575,7 +575,8 @@ __device__ int execute_path(const TableView& t, uint32_t tid, const uint32_t (&p
 // hole of its other bucket y, and k takes slot sx. Under the locks of x, y and
 // (when x is k's secondary) k's primary, the path is valid if slot sx is busy
 // and its entry's other bucket, from the key and in_secondary bit read under
-// the locks, is still y, and the hole is still free or dead. The entry's value
+// the locks, is still y, and y still has room: the hole if it is still free or
+// dead, else any slot of y that is free now. The entry's value
 // and expiry are read in the same round trip as its key; its tag and filter
 // bits come from its two hashes. The moves are those of execute_path. 1
 // placed, 0 stale path, -1 lock timeout.
@@ -618,7 +619,15 @@ __device__ int execute_move1(const TableView& t, uint32_t tid, uint32_t x, uint3
   const uint32_t etag = (uint32_t)(h1 & 0xFFFF);
   const uint64_t bits = (1ull << (h2 & 63)) | (1ull << ((h2 >> 6) & 63));
   bool ok = ((cw[ix] >> sx) & 1u) && other == y;
-  const bool end_busy = (cw[iy] >> hole) & 1u;
+  bool end_busy = (cw[iy] >> hole) & 1u;
+  if (end_busy && !(t.timers && !alive16(hexp, now))) {
+    // another key took the hole since the search: any slot of y that is free now will do
+    const uint32_t fr = ~cw[iy] & kBusyMask;
+    if (fr) {
+      hole = __ffs(fr) - 1;
+      end_busy = false;
+    }
+  }
   if (ok && end_busy) ok = t.timers && !alive16(hexp, now);
   if (ok) {
     if (end_busy) evict_entry(t, tid, y, hole, cw[iy], ws);
