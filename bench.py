@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--serve-modes", default="batched,plain", help="served: arms to run")
     p.add_argument("--serve-max-inflight", type=int, default=None,
                    help="served: turns queued on the device at most (0: no limit)")
+    p.add_argument("--serve-one-stream", action="store_true",
+                   help="served: flushes on the lookups' stream (default: on a second stream, beside later turns)")
     p.add_argument("--serve-flush-keys", type=int, default=None,
                    help="served: coalesced inserts go out once this many keys wait (default: the loop's own)")
     p.add_argument("--serve-flush-us", type=float, default=None,
@@ -967,6 +969,8 @@ def run_served(args):
         cfg.insert_flush_s = args.serve_flush_us * 1e-6
     if args.serve_max_inflight is not None:
         cfg.max_inflight = args.serve_max_inflight
+    if args.serve_one_stream:
+        cfg.overlap = False
     out = {}
     for mode in args.serve_modes.split(","):
         svc = Service(cfg)
@@ -983,7 +987,7 @@ def run_served(args):
                        "footprint_budget_bytes": cfg.footprint_bytes, "insert_flush_keys": cfg.insert_flush_keys,
                        "insert_flush_us": round(cfg.insert_flush_s * 1e6, 1),
                        "lookup_hold_us": round(cfg.lookup_hold_s * 1e6, 1), "raw_fraction": cfg.raw_fraction,
-                       "max_inflight_turns": cfg.max_inflight},
+                       "max_inflight_turns": cfg.max_inflight, "overlap": cfg.overlap},
             "batched": b, "plain_per_burst": out.get("plain")}
 
 

@@ -247,8 +247,11 @@ int ckpp_batch_delete(ckpp_batch* batch, const ckpp_key* keys, const uint32_t* t
  * jobs; d_n_jobs: NULL (use max_jobs) or a device uint32 job count, clamped to
  * max_jobs. tuning: NULL for the default (see ckpp_batch_tuning). Launches on
  * one batch must not overlap on the GPU (they share its work counter). The job data is not validated on the host: every job's pointers must
- * be valid device memory. Errors: CKPP_EINVAL (max_jobs above
- * CKPP_BATCH_MAX_JOBS, bad tuning), CKPP_ESTALE (a timers table), CKPP_ECUDA. */
+ * be valid device memory. The launch draws work from counters in the
+ * descriptor, so lookups on one descriptor must not run concurrently (order
+ * them on one stream; use a second descriptor over the same tables for a
+ * second stream). Errors: CKPP_EINVAL (max_jobs above CKPP_BATCH_MAX_JOBS, bad
+ * tuning), CKPP_ESTALE (a timers table), CKPP_ECUDA. */
 int ckpp_batch_lookup(ckpp_batch* batch, const ckpp_lookup_job* d_jobs, uint32_t max_jobs, const uint32_t* d_n_jobs,
                       uint32_t now, const ckpp_batch_tuning* tuning, ckpp_stream_t stream);
 

@@ -34,6 +34,13 @@
  *    turn's admission and forces the flush (the held lookup must not see it).
  *    A lookup beyond max_jobs ends admission too, and forces the flush of any
  *    waiting inserts.
+ *  - overlap (optional): flushes run on a second stream, beside later turns'
+ *    lookups. A turn then launches its free lookups on the first stream and,
+ *    on the second, after waiting for them: the lookups whose table has a
+ *    flush in flight (launched, not yet reported complete: "trailing", so
+ *    they still see every earlier insert of their table), the flush, and the
+ *    lookups held behind it. A trailing lookup runs before the turn's own
+ *    flush, which holds only inserts that arrived after it.
  */
 #ifndef CKPP_SERVE_H
 #define CKPP_SERVE_H
@@ -55,7 +62,8 @@ typedef struct ckpp_plan_config {
   uint64_t insert_flush_keys;  /* ... or this many insert keys wait */
   uint64_t footprint_bytes;    /* staging budget of admitted, uncompleted bursts */
   uint64_t bytes_per_key;      /* staging footprint of one key (keys in, results out) */
-  uint32_t max_jobs;           /* lookup bursts per turn (both lookup launches together), >= 1 */
+  uint32_t max_jobs;           /* lookup bursts per turn (all its lookup launches together), >= 1 */
+  uint32_t overlap;            /* 1: flushes on a second stream (see above); 0: one stream */
 } ckpp_plan_config;
 
 /* The stream, in arrival order (arrival nondecreasing; checked). n bursts:
@@ -85,18 +93,27 @@ typedef struct ckpp_turn {
   int64_t n_after;       /* bursts written to after[] (lookups held behind the flush) */
   int64_t insert_first;  /* insert-pool offset of inserts[0] */
   int64_t insert_keys;   /* keys of inserts[] (a contiguous range of the insert pool) */
-  int64_t nbytes;        /* footprint the turn's bursts release when it completes */
+  int64_t nbytes;        /* footprint the turn's bursts release when it completes (with overlap: its
+                            first-stream part, the free lookups) */
+  int64_t n_trailing;    /* overlap: bursts written to trailing[] (lookups behind a flush in flight) */
+  int64_t nbytes_b;      /* overlap: footprint of the second-stream part (trailing, flush, held) */
 } ckpp_turn;
 
 /* Plans one turn at host time `now`; `outstanding` != 0 when an earlier turn
- * has not completed. lookups/inserts/after receive burst indices (ascending)
- * and must each hold `cap` entries; cap >= n always suffices.
+ * has not completed. lookups/trailing/inserts/after receive burst indices
+ * (ascending) and must each hold `cap` entries (trailing may be NULL without
+ * overlap); cap >= n always suffices.
  * Errors: CKPP_EINVAL (NULL pointer, cap too small for the turn: the planner's
  * state is then unchanged). */
-int ckpp_plan_next(ckpp_planner* p, double now, int outstanding, ckpp_turn* turn, int64_t* lookups, int64_t* inserts,
-                   int64_t* after, int64_t cap);
-/* Reports a launched turn as completed: frees its footprint (turn->nbytes). */
+int ckpp_plan_next(ckpp_planner* p, double now, int outstanding, ckpp_turn* turn, int64_t* lookups,
+                   int64_t* trailing, int64_t* inserts, int64_t* after, int64_t cap);
+/* Reports a launched turn (with overlap: its first-stream part) as completed:
+ * frees its footprint (turn->nbytes). */
 int ckpp_plan_complete(ckpp_planner* p, int64_t nbytes);
+/* Overlap: reports a turn's second-stream part as completed (parts complete
+ * in launch order): frees turn->nbytes_b and, if the part carried a flush
+ * (flushed != 0), ends that flush's flight on its tables. */
+int ckpp_plan_complete_b(ckpp_planner* p, int64_t nbytes_b, int flushed);
 /* The planner's state: insert keys waiting, footprint outstanding, and whether
  * every burst has been admitted and launched. Any output pointer may be NULL. */
 int ckpp_plan_state(const ckpp_planner* p, int64_t* pending_keys, int64_t* flight_bytes, int* finished);
@@ -125,6 +142,11 @@ int ckpp_serve_stage_jobs(const int64_t* bursts, int64_t n_bursts, const uint32_
  * the lookups held behind them. A turn completes when an event recorded after
  * its launches does; its bursts then release their footprint.
  *
+ * With the planner's overlap mode, ckpp_serve_run puts each turn's free lookups
+ * on `stream` and its trailing lookups, flush and held lookups on a second
+ * stream it creates, which waits for the first at each turn; it keeps at most
+ * max_inflight first-stream parts and two second-stream parts queued.
+ *
  * ckpp_serve_run_plain (the comparison arm) launches one ckpp_bulk_lookup or
  * ckpp_bulk_insert per burst on the burst's own table, in arrival order, as
  * bursts arrive, with one event per group of bursts launched together.
@@ -151,11 +173,13 @@ typedef struct ckpp_serve_buffers {
   uint8_t* ins_status;         /* device status per insert key (out) */
   void* ins_workspace;         /* device workspace for the largest insert call */
   size_t ins_workspace_bytes;
-  ckpp_lookup_job* d_jobs;     /* device job array of max_jobs records */
+  ckpp_lookup_job* d_jobs;     /* device job records: max_jobs, or ring_slots x max_jobs with overlap */
   ckpp_lookup_job* h_jobs;     /* pinned host memory: ring_slots x max_jobs records */
   uint32_t ring_slots;         /* >= 1 */
   uint32_t max_inflight;       /* ckpp_serve_run: turns queued on the device at most (0: no limit); at the
                                   limit the loop waits for the oldest, and arrivals gather meanwhile */
+  ckpp_batch* batch_b;         /* overlap: a second descriptor over the same tables, for the second stream's
+                                  lookups (one descriptor's lookup launches must not overlap); else NULL */
 } ckpp_serve_buffers;
 
 typedef struct ckpp_serve_stats {
@@ -166,6 +190,8 @@ typedef struct ckpp_serve_stats {
   uint64_t flushes;       /* insert calls (batched) */
   uint64_t held;          /* lookup bursts launched behind a flush (batched) */
   uint64_t admitted;      /* bursts admitted, summed over turns */
+  double gpu_busy_b_s;    /* overlap: the same for the second-stream parts (gpu_busy_s then counts the first) */
+  uint64_t trailing;      /* overlap: lookup bursts launched behind a flush in flight */
 } ckpp_serve_stats;
 
 int ckpp_serve_run(ckpp_planner* planner, ckpp_batch* batch, const ckpp_serve_buffers* buffers,

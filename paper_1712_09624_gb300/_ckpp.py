@@ -47,14 +47,15 @@ class ckpp_batch_tuning(C.Structure):
 
 class ckpp_plan_config(C.Structure):
     _fields_ = [("insert_flush_s", C.c_double), ("lookup_hold_s", C.c_double), ("insert_flush_keys", C.c_uint64),
-                ("footprint_bytes", C.c_uint64), ("bytes_per_key", C.c_uint64), ("max_jobs", C.c_uint32)]
+                ("footprint_bytes", C.c_uint64), ("bytes_per_key", C.c_uint64), ("max_jobs", C.c_uint32),
+                ("overlap", C.c_uint32)]
 
 
 class ckpp_turn(C.Structure):
     _fields_ = [("action", C.c_int32), ("pad", C.c_int32), ("wake", C.c_double), ("admitted_lo", C.c_int64),
                 ("admitted_hi", C.c_int64), ("n_lookups", C.c_int64), ("n_inserts", C.c_int64),
                 ("n_after", C.c_int64), ("insert_first", C.c_int64), ("insert_keys", C.c_int64),
-                ("nbytes", C.c_int64)]
+                ("nbytes", C.c_int64), ("n_trailing", C.c_int64), ("nbytes_b", C.c_int64)]
 
 
 class ckpp_serve_buffers(C.Structure):
@@ -62,12 +63,14 @@ class ckpp_serve_buffers(C.Structure):
                 ("n_tables", C.c_uint32), ("max_jobs", C.c_uint32), ("ins_keys", C.c_void_p),
                 ("ins_tables", C.c_void_p), ("ins_vals", C.c_void_p), ("ins_status", C.c_void_p),
                 ("ins_workspace", C.c_void_p), ("ins_workspace_bytes", C.c_size_t), ("d_jobs", C.c_void_p),
-                ("h_jobs", C.c_void_p), ("ring_slots", C.c_uint32), ("max_inflight", C.c_uint32)]
+                ("h_jobs", C.c_void_p), ("ring_slots", C.c_uint32), ("max_inflight", C.c_uint32),
+                ("batch_b", C.c_void_p)]
 
 
 class ckpp_serve_stats(C.Structure):
     _fields_ = [("wall_s", C.c_double), ("gpu_busy_s", C.c_double), ("turns", C.c_uint64),
-                ("launches", C.c_uint64), ("flushes", C.c_uint64), ("held", C.c_uint64), ("admitted", C.c_uint64)]
+                ("launches", C.c_uint64), ("flushes", C.c_uint64), ("held", C.c_uint64), ("admitted", C.c_uint64),
+                ("gpu_busy_b_s", C.c_double), ("trailing", C.c_uint64)]
 
 
 LOOKUP_BLOOM, LOOKUP_OPTIMISTIC, LOOKUP_PESSIMISTIC = 0, 1, 2
@@ -119,8 +122,9 @@ def _load():
         # include/ckpp_serve.h (host code)
         "ckpp_plan_create": (C.c_int, [vp, vp, vp, vp, vp, C.c_int64, C.POINTER(ckpp_plan_config), C.POINTER(vp)]),
         "ckpp_plan_destroy": (C.c_int, [vp]),
-        "ckpp_plan_next": (C.c_int, [vp, C.c_double, C.c_int, C.POINTER(ckpp_turn), vp, vp, vp, C.c_int64]),
+        "ckpp_plan_next": (C.c_int, [vp, C.c_double, C.c_int, C.POINTER(ckpp_turn), vp, vp, vp, vp, C.c_int64]),
         "ckpp_plan_complete": (C.c_int, [vp, C.c_int64]),
+        "ckpp_plan_complete_b": (C.c_int, [vp, C.c_int64, C.c_int]),
         "ckpp_plan_state": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
         "ckpp_serve_stage_jobs": (C.c_int, [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp]),
         "ckpp_serve_run": (C.c_int, [vp, vp, C.POINTER(ckpp_serve_buffers), C.POINTER(ckpp_batch_tuning), vp, vp,
@@ -146,7 +150,8 @@ EXPORTED = ("ckpp_required_bytes", "ckpp_workspace_bytes", "ckpp_create", "ckpp_
             "ckpp_batch_delete", "ckpp_shard_workspace_bytes", "ckpp_shard_partition", "ckpp_shard_unpermute",
             "ckpp_set_insert_launch", "ckpp_attach")
 SERVE_EXPORTED = ("ckpp_plan_create", "ckpp_plan_destroy", "ckpp_plan_next", "ckpp_plan_complete",
-                  "ckpp_plan_state", "ckpp_serve_stage_jobs", "ckpp_serve_run", "ckpp_serve_run_plain")
+                  "ckpp_plan_complete_b", "ckpp_plan_state", "ckpp_serve_stage_jobs", "ckpp_serve_run",
+                  "ckpp_serve_run_plain")
 INSERT_LAUNCH_CHAIN, INSERT_LAUNCH_SINGLE = 0, 1
 NOALLOC_MAX_KEYS = 65536
 MAX_SHARDS = 64

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <deque>
 #include <vector>
 
 #include "../../include/ckpp.h"
@@ -31,6 +32,9 @@ struct ckpp_planner {
   std::vector<uint8_t> pend_mask;  // per table: an insert waits
   std::vector<uint8_t> held_mask;  // per table: a lookup is held
   std::vector<int64_t> lookups;    // scratch: this turn's free lookups
+  std::vector<int64_t> trailing;   // scratch (overlap): this turn's lookups behind a flush in flight
+  std::vector<uint32_t> flight_cnt;              // overlap, per table: flushes in flight holding its inserts
+  std::deque<std::vector<uint32_t>> flushes;     // overlap: the tables of each flush in flight, in launch order
   int64_t flight_bytes = 0;        // footprint admitted and not yet completed
 
   int64_t foot(int64_t b) const { return int64_t(size[b]) * int64_t(cfg.bytes_per_key); }

@@ -18,7 +18,8 @@ extern "C" int ckpp_plan_create(const double* arrival, const uint32_t* table, co
                                 const uint8_t* insert, const int64_t* offset, int64_t n, const ckpp_plan_config* cfg,
                                 ckpp_planner** out) {
   if (!out || !cfg || n < 0 || (n > 0 && (!arrival || !table || !size || !insert || !offset))) return CKPP_EINVAL;
-  if (cfg->max_jobs < 1 || cfg->bytes_per_key < 1 || !(cfg->insert_flush_s >= 0) || !(cfg->lookup_hold_s >= 0))
+  if (cfg->max_jobs < 1 || cfg->bytes_per_key < 1 || !(cfg->insert_flush_s >= 0) || !(cfg->lookup_hold_s >= 0) ||
+      cfg->overlap > 1)
     return CKPP_EINVAL;
   uint32_t n_tables = 1;
   for (int64_t b = 0; b < n; ++b) {
@@ -38,6 +39,7 @@ extern "C" int ckpp_plan_create(const double* arrival, const uint32_t* table, co
   try {
     p->pend_mask.assign(n_tables, 0);
     p->held_mask.assign(n_tables, 0);
+    p->flight_cnt.assign(n_tables, 0);
   } catch (...) {
     delete p;
     return CKPP_EINVAL;
@@ -52,8 +54,8 @@ extern "C" int ckpp_plan_destroy(ckpp_planner* p) {
 }
 
 extern "C" int ckpp_plan_next(ckpp_planner* p, double now, int outstanding, ckpp_turn* turn, int64_t* lookups,
-                              int64_t* inserts, int64_t* after, int64_t cap) {
-  if (!p || !turn || !lookups || !inserts || !after || cap < 0) return CKPP_EINVAL;
+                              int64_t* trailing, int64_t* inserts, int64_t* after, int64_t cap) {
+  if (!p || !turn || !lookups || !inserts || !after || cap < 0 || (p->cfg.overlap && !trailing)) return CKPP_EINVAL;
   std::memset(turn, 0, sizeof(*turn));
   const int64_t n = p->n;
   const bool arrived = p->nxt < n && p->arrival[p->nxt] <= now;
@@ -69,6 +71,7 @@ extern "C" int ckpp_plan_next(ckpp_planner* p, double now, int outstanding, ckpp
   const int64_t hi = arrived ? std::upper_bound(p->arrival + lo, p->arrival + n, now) - p->arrival : lo;
   if (int64_t(p->pending.size() + p->held.size()) + (hi - lo) > cap) return CKPP_EINVAL;
   p->lookups.clear();
+  p->trailing.clear();
   int64_t stop = lo;
   if (arrived) {
     const int64_t room = int64_t(p->cfg.footprint_bytes) - p->flight_bytes;
@@ -96,13 +99,15 @@ extern "C" int ckpp_plan_next(ckpp_planner* p, double now, int outstanding, ckpp
         p->pending_keys += p->size[b];
         p->pend_mask[t] = 1;
       } else {
-        if (p->lookups.size() + p->held.size() >= p->cfg.max_jobs) {
+        if (p->lookups.size() + p->trailing.size() + p->held.size() >= p->cfg.max_jobs) {
           flush = true;  // the job array is full (flushes only if inserts wait)
           break;
         }
         if (p->pend_mask[t]) {
           p->held.push_back(b);
           p->held_mask[t] = 1;
+        } else if (p->flight_cnt[t]) {
+          p->trailing.push_back(b);  // behind the flush in flight on the second stream
         } else {
           p->lookups.push_back(b);
         }
@@ -115,39 +120,66 @@ extern "C" int ckpp_plan_next(ckpp_planner* p, double now, int outstanding, ckpp
   turn->admitted_lo = lo;
   turn->admitted_hi = stop;
   flush = !p->pending.empty() && (flush || p->flush_due(now));
-  if (p->lookups.empty() && !flush) {
+  if (p->lookups.empty() && p->trailing.empty() && !flush) {
     turn->action = CKPP_PLAN_NONE;
     return CKPP_OK;
   }
   turn->action = CKPP_PLAN_LAUNCH;
-  int64_t nbytes = 0;
+  int64_t nbytes = 0, nbytes_b = 0;
   turn->n_lookups = int64_t(p->lookups.size());
   for (size_t i = 0; i < p->lookups.size(); ++i) {
     lookups[i] = p->lookups[i];
     nbytes += p->foot(p->lookups[i]);
   }
+  turn->n_trailing = int64_t(p->trailing.size());
+  for (size_t i = 0; i < p->trailing.size(); ++i) {
+    trailing[i] = p->trailing[i];
+    nbytes_b += p->foot(p->trailing[i]);
+  }
   if (flush) {
     turn->n_inserts = int64_t(p->pending.size());
     turn->insert_first = p->offset[p->pending.front()];
     turn->insert_keys = p->pending_keys;
+    std::vector<uint32_t> tables;  // overlap: the flush's tables, each once
     for (size_t i = 0; i < p->pending.size(); ++i) {
       const int64_t b = p->pending[i];
       inserts[i] = b;
-      nbytes += p->foot(b);
+      nbytes_b += p->foot(b);
+      if (p->cfg.overlap && p->pend_mask[p->table[b]]) {
+        tables.push_back(p->table[b]);
+        ++p->flight_cnt[p->table[b]];
+      }
       p->pend_mask[p->table[b]] = 0;
     }
+    if (p->cfg.overlap) p->flushes.push_back(std::move(tables));
     turn->n_after = int64_t(p->held.size());
     for (size_t i = 0; i < p->held.size(); ++i) {
       const int64_t b = p->held[i];
       after[i] = b;
-      nbytes += p->foot(b);
+      nbytes_b += p->foot(b);
       p->held_mask[p->table[b]] = 0;
     }
     p->pending.clear();
     p->pending_keys = 0;
     p->held.clear();
   }
-  turn->nbytes = nbytes;
+  if (p->cfg.overlap) {
+    turn->nbytes = nbytes;
+    turn->nbytes_b = nbytes_b;
+  } else {
+    turn->nbytes = nbytes + nbytes_b;
+  }
+  return CKPP_OK;
+}
+
+extern "C" int ckpp_plan_complete_b(ckpp_planner* p, int64_t nbytes_b, int flushed) {
+  if (!p || !p->cfg.overlap || nbytes_b < 0 || nbytes_b > p->flight_bytes || (flushed && p->flushes.empty()))
+    return CKPP_EINVAL;
+  p->flight_bytes -= nbytes_b;
+  if (flushed) {
+    for (uint32_t t : p->flushes.front()) --p->flight_cnt[t];
+    p->flushes.pop_front();
+  }
   return CKPP_OK;
 }
 

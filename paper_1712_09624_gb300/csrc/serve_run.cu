@@ -74,6 +74,11 @@ bool buffers_ok(const ckpp_serve_buffers* b, const ckpp_planner* p) {
 
 }  // namespace
 
+namespace {
+int serve_run_overlap(ckpp_planner* p, ckpp_batch* batch, const ckpp_serve_buffers* buf,
+                      const ckpp_batch_tuning* tuning, cudaStream_t s, double* done_at, ckpp_serve_stats* stats);
+}  // namespace
+
 extern "C" int ckpp_serve_run(ckpp_planner* p, ckpp_batch* batch, const ckpp_serve_buffers* buf,
                               const ckpp_batch_tuning* tuning, ckpp_stream_t stream, double* done_at,
                               ckpp_serve_stats* stats) {
@@ -82,6 +87,10 @@ extern "C" int ckpp_serve_run(ckpp_planner* p, ckpp_batch* batch, const ckpp_ser
   if (n > 0 && (!buf->ins_keys || !buf->ins_tables || !buf->ins_vals || !buf->ins_status)) {
     for (int64_t b = 0; b < n; ++b)
       if (p->insert[b]) return CKPP_EINVAL;
+  }
+  if (p->cfg.overlap) {
+    if (!buf->batch_b || buf->batch_b == batch) return CKPP_EINVAL;
+    return serve_run_overlap(p, batch, buf, tuning, reinterpret_cast<cudaStream_t>(stream), done_at, stats);
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   *stats = ckpp_serve_stats{};
@@ -131,8 +140,8 @@ extern "C" int ckpp_serve_run(ckpp_planner* p, ckpp_batch* batch, const ckpp_ser
     }
     const double now = seconds_since(t0);
     ckpp_turn turn;
-    if ((rc = ckpp_plan_next(p, now, flight.empty() ? 0 : 1, &turn, lookups.data(), inserts.data(), after.data(),
-                             n)) != CKPP_OK)
+    if ((rc = ckpp_plan_next(p, now, flight.empty() ? 0 : 1, &turn, lookups.data(), nullptr, inserts.data(),
+                             after.data(), n)) != CKPP_OK)
       break;
     if (turn.action == CKPP_PLAN_IDLE) {
       if (flight.empty()) {
@@ -313,3 +322,216 @@ extern "C" int ckpp_serve_run_plain(const ckpp_planner* p, ckpp_table* const* ta
   cudaEventDestroy(e0);
   return rc;
 }
+
+namespace {
+
+// One stream's part of a turn, in flight.
+struct Part {
+  cudaEvent_t start, end;
+  std::vector<int64_t> bursts;
+  int64_t nbytes;
+  bool flushed;   // second-stream part carrying a flush
+  int ring_slot;
+};
+
+// Continuous batching with the flushes on a second stream (the planner's
+// overlap mode): a turn's free lookups go to the caller's stream; its trailing
+// lookups, flush and held lookups to the second stream, after an event wait on
+// the first (so a flush follows every lookup launched before it). The second
+// stream's lookups use their own batch descriptor (buf->batch_b): a
+// descriptor's work counters serve one launch at a time. Each turn
+// stages its jobs in its own ring slot of host and device job records
+// (ring_slots x max_jobs each), reused only after both parts that read it ran.
+int serve_run_overlap(ckpp_planner* p, ckpp_batch* batch, const ckpp_serve_buffers* buf,
+                      const ckpp_batch_tuning* tuning, cudaStream_t s, double* done_at, ckpp_serve_stats* stats) {
+  const int64_t n = p->n;
+  *stats = ckpp_serve_stats{};
+  std::vector<int64_t> lookups(n > 0 ? n : 1), trailing(n > 0 ? n : 1), inserts(n > 0 ? n : 1),
+      after(n > 0 ? n : 1), jobs_idx;
+  std::vector<cudaEvent_t> ring_a(buf->ring_slots, nullptr), ring_b(buf->ring_slots, nullptr);
+  std::deque<Part> flight_a, flight_b;
+  EventPool events;
+  cudaStream_t sb;
+  if (cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) != cudaSuccess) return CKPP_ECUDA;
+  cudaEvent_t e0;
+  if (cudaEventCreate(&e0) != cudaSuccess) {
+    cudaStreamDestroy(sb);
+    return CKPP_ECUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaStreamDestroy(sb);
+    return CKPP_ECUDA;
+  }
+  const Clock::time_point t0 = Clock::now();
+  int rc = cudaEventRecord(e0, s) == cudaSuccess ? CKPP_OK : CKPP_ECUDA;
+  uint32_t slot = 0;
+  double last_done = 0.0;
+  const ckpp_stream_t ha = reinterpret_cast<ckpp_stream_t>(s), hb = reinterpret_cast<ckpp_stream_t>(sb);
+  // retire the completed parts of one stream (block: wait for its oldest part first)
+  auto retire = [&](std::deque<Part>& q, std::vector<cudaEvent_t>& ring, bool second, bool block) -> int {
+    while (!q.empty()) {
+      Part& f = q.front();
+      const cudaError_t st = block ? cudaEventSynchronize(f.end) : cudaEventQuery(f.end);
+      if (st == cudaErrorNotReady) return CKPP_OK;
+      if (st != cudaSuccess) return CKPP_ECUDA;
+      double t_end = 0, busy = 0;
+      if (event_seconds(e0, f.end, t_end) != cudaSuccess || event_seconds(f.start, f.end, busy) != cudaSuccess)
+        return CKPP_ECUDA;
+      for (int64_t b : f.bursts) done_at[b] = t_end;
+      last_done = t_end > last_done ? t_end : last_done;
+      if (second) {
+        stats->gpu_busy_b_s += busy;
+        if (ckpp_plan_complete_b(p, f.nbytes, f.flushed ? 1 : 0) != CKPP_OK) return CKPP_EINVAL;
+      } else {
+        stats->gpu_busy_s += busy;
+        if (ckpp_plan_complete(p, f.nbytes) != CKPP_OK) return CKPP_EINVAL;
+      }
+      if (f.ring_slot >= 0 && ring[f.ring_slot] == f.end) ring[f.ring_slot] = nullptr;
+      events.put(f.start);
+      events.put(f.end);
+      q.pop_front();
+      block = false;
+    }
+    return CKPP_OK;
+  };
+  while (rc == CKPP_OK) {
+    int fin = 0;
+    ckpp_plan_state(p, nullptr, nullptr, &fin);
+    if (fin && flight_a.empty() && flight_b.empty()) break;
+    if ((rc = retire(flight_a, ring_a, false, false)) != CKPP_OK) break;
+    if ((rc = retire(flight_b, ring_b, true, false)) != CKPP_OK) break;
+    // pace the first stream as the one-stream loop does, and keep at most two parts on the second
+    if (buf->max_inflight && flight_a.size() >= buf->max_inflight) {
+      rc = retire(flight_a, ring_a, false, true);
+      continue;
+    }
+    if (flight_b.size() >= 2) {
+      rc = retire(flight_b, ring_b, true, true);
+      continue;
+    }
+    const double now = seconds_since(t0);
+    ckpp_turn turn;
+    const int outstanding = (flight_a.empty() && flight_b.empty()) ? 0 : 1;
+    if ((rc = ckpp_plan_next(p, now, outstanding, &turn, lookups.data(), trailing.data(), inserts.data(),
+                             after.data(), n)) != CKPP_OK)
+      break;
+    if (turn.action == CKPP_PLAN_IDLE) {
+      if (!outstanding) {
+        const double wait = turn.wake - now;
+        if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait < 50e-6 ? wait : 50e-6));
+      }
+      continue;
+    }
+    if (turn.action == CKPP_PLAN_BLOCK) {  // wait for the older of the two streams' oldest parts
+      if (!flight_a.empty()) {
+        rc = retire(flight_a, ring_a, false, true);
+      } else {
+        rc = retire(flight_b, ring_b, true, true);
+      }
+      continue;
+    }
+    if (turn.action == CKPP_PLAN_NONE) continue;
+    const int64_t nj = turn.n_lookups + turn.n_trailing + turn.n_after;
+    const bool has_b = turn.n_trailing || turn.n_inserts || turn.n_after;
+    ckpp_lookup_job* d = buf->d_jobs + (size_t)slot * buf->max_jobs;
+    int used_slot = -1;
+    if (nj) {
+      for (cudaEvent_t e : {ring_a[slot], ring_b[slot]})
+        if (e && cudaEventSynchronize(e) != cudaSuccess) rc = CKPP_ECUDA;
+      if (rc != CKPP_OK) break;
+      jobs_idx.assign(lookups.begin(), lookups.begin() + turn.n_lookups);
+      jobs_idx.insert(jobs_idx.end(), trailing.begin(), trailing.begin() + turn.n_trailing);
+      jobs_idx.insert(jobs_idx.end(), after.begin(), after.begin() + turn.n_after);
+      ckpp_lookup_job* h = buf->h_jobs + (size_t)slot * buf->max_jobs;
+      ckpp_serve_stage_jobs(jobs_idx.data(), nj, p->table, p->offset, p->size, buf->pool_keys, buf->pool_vals,
+                            buf->pool_found, h);
+      if (cudaMemcpyAsync(d, h, (size_t)nj * sizeof(ckpp_lookup_job), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        rc = CKPP_ECUDA;
+        break;
+      }
+      used_slot = (int)slot;
+    }
+    Part a;
+    if (events.get(a.start) != cudaSuccess || events.get(a.end) != cudaSuccess ||
+        cudaEventRecord(a.start, s) != cudaSuccess) {
+      rc = CKPP_ECUDA;
+      break;
+    }
+    if (turn.n_lookups) {  // free lookups on the first stream
+      if ((rc = ckpp_batch_lookup(batch, d, (uint32_t)turn.n_lookups, nullptr, 0, tuning, ha))) break;
+      ++stats->launches;
+    }
+    if (cudaEventRecord(a.end, s) != cudaSuccess) {
+      rc = CKPP_ECUDA;
+      break;
+    }
+    if (has_b) {
+      Part b;
+      if (cudaStreamWaitEvent(sb, a.end, 0) != cudaSuccess || events.get(b.start) != cudaSuccess ||
+          events.get(b.end) != cudaSuccess || cudaEventRecord(b.start, sb) != cudaSuccess) {
+        rc = CKPP_ECUDA;
+        break;
+      }
+      if (turn.n_trailing) {  // behind the flushes in flight
+        if ((rc = ckpp_batch_lookup(buf->batch_b, d + turn.n_lookups, (uint32_t)turn.n_trailing, nullptr, 0, tuning,
+                                    hb)))
+          break;
+        ++stats->launches;
+        stats->trailing += (uint64_t)turn.n_trailing;
+      }
+      if (turn.n_inserts) {
+        const int64_t first = turn.insert_first;
+        if ((rc = ckpp_batch_insert(batch, buf->ins_keys + first, buf->ins_tables + first, buf->ins_vals + first,
+                                    (uint64_t)turn.insert_keys, 0, 0, buf->ins_status + first, buf->ins_workspace,
+                                    buf->ins_workspace_bytes, hb)))
+          break;
+        ++stats->launches;
+        ++stats->flushes;
+      }
+      if (turn.n_after) {
+        if ((rc = ckpp_batch_lookup(buf->batch_b, d + turn.n_lookups + turn.n_trailing, (uint32_t)turn.n_after,
+                                    nullptr, 0, tuning, hb)))
+          break;
+        ++stats->launches;
+        stats->held += (uint64_t)turn.n_after;
+      }
+      if (cudaEventRecord(b.end, sb) != cudaSuccess) {
+        rc = CKPP_ECUDA;
+        break;
+      }
+      b.bursts.insert(b.bursts.end(), trailing.begin(), trailing.begin() + turn.n_trailing);
+      b.bursts.insert(b.bursts.end(), inserts.begin(), inserts.begin() + turn.n_inserts);
+      b.bursts.insert(b.bursts.end(), after.begin(), after.begin() + turn.n_after);
+      b.nbytes = turn.nbytes_b;
+      b.flushed = turn.n_inserts > 0;
+      b.ring_slot = used_slot;
+      if (used_slot >= 0) ring_b[used_slot] = b.end;
+      flight_b.push_back(std::move(b));
+    }
+    a.bursts.assign(lookups.begin(), lookups.begin() + turn.n_lookups);
+    a.nbytes = turn.nbytes;
+    a.flushed = false;
+    a.ring_slot = used_slot;
+    if (used_slot >= 0) {
+      ring_a[used_slot] = a.end;
+      slot = (slot + 1) % buf->ring_slots;
+    }
+    flight_a.push_back(std::move(a));
+    ++stats->turns;
+    stats->admitted += (uint64_t)(turn.admitted_hi - turn.admitted_lo);
+  }
+  if (rc != CKPP_OK) {
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(sb);
+  } else {
+    rc = retire(flight_a, ring_a, false, true);
+    if (rc == CKPP_OK) rc = retire(flight_b, ring_b, true, true);
+  }
+  stats->wall_s = last_done;
+  cudaEventDestroy(e0);
+  cudaStreamDestroy(sb);
+  return rc;
+}
+
+}  // namespace

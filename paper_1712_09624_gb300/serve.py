@@ -97,6 +97,8 @@ class Service:
         self.ins_status = torch.zeros(n_ins, dtype=torch.uint8, device=dev)
         self.ins_ws = torch.empty(K.ckpp_workspace_bytes(max(1, n_ins)), dtype=torch.uint8, device=dev)
         self.batch = BatchedLookup(self.tables, max_jobs=K.BATCH_MAX_JOBS, device=dev)
+        # a second descriptor for the second stream's lookups (overlap): a descriptor's launches must not overlap
+        self.batch_b = BatchedLookup(self.tables, max_jobs=1, device=dev) if cfg.overlap else None
         torch.cuda.synchronize(dev)
 
     def reset_outputs(self):
@@ -120,11 +122,14 @@ class Service:
         ring_slots = 8
         h_jobs = torch.zeros(ring_slots * K.BATCH_MAX_JOBS * K.JOB_BYTES, dtype=torch.uint8).pin_memory()
         pools = [np.array([p[name].data_ptr() for p in self.pools], np.uint64) for name in ("keys", "vals", "found")]
+        # with overlap every turn reads its own ring slot of device job records
+        d_jobs = (torch.empty(ring_slots * K.BATCH_MAX_JOBS * K.JOB_BYTES, dtype=torch.uint8, device=dev)
+                  if cfg.overlap else self.batch.jobs)
         buf = K.ckpp_serve_buffers(
             pools[0].ctypes.data, pools[1].ctypes.data, pools[2].ctypes.data, cfg.n_tables, K.BATCH_MAX_JOBS,
             self.ins_keys.data_ptr(), self.ins_tables.data_ptr(), self.ins_vals.data_ptr(),
-            self.ins_status.data_ptr(), self.ins_ws.data_ptr(), self.ins_ws.numel(), self.batch.jobs.data_ptr(),
-            h_jobs.data_ptr(), ring_slots, cfg.max_inflight)
+            self.ins_status.data_ptr(), self.ins_ws.data_ptr(), self.ins_ws.numel(), d_jobs.data_ptr(),
+            h_jobs.data_ptr(), ring_slots, cfg.max_inflight, self.batch_b.handle if self.batch_b else None)
         done_at = np.full(n_bursts, np.nan)
         stats = K.ckpp_serve_stats()
         lib = K.library()
@@ -141,7 +146,7 @@ class Service:
                                           C.byref(stats))
             K._check(rc, "ckpp_serve_run_plain")
         torch.cuda.synchronize(dev)
-        del pools, h_jobs
+        del pools, h_jobs, d_jobs
         if np.isnan(done_at).any():
             raise RuntimeError(f"{int(np.isnan(done_at).sum())} bursts were never completed")
         wall = stats.wall_s
@@ -164,6 +169,10 @@ class Service:
             "insert_latency_us": percentiles(lat[keep & st.insert]),
             "insert_flushes": int(stats.flushes) if mode == "batched" else None,
             "held_lookup_bursts": int(stats.held) if mode == "batched" else None,
+            "overlap": bool(cfg.overlap) if mode == "batched" else None,
+            "trailing_lookup_bursts": int(stats.trailing) if mode == "batched" and cfg.overlap else None,
+            "gpu_busy_second_stream_fraction": (round(stats.gpu_busy_b_s / wall, 3)
+                                                if mode == "batched" and cfg.overlap and wall else None),
             "read_after_write_keys": int(st.raw_pos.shape[0]),
         }
 

@@ -33,6 +33,9 @@ Turn planner, called whenever the loop is free to launch:
   waiting (held until that flush). An insert that arrives for a table with a
   held lookup ends the turn's admission and forces the flush, so that the held
   lookup cannot see it; it starts the next group of waiting inserts.
+* overlap (the default): flushes run on a second stream, beside later turns'
+  lookups; a lookup whose table has a flush in flight trails it on that
+  stream (include/ckpp_serve.h).
 """
 
 from __future__ import annotations
@@ -62,6 +65,7 @@ class ServeConfig:
     lookup_hold_s: float = 100e-6     # ... or a lookup held behind them has waited this long
     raw_fraction: float = 0.2         # share of lookup keys naming flows inserted earlier in the run
     max_inflight: int = 1             # turns queued on the device at most (0: no limit)
+    overlap: bool = True              # flushes on a second stream, beside later turns' lookups
     seed: int = 7
 
 
@@ -147,19 +151,28 @@ def draw_read_after_write(cfg: ServeConfig, rng, table, size, insert, offset):
 @dataclass
 class Turn:
     """What one turn launches, in this order: ``lookups``, then the flush of
-    ``inserts``, then ``lookups_after``."""
+    ``inserts``, then ``lookups_after``. With overlap, ``lookups`` go to the
+    first stream and the rest to the second, after ``trailing`` (lookups
+    behind a flush in flight)."""
     admitted: slice                 # bursts admitted this turn (arrival order)
-    lookups: np.ndarray             # lookup bursts whose table has no waiting insert
+    lookups: np.ndarray             # lookup bursts whose table has no waiting insert (nor flush in flight)
     inserts: list = field(default_factory=list)  # insert bursts to launch now, in arrival order
     insert_first: int = 0           # insert-pool offset of inserts[0]
     insert_keys: int = 0            # keys in inserts (a contiguous range of the insert pool)
     lookups_after: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))  # held behind inserts
     nbytes: int = 0                 # staging footprint the turn's bursts release when it completes
+    trailing: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))  # overlap: behind a flush in flight
+    nbytes_b: int = 0               # overlap: footprint of the second-stream part
 
     @property
     def done(self) -> np.ndarray:
         """The bursts that complete with this turn."""
-        return np.concatenate([self.lookups, np.asarray(self.inserts, np.int64), self.lookups_after])
+        return np.concatenate([self.lookups, self.trailing, np.asarray(self.inserts, np.int64), self.lookups_after])
+
+    @property
+    def part_b(self) -> np.ndarray:
+        """Overlap: the bursts of the second-stream part."""
+        return np.concatenate([self.trailing, np.asarray(self.inserts, np.int64), self.lookups_after])
 
 
 class TurnPlanner:
@@ -186,12 +199,12 @@ class TurnPlanner:
                         np.ascontiguousarray(stream.insert, np.uint8),
                         np.ascontiguousarray(stream.offset, np.int64))
         conf = K.ckpp_plan_config(cfg.insert_flush_s, cfg.lookup_hold_s, cfg.insert_flush_keys,
-                                  cfg.footprint_bytes, KEY_BYTES_IO, max_jobs)
+                                  cfg.footprint_bytes, KEY_BYTES_IO, max_jobs, 1 if cfg.overlap else 0)
         self._h = C.c_void_p()
         K._check(self.lib.ckpp_plan_create(*(a.ctypes.data for a in self._arrays), n, C.byref(conf),
                                            C.byref(self._h)), "ckpp_plan_create")
-        self._out = np.empty((3, max(n, 1)), np.int64)
-        self._ptrs = tuple(int(self._out[i].ctypes.data) for i in range(3))
+        self._out = np.empty((4, max(n, 1)), np.int64)
+        self._ptrs = tuple(int(self._out[i].ctypes.data) for i in range(4))
         self._turn = K.ckpp_turn()
         self._turn_ref = C.byref(self._turn)
 
@@ -236,9 +249,16 @@ class TurnPlanner:
             return "none", None, 0.0
         out = self._out
         turn = Turn(admitted=slice(t.admitted_lo, t.admitted_hi), lookups=out[0, :t.n_lookups].copy(),
-                    inserts=out[1, :t.n_inserts].tolist(), insert_first=t.insert_first, insert_keys=t.insert_keys,
-                    lookups_after=out[2, :t.n_after].copy(), nbytes=t.nbytes)
+                    trailing=out[1, :t.n_trailing].copy(), inserts=out[2, :t.n_inserts].tolist(),
+                    insert_first=t.insert_first, insert_keys=t.insert_keys,
+                    lookups_after=out[3, :t.n_after].copy(), nbytes=t.nbytes, nbytes_b=t.nbytes_b)
         return "launch", turn, 0.0
 
     def complete(self, turn: Turn):
+        """The turn (with overlap: its first-stream part) completed."""
         self.K._check(self.lib.ckpp_plan_complete(self._h, turn.nbytes), "ckpp_plan_complete")
+
+    def complete_b(self, turn: Turn):
+        """Overlap: the turn's second-stream part completed."""
+        self.K._check(self.lib.ckpp_plan_complete_b(self._h, turn.nbytes_b, 1 if turn.inserts else 0),
+                      "ckpp_plan_complete_b")

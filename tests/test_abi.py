@@ -43,7 +43,7 @@ def test_serve_runtime_exports(K):
     text = open(os.path.join(ROOT, "include", "ckpp_serve.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = sorted(set(re.findall(r"\b(ckpp_[a-z_0-9]+)\s*\(", text)))
-    assert set(K.SERVE_EXPORTED) == set(names) and len(names) == 8
+    assert set(K.SERVE_EXPORTED) == set(names) and len(names) == 9
     lib = ctypes.CDLL(K.LIB_PATH)
     for name in names:
         assert hasattr(lib, name)

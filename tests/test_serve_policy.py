@@ -20,7 +20,7 @@ def _library():
 
 SMALL = ServeConfig(n_tables=8, ports=8, min_burst=32, max_burst=1024, offered_lookups_per_s=50e6,
                     insert_fraction=0.2, duration_s=0.02, footprint_bytes=4 << 20, insert_flush_keys=8192,
-                    insert_flush_s=200e-6, seed=3)
+                    insert_flush_s=200e-6, seed=3, overlap=False)  # one stream; overlap mode is tested below
 
 
 def simulate(cfg, host_s=10e-6, dev_fixed_s=5e-6, dev_per_key_s=0.2e-9, max_jobs=4096, planner=TurnPlanner):
@@ -283,6 +283,7 @@ class RefPlanner:
         self.pending, self.pending_keys, self.pending_tables = [], 0, set()
         self.held, self.held_tables = [], set()
         self.flight_bytes = 0
+        self.flight_cnt, self.flushes = {}, []  # overlap: flushes in flight per table, their tables in order
 
     def finished(self):
         return self.nxt >= self.n and not self.pending and not self.held
@@ -309,7 +310,7 @@ class RefPlanner:
         if not arrived and not flush:
             return "idle", None, self._wake(now)
         lo = stop = self.nxt
-        lookups = []
+        lookups, trailing = [], []
         if arrived:
             hi = lo
             while hi < self.n and st.arrival[hi] <= now:
@@ -336,31 +337,49 @@ class RefPlanner:
                     self.pending_keys += int(st.size[b])
                     self.pending_tables.add(t)
                 else:
-                    if len(lookups) + len(self.held) >= self.max_jobs:
+                    if len(lookups) + len(trailing) + len(self.held) >= self.max_jobs:
                         flush = True
                         break
                     if t in self.pending_tables:
                         self.held.append(b)
                         self.held_tables.add(t)
+                    elif self.flight_cnt.get(t, 0):
+                        trailing.append(b)
                     else:
                         lookups.append(b)
                 stop = b + 1
             self.flight_bytes += int(self.foot[lo:stop].sum())
             self.nxt = stop
         flush = bool(self.pending) and (flush or self._flush_due(now))
-        if not lookups and not flush:
+        if not lookups and not trailing and not flush:
             return "none", None, 0.0
-        turn = Turn(admitted=slice(lo, stop), lookups=np.asarray(lookups, np.int64))
+        turn = Turn(admitted=slice(lo, stop), lookups=np.asarray(lookups, np.int64),
+                    trailing=np.asarray(trailing, np.int64))
         if flush:
             turn.inserts, turn.insert_first = self.pending, int(st.offset[self.pending[0]])
             turn.insert_keys, turn.lookups_after = self.pending_keys, np.asarray(self.held, np.int64)
+            if cfg.overlap:
+                tables = list(dict.fromkeys(int(st.table[b]) for b in self.pending))
+                for t in tables:
+                    self.flight_cnt[t] = self.flight_cnt.get(t, 0) + 1
+                self.flushes.append(tables)
             self.pending, self.pending_keys, self.pending_tables = [], 0, set()
             self.held, self.held_tables = [], set()
-        turn.nbytes = int(self.foot[turn.done].sum())
+        if cfg.overlap:
+            turn.nbytes = int(self.foot[turn.lookups].sum())
+            turn.nbytes_b = int(self.foot[turn.part_b].sum())
+        else:
+            turn.nbytes = int(self.foot[turn.done].sum())
         return "launch", turn, 0.0
 
     def complete(self, turn):
         self.flight_bytes -= turn.nbytes
+
+    def complete_b(self, turn):
+        self.flight_bytes -= turn.nbytes_b
+        if turn.inserts:
+            for t in self.flushes.pop(0):
+                self.flight_cnt[t] -= 1
 
 
 @pytest.mark.parametrize("variant", ["small", "two_tables", "few_jobs", "tiny_budget", "many_tables"])
@@ -404,9 +423,9 @@ def test_native_planner_argument_errors():
     assert lib.ckpp_plan_create(*args(arrival, np.array([0, 1 << 20, 2], np.uint32))) == K.CKPP_EINVAL
     assert lib.ckpp_plan_create(*args(arrival, table)) == K.CKPP_OK
     try:
-        out = np.zeros((3, 3), np.int64)
+        out = np.zeros((4, 3), np.int64)
         turn = K.ckpp_turn()
-        ptrs = [out[i].ctypes.data for i in range(3)]
+        ptrs = [out[i].ctypes.data for i in range(4)]
         assert lib.ckpp_plan_next(h, 1.0, 0, C.byref(turn), *ptrs, 2) == K.CKPP_EINVAL  # three bursts arrived
         assert lib.ckpp_plan_next(h, 1.0, 0, C.byref(turn), *ptrs, 3) == K.CKPP_OK
         assert turn.action == K.PLAN_LAUNCH and (turn.admitted_lo, turn.admitted_hi) == (0, 3)
@@ -471,3 +490,128 @@ def test_serving_loops_refuse_bad_arguments_without_a_gpu():
                                     C.byref(stats)) == K.CKPP_EINVAL
     assert lib.ckpp_serve_run(pl._h, C.c_void_p(1), C.byref(buf), None, None, done.ctypes.data,
                               C.byref(stats)) == K.CKPP_EINVAL
+
+
+# ---------------------------------------------------------------- overlap mode
+
+def simulate_overlap(cfg, host_s=10e-6, dev_fixed_s=5e-6, dev_per_key_s=0.2e-9, max_jobs=4096,
+                     planner=TurnPlanner):
+    """Runs the planner in overlap mode against a simulated device with two
+    in-order streams: a turn's first-stream part (its free lookups) runs in
+    order on stream A; its second-stream part (trailing lookups, flush, held
+    lookups) on stream B, after A's part of the same turn. Completions are
+    reported when the clock passes them, before the next planning call.
+    Returns the stream and the turns as (launch time, turn, A end, B end or
+    None)."""
+    st = draw_stream(cfg)
+    pl = planner(st, cfg, max_jobs)
+    now, a_free, b_free = 0.0, 0.0, 0.0
+    out_a, out_b, launched = deque(), deque(), []
+    for _ in range(10_000_000):
+        if pl.finished() and not out_a and not out_b:
+            break
+        while out_a and out_a[0][0] <= now:
+            pl.complete(out_a.popleft()[1])
+        while out_b and out_b[0][0] <= now:
+            pl.complete_b(out_b.popleft()[1])
+        action, turn, wake = pl.plan(now, bool(out_a or out_b))
+        if action == "idle":
+            times = [w for w in (wake,) if w > now] + [q[0][0] for q in (out_a, out_b) if q]
+            now = min(times) if times else now + 1e-6
+            continue
+        if action == "block":
+            now = max(now, min(q[0][0] for q in (out_a, out_b) if q))
+            continue
+        if action == "none":
+            continue
+        keys_a = int(st.size[turn.lookups].sum())
+        a_end = max(now, a_free) + (dev_fixed_s + dev_per_key_s * keys_a if keys_a else 0.0)
+        a_free = a_end
+        out_a.append((a_end, turn))
+        b_end = None
+        if turn.part_b.shape[0]:
+            b_end = max(now, b_free, a_end) + dev_fixed_s + dev_per_key_s * int(st.size[turn.part_b].sum())
+            b_free = b_end
+            out_b.append((b_end, turn))
+        launched.append((now, turn, a_end, b_end))
+        now += host_s
+    else:
+        raise AssertionError("planner did not finish")
+    return st, launched
+
+
+def check_overlap_order(st, launched):
+    """Every burst is launched once; per table, each lookup and each insert
+    are ordered as they arrived, by the device's dependencies alone: the same
+    stream's order, a second-stream part waiting for its turn's first-stream
+    part (and so for every earlier one), and a second-stream part reported
+    complete before a later turn was planned."""
+    n = st.arrival.shape[0]
+    seen = np.zeros(n, np.int64)
+    where = {}  # burst -> (stream, turn index, phase)
+    launch_t, b_end = [], []
+    for k, (t, turn, a_end, be) in enumerate(launched):
+        launch_t.append(t)
+        b_end.append(be)
+        for b in turn.lookups:
+            where[int(b)] = ("A", k, 0)
+        for ph, arr in ((0, turn.trailing), (1, np.asarray(turn.inserts, np.int64)), (2, turn.lookups_after)):
+            for b in arr:
+                where[int(b)] = ("B", k, ph)
+        seen[turn.done] += 1
+    assert (seen == 1).all(), "every burst is launched exactly once"
+
+    def before(x, y):  # x happens before y
+        (sx, kx, px), (sy, ky, py) = where[x], where[y]
+        if sx == sy:
+            return (kx, px) < (ky, py)
+        if sx == "A":  # y on B waits for its turn's first-stream part, which follows x's
+            return kx <= ky
+        return b_end[kx] is not None and b_end[kx] <= launch_t[ky]  # reported complete before y's turn
+    for t in np.unique(st.table):
+        idx = np.flatnonzero(st.table == t)
+        ins = [int(b) for b in idx if st.insert[b]]
+        for lk in (int(b) for b in idx if not st.insert[b]):
+            for i in ins:
+                if i < lk:
+                    assert before(i, lk), f"lookup {lk} of table {t} runs before the earlier insert {i}"
+                else:
+                    assert before(lk, i), f"insert {i} of table {t} is applied before the earlier lookup {lk}"
+
+
+OVERLAP = replace(SMALL, overlap=True)
+
+
+@pytest.mark.parametrize("variant", ["small", "two_tables", "few_jobs", "many_tables", "slow_device"])
+def test_overlap_orders_every_table_and_matches_plain_rules(variant):
+    cfg = {"small": OVERLAP, "few_jobs": OVERLAP, "slow_device": OVERLAP,
+           "two_tables": replace(OVERLAP, n_tables=2, insert_fraction=0.5, lookup_hold_s=5e-4),
+           "many_tables": replace(OVERLAP, n_tables=1024)}[variant]
+    kw = {"max_jobs": 3} if variant == "few_jobs" else {}
+    if variant == "slow_device":
+        kw.update(dev_per_key_s=20e-9)  # flushes long enough that many turns meet one in flight
+    runs = [simulate_overlap(cfg, planner=cls, **kw) for cls in (TurnPlanner, RefPlanner)]
+    (st, a), (_, b) = runs
+    assert len(a) == len(b)
+    for (ta, x, _, _), (tb, y, _, _) in zip(a, b):
+        assert ta == tb and x.admitted == y.admitted and x.inserts == y.inserts
+        for f in ("lookups", "trailing", "lookups_after"):
+            assert np.array_equal(getattr(x, f), getattr(y, f)), f
+        assert (x.insert_first, x.insert_keys, x.nbytes, x.nbytes_b) == (y.insert_first, y.insert_keys, y.nbytes,
+                                                                         y.nbytes_b)
+    check_overlap_order(st, a)
+    if variant in ("small", "slow_device"):
+        assert sum(x.trailing.shape[0] for _, x, _, _ in a) > 0, "no lookup trailed a flush in flight"
+
+
+def test_overlap_order_check_catches_trailing_lookups_on_the_first_stream():
+    """Planted mistake: trailing lookups launched with the free lookups (on
+    the first stream, not behind the flush in flight) can run before an
+    earlier insert of their table, and the check says so."""
+    from dataclasses import replace as dc_replace
+    st, launched = simulate_overlap(replace(OVERLAP, n_tables=2, insert_fraction=0.5), dev_per_key_s=20e-9)
+    check_overlap_order(st, launched)
+    moved = [(t, dc_replace(turn, lookups=np.sort(np.concatenate([turn.lookups, turn.trailing])),
+                            trailing=np.zeros(0, np.int64)), a, b) for t, turn, a, b in launched]
+    with pytest.raises(AssertionError):
+        check_overlap_order(st, moved)
