@@ -664,13 +664,17 @@ def mutation_rates(table, dev, stream, ins_times, seed):
     out["insert_at_lf0.9_Mops"] = round(k.shape[0] / (e[1].elapsed_time(e[2]) / 1e3) / 1e6, 1)
     out["delete_ok"] = bool((st == 4).all())
     out["reinsert_ok"] = bool((st2 == 1).all())
-    # expiration scan over a timers table of the same bucket count
+    # expiration scan over a timers table of the same bucket count (one untimed scan first: the
+    # table's pages are touched once before the timed scans)
     tt = FlowTable(table.n_buckets, timers=True, seed=seed, device=dev)
-    e[0].record(stream)
     tt.expire(100, stream)
+    reps = 5
+    e[0].record(stream)
+    for r in range(reps):
+        tt.expire(101 + r, stream)
     e[1].record(stream)
     e[1].synchronize()
-    secs = e[0].elapsed_time(e[1]) / 1e3
+    secs = e[0].elapsed_time(e[1]) / 1e3 / reps
     out["expire_scan_GBs"] = round(table.n_buckets * 64 / secs / 1e9, 1)
     del tt
     return out
