@@ -25,8 +25,9 @@
 //             bucket of the path plus the key's primary, re-validate the path,
 //             and move the entries backwards and store the key, all under
 //             those locks; retry a bounded number of times. Keys still
-//             unplaced get a wider search by 8 single-warp blocks, then the
-//             widest by 16 single-thread blocks; only then FULL.
+//             unplaced get a wider search, then the widest, each run by a
+//             whole warp per key (a level of the search in two round trips);
+//             only then FULL.
 //   fixup and finish (one kernel) - reset the filter of buckets whose moved
 //             counter reached zero off their lock (the reset of Sec. 4.1,
 //             deferred so that it never races a concurrent setter); non-leader
@@ -337,12 +338,13 @@ __global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t
 // --------------------------------------------------------------- phase 2
 // Search budgets of the displacement passes after move1 (queue in shared
 // memory, at most 48 KB per block): the grid pass searches 96 buckets up to 4
-// moves deep per thread; the second pass (8 blocks of one warp) 192 buckets, 5
-// moves; the last pass (16 blocks of one thread) 2048 buckets, 6 moves (the
-// sequential CPU reference searches 1024 buckets, 5 moves). Each later pass
-// runs far fewer searches at once, so paths rarely collide, and takes on at
-// most kSecondPassKeys / kLastPassKeys keys: more failures than that mean the
-// table is full, not contended, and the rest are FULL without a search.
+// moves deep, one thread per key (many keys, so the searches in flight matter
+// most); the second pass 192 buckets, 5 moves, and the last pass 2048 buckets,
+// 6 moves, one warp per key (few keys, so the time of one search matters
+// most; the sequential CPU reference searches 1024 buckets, 5 moves). Each
+// later pass takes on at most kSecondPassKeys / kLastPassKeys keys: more
+// failures than that mean the table is full, not contended, and the rest are
+// FULL without a search.
 //
 // Within one insert call no bucket gains a free or dead slot: phase 1 fills
 // them, a path ends by filling one, every move along it vacates a slot that
@@ -352,8 +354,6 @@ __global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t
 constexpr int kP2Threads = 64;
 constexpr uint32_t kSecondPassKeys = 4096;  // keys the second pass takes on
 constexpr uint32_t kLastPassKeys = 128;     // keys the last pass takes on
-constexpr unsigned kSecondPassBlocks = 8;
-constexpr unsigned kLastPassBlocks = 16;
 constexpr int kMaxDepth = 6;
 constexpr int kPathBuckets = kMaxDepth + 1;
 constexpr int kMaxLocks = kPathBuckets + 1;   // the path plus the key's primary
@@ -473,6 +473,126 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue&
         return nq - 1;
       }
     }
+  }
+  return -1;
+}
+
+// The same search run by a whole warp for one key. A round expands up to 32
+// queued buckets at once, one per lane, with the thread form's two round trips
+// (a lane's bucket keys and control word, then the control words of the 8
+// buckets its entries can move to), so a level of the search costs two round
+// trips however wide it is. The children of a round enter the queue in queue
+// order (lane, then slot; the queue stays sorted by depth), each bucket once:
+// the visited set is a shared open-addressing table updated with atomicCAS,
+// sized for the queue plus one round of children. The hole is the first child
+// in queue order with a free or dead slot, a shortest path as in the thread
+// form. q: the warp's queue (kBfsNodes nodes); seen: its set. Every lane
+// returns the same node index (or -1) and hole.
+constexpr uint32_t kWarpAll = 0xFFFFFFFFu;
+
+template <int kBfsNodes>
+struct WarpSeen {
+  // smallest power of two at least 1.5 x (kBfsNodes + the 256 children of a round)
+  static constexpr uint32_t kNeed = (kBfsNodes + 256) * 3 / 2;
+  static constexpr uint32_t kSize = kNeed <= 1024 ? 1024 : (kNeed <= 2048 ? 2048 : (kNeed <= 4096 ? 4096 : 8192));
+  static_assert(kNeed <= 8192, "visited set too large");
+};
+
+template <uint32_t kSize>
+__device__ __forceinline__ bool seen_insert_shared(uint32_t* seen, uint32_t b) {
+  uint32_t h = (b * 0x9E3779B1u) & (kSize - 1);
+  for (uint32_t probe = 0; probe < kSize; ++probe) {
+    const uint32_t old = atomicCAS(&seen[h], 0xFFFFFFFFu, b);
+    if (old == 0xFFFFFFFFu) return true;
+    if (old == b) return false;
+    h = (h + 1) & (kSize - 1);
+  }
+  return false;  // not reached: the set is sized for every bucket a search can meet
+}
+
+template <int kBfsNodes, int kBfsDepth>
+__device__ int bfs_warp(const TableView& t, const Addr& a, uint32_t now, Node* q, uint32_t* seen, uint32_t& hole) {
+  constexpr uint32_t kSeen = WarpSeen<kBfsNodes>::kSize;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t j = lane; j < kSeen; j += 32) seen[j] = 0xFFFFFFFFu;
+  __syncwarp();
+  if (lane == 0) {
+    q[0] = Node{a.b1, -1, 0, 0};
+    q[1] = Node{a.b2, -1, 0, 0};
+    seen_insert_shared<kSeen>(seen, a.b1);
+    seen_insert_shared<kSeen>(seen, a.b2);
+  }
+  __syncwarp();
+  int nq = 2;
+  for (int head = 0; head < nq && nq < kBfsNodes;) {
+    const int chunk_end = min(nq, head + 32);
+    const int qi = head + (int)lane;
+    Node cur{0, -1, 0, (uint8_t)kBfsDepth};
+    if (qi < chunk_end) cur = q[qi];
+    uint32_t y[kSlots];
+    uint32_t fresh = 0;   // children this lane queues
+    uint64_t holes = 0;   // their free or dead slots, 8 bits per child
+    if (cur.depth < kBfsDepth) {
+      uint64_t k0[kSlots], k1[kSlots];
+      const uint32_t cc = load_bucket_keys(t, cur.bucket, k0, k1);
+      uint32_t cy[kSlots];
+      uint64_t e0[kSlots], e1[kSlots];
+#pragma unroll
+      for (uint32_t sl = 0; sl < kSlots; ++sl)
+        y[sl] = other_bucket(Key{k0[sl], k1[sl]}, cur.bucket, (cc >> (kInsecShift + sl)) & 1u, t.nb, t.seed);
+#pragma unroll
+      for (uint32_t sl = 0; sl < kSlots; ++sl) {
+        cy[sl] = ld32_cg(ctrl_ptr(t, y[sl]));
+        if (t.timers) {
+          ld128_cg(expiry_ptr(t, y[sl], 0), e0[sl], e1[sl]);
+        } else {
+          e0[sl] = e1[sl] = 0;
+        }
+      }
+#pragma unroll
+      for (uint32_t sl = 0; sl < kSlots; ++sl) {
+        if (!seen_insert_shared<kSeen>(seen, y[sl])) continue;
+        fresh |= 1u << sl;
+        Snap s;
+        s.e0 = e0[sl];
+        s.e1 = e1[sl];
+        holes |= (uint64_t)free_mask(t, cy[sl], s, now) << (8 * sl);
+      }
+    }
+    // queue positions: the children of lower lanes first
+    const uint32_t cnt = __popc(fresh);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(kWarpAll, incl, d);
+      if ((int)lane >= d) incl += o;
+    }
+    const uint32_t total = __shfl_sync(kWarpAll, incl, 31);
+    int pos = nq + (int)(incl - cnt);
+    int best = 0x7FFFFFFF;  // this lane's first queued child with room
+    uint32_t best_hole = 0;
+#pragma unroll
+    for (uint32_t sl = 0; sl < kSlots; ++sl) {
+      if (!((fresh >> sl) & 1u)) continue;
+      if (pos < kBfsNodes) {
+        q[pos] = Node{y[sl], (int16_t)qi, (uint8_t)sl, (uint8_t)(cur.depth + 1)};
+        const uint32_t f = (uint32_t)(holes >> (8 * sl)) & 0xFFu;
+        if (f && best == 0x7FFFFFFF) {
+          best = pos;
+          best_hole = __ffs(f) - 1;
+        }
+      }
+      ++pos;
+    }
+    __syncwarp();  // the new nodes before any lane reads them
+    const int wbest = __reduce_min_sync(kWarpAll, best);
+    if (wbest != 0x7FFFFFFF) {
+      const uint32_t src = __ffs(__ballot_sync(kWarpAll, best == wbest)) - 1;
+      hole = __shfl_sync(kWarpAll, best_hole, src);
+      return wbest;
+    }
+    nq = min(nq + (int)total, kBfsNodes);
+    head = chunk_end;
   }
   return -1;
 }
@@ -783,6 +903,81 @@ __device__ void phase2_range(const TableSet& ts, const uint8_t* __restrict__ key
   }
 }
 
+// phase2_range with one warp per key (bfs_warp): warp / warps are this warp's
+// index among the warps sharing the pass; q and seen are the warp's own.
+template <int kBfsNodes, int kBfsDepth>
+__device__ void phase2_range_warp(const TableSet& ts, const uint8_t* __restrict__ keys,
+                                  const uint64_t* __restrict__ vals, uint32_t now, uint32_t expiry,
+                                  uint8_t* __restrict__ status, const Workspace& ws, const uint32_t* list,
+                                  const uint32_t* count_ptr, uint32_t* retry, uint32_t* retry_count,
+                                  uint32_t max_keys, Node* q, uint32_t* seen, uint32_t warp, uint32_t warps) {
+  static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t listed = ld32_cg(count_ptr);
+  const uint32_t count = min(listed, max_keys);
+  for (uint32_t j = count + warp * 32 + lane; j < listed; j += warps * 32) status[list[j]] = kStFull;
+  for (uint32_t j = warp; j < count; j += warps) {
+    const uint32_t i = list[j];
+    const TableView t = ts.of(i);
+    const uint32_t tid = ts.id(i);
+    const uint64_t v = value_of(ws, vals, i);
+    const Key k = load_key(keys, i);
+    const Addr a = address_of(k, t.nb, t.seed);
+    uint8_t st = kStFull;
+    for (int attempt = 0; attempt < kPathAttempts; ++attempt) {
+      uint32_t hole = 0;
+      const int end = bfs_warp<kBfsNodes, kBfsDepth>(t, a, now, q, seen, hole);
+      if (end < 0) break;  // no cuckoo path within the search bound: FULL
+      int r = 0;
+      if (lane == 0) {
+        uint32_t path[kPathBuckets], slot[kPathBuckets];
+        const int len = q[end].depth;
+        for (int node = end; node >= 0; node = q[node].parent) {
+          path[q[node].depth] = q[node].bucket;
+          if (q[node].depth > 0) slot[q[node].depth - 1] = q[node].slot;
+        }
+        r = execute_path(t, tid, path, slot, len, hole, k, v, a, now, expiry, ws);
+      }
+      r = __shfl_sync(kWarpAll, r, 0);  // also: lane 0 is done with the queue
+      if (r != 0) {
+        st = r > 0 ? kStInserted : kStBusy;
+        break;
+      }
+    }
+    if (lane == 0) {
+      if (st == kStFull && retry) {
+        retry[atomicAdd(retry_count, 1u)] = i;
+      } else {
+        if (st == kStBusy) latch_error(t, kErrLockTimeout);
+        status[i] = st;
+      }
+    }
+  }
+}
+
+template <int kBfsNodes>
+__host__ __device__ constexpr size_t warp_search_bytes() {
+  return kBfsNodes * sizeof(Node) + WarpSeen<kBfsNodes>::kSize * sizeof(uint32_t);
+}
+
+template <int kWarps, int kBfsNodes, int kBfsDepth>
+__global__ void __launch_bounds__(kWarps * 32, 1) insert_phase2_warp(TableSet ts, const uint8_t* __restrict__ keys,
+                                                                  const uint64_t* __restrict__ vals, uint32_t now,
+                                                                  uint32_t expiry, uint8_t* __restrict__ status,
+                                                                  Workspace ws, const uint32_t* list,
+                                                                  const uint32_t* count_ptr, uint32_t* retry,
+                                                                  uint32_t* retry_count, uint32_t max_keys) {
+  pdl_wait();
+  pdl_release();
+  static_assert(kWarps * warp_search_bytes<kBfsNodes>() <= 48 * 1024, "search state exceeds 48 KB");
+  __shared__ Node queues[kWarps][kBfsNodes];
+  __shared__ uint32_t sets[kWarps][WarpSeen<kBfsNodes>::kSize];
+  const uint32_t w = threadIdx.x >> 5;
+  phase2_range_warp<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, count_ptr, retry,
+                                          retry_count, max_keys, queues[w], sets[w], blockIdx.x * kWarps + w,
+                                          gridDim.x * kWarps);
+}
+
 template <int kThreadsPerBlock, int kBfsNodes, int kBfsDepth>
 __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, const uint8_t* __restrict__ keys,
                                                                   const uint64_t* __restrict__ vals, uint32_t now,
@@ -854,17 +1049,19 @@ __global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uin
 // kernel reaches), so the barrier cannot wait on a block that has not
 // started. Search queues live in 48 KB of dynamic shared memory per block: the
 // grid pass runs on 64 threads of every block (96 nodes each), the second pass
-// on one warp of each of the first 8 blocks (192 nodes), the last on one thread
-// of each of the next 16 blocks (2048 nodes and the visited set).
+// on every warp (192 nodes and a visited set each), the last on the first warp
+// of every block (2048 nodes and the visited set).
 constexpr int kSingleThreads = 256;
 constexpr size_t kSingleSmem = 48 * 1024;
+constexpr unsigned kSingleMinBlocks = 8;
 // Bounded wait at a barrier: about 2-4 s of polls (each a load and a 64 ns sleep), longer than
 // the bounded lock waits a stage may contain, so a barrier gives up only if a block never arrives.
 constexpr int kBarrierSpins = 1 << 22;
 
 static_assert(96 * 64 * sizeof(Node) <= kSingleSmem, "grid pass queues exceed the shared memory");
-static_assert(192 * 32 * sizeof(Node) <= kSingleSmem, "second pass queues exceed the shared memory");
-static_assert(2048 * sizeof(Node) + SeenSet<2048>::kSize * 4 <= kSingleSmem, "last pass state exceeds the shared memory");
+static_assert((kSingleThreads / 32) * warp_search_bytes<192>() <= kSingleSmem,
+              "second pass state exceeds the shared memory");
+static_assert(warp_search_bytes<2048>() <= kSingleSmem, "last pass state exceeds the shared memory");
 
 __device__ __forceinline__ uint32_t ld_acquire32(const uint32_t* p) {
   uint32_t v;
@@ -936,23 +1133,21 @@ __global__ void __launch_bounds__(kSingleThreads, 2) insert_single_launch(TableS
     }
     ok &= grid_barrier(bar_count, bar_gen);
   }
+  const uint32_t w = threadIdx.x >> 5;
   if (ld32_cg(ws.counters + 5)) {
-    if (blockIdx.x < kSecondPassBlocks && threadIdx.x < 32) {
-      const Queue q{nodes + threadIdx.x, 32};
-      phase2_range<192, 5>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 5, ws.retry,
-                           ws.counters + 6, kSecondPassKeys, q, nullptr, blockIdx.x * 32 + threadIdx.x,
-                           kSecondPassBlocks * 32);
-    }
+    constexpr size_t kPer = warp_search_bytes<192>();
+    uint8_t* mine = smem + w * kPer;
+    phase2_range_warp<192, 5>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 5, ws.retry,
+                              ws.counters + 6, kSecondPassKeys, reinterpret_cast<Node*>(mine),
+                              reinterpret_cast<uint32_t*>(mine + 192 * sizeof(Node)),
+                              blockIdx.x * (kSingleThreads / 32) + w, gridDim.x * (kSingleThreads / 32));
     ok &= grid_barrier(bar_count, bar_gen);
   }
   if (ld32_cg(ws.counters + 6)) {
-    if (blockIdx.x >= kSecondPassBlocks && blockIdx.x < kSecondPassBlocks + kLastPassBlocks && threadIdx.x == 0) {
-      const Queue q{nodes, 1};
-      uint32_t* seen = reinterpret_cast<uint32_t*>(smem + 2048 * sizeof(Node));
-      phase2_range<2048, 6>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 6, (uint32_t*)nullptr,
-                            (uint32_t*)nullptr, kLastPassKeys, q, seen, blockIdx.x - kSecondPassBlocks,
-                            kLastPassBlocks);
-    }
+    if (w == 0)
+      phase2_range_warp<2048, 6>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 6,
+                                 (uint32_t*)nullptr, (uint32_t*)nullptr, kLastPassKeys, nodes,
+                                 reinterpret_cast<uint32_t*>(smem + 2048 * sizeof(Node)), blockIdx.x, gridDim.x);
     ok &= grid_barrier(bar_count, bar_gen);
   }
   fixup_finish_range(ts, n, status, ws, tid, threads);
@@ -1081,8 +1276,7 @@ int single_launch_blocks_per_sm() {
     cudaGetLastError();
     return 0;
   }
-  v = (coop && per_sm > 0 && (uint64_t)device_sm_count() * (per_sm < 2 ? per_sm : 2) >=
-                                 kSecondPassBlocks + kLastPassBlocks)
+  v = (coop && per_sm > 0 && (uint64_t)device_sm_count() * (per_sm < 2 ? per_sm : 2) >= kSingleMinBlocks)
           ? (per_sm < 2 ? per_sm : 2)
           : -1;
   cache[dev].store(v, std::memory_order_relaxed);
@@ -1095,9 +1289,9 @@ cudaError_t launch_single(const TableSet& ts, const uint8_t* keys, const uint64_
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cudaLaunchConfig_t cfg = {};
-  // one thread per key up to the resident limit, and at least the blocks the search passes use
+  // one thread per key up to the resident limit, and a few blocks for the warps of the search passes
   const uint64_t want = (n + kSingleThreads - 1) / kSingleThreads;
-  const uint64_t lo = kSecondPassBlocks + kLastPassBlocks, hi = (uint64_t)device_sm_count() * per_sm;
+  const uint64_t lo = kSingleMinBlocks, hi = (uint64_t)device_sm_count() * per_sm;
   cfg.gridDim = dim3((unsigned)(want < lo ? lo : (want > hi ? hi : want)));
   cfg.blockDim = dim3(kSingleThreads);
   cfg.dynamicSmemBytes = kSingleSmem;
@@ -1137,14 +1331,13 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
                      ws, (const uint32_t*)ws.retry, (const uint32_t*)(ws.counters + 3), ws.pending, ws.counters + 5,
                      0xFFFFFFFFu);
   if (e != cudaSuccess) return e;
-  // second pass, 8 single-warp blocks: the keys the grid pass could not place
-  e = launch_chained(insert_phase2<32, 192, 5>, kSecondPassBlocks, 32, s, ts, keys, vals, now, expiry, status, ws,
+  // second pass, one warp per key: the keys the grid pass could not place
+  e = launch_chained(insert_phase2_warp<8, 192, 5>, sms, 8 * 32, s, ts, keys, vals, now, expiry, status, ws,
                      (const uint32_t*)ws.pending, (const uint32_t*)(ws.counters + 5), ws.retry, ws.counters + 6,
                      kSecondPassKeys);
   if (e != cudaSuccess) return e;
-  // last pass, 16 single-thread blocks: the widest search, a few searches at
-  // a time; a key is FULL only if it finds no path
-  e = launch_chained(insert_phase2<1, 2048, 6>, kLastPassBlocks, 1, s, ts, keys, vals, now, expiry, status, ws,
+  // last pass, one warp per key: the widest search; a key is FULL only if it finds no path
+  e = launch_chained(insert_phase2_warp<1, 2048, 6>, kLastPassKeys, 32, s, ts, keys, vals, now, expiry, status, ws,
                      (const uint32_t*)ws.retry, (const uint32_t*)(ws.counters + 6), (uint32_t*)nullptr,
                      (uint32_t*)nullptr, kLastPassKeys);
   if (e != cudaSuccess) return e;

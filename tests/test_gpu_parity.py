@@ -283,6 +283,43 @@ def test_near_full_tiny_table_stays_consistent(K, insert_launch):
 
 
 @pytest.mark.parametrize("timers", [False, True])
+def test_batches_past_capacity_reach_every_search_pass(K, timers, insert_launch):
+    """Batches of new keys into a 2^14-bucket table until past LF 0.99, as the
+    insert-rate workload does at scale: the wide search passes (one warp per
+    key) place keys the grid search could not, no key is FULL below LF 0.95,
+    FULL keys are absent and every other key is present with its value, and
+    the invariants hold after every batch."""
+    nb, batch = 1 << 14, 4096
+    g = FT(nb, timers=timers, seed=47)
+    now, ttl = (7, 1000) if timers else (0, 0)
+    f = W.fill(47, int(1.3 * nb * 8))
+    stored, drawn, passes = 0, 0, np.zeros(3, dtype=np.int64)
+    all_st = []
+    while stored < 0.99 * nb * 8:
+        sl = slice(drawn, drawn + batch)
+        drawn += batch
+        assert drawn <= f.keys.shape[0]
+        st = g.insert(f.keys[sl], f.values[sl], now, ttl).cpu().numpy()
+        diag = g.workspace(batch)[:32].cpu().numpy().view(np.uint32)
+        passes += [diag[3] > 0, diag[5] > 0, diag[6] > 0]
+        assert set(np.unique(st)) <= {K.ST_INSERTED, K.ST_FULL}
+        if stored < 0.95 * nb * 8:
+            assert (st == K.ST_INSERTED).all()
+        stored += int((st == K.ST_INSERTED).sum())
+        all_st.append(st)
+        assert g.sync_status() == 0
+        assert download(g).check() == []
+    assert stored / (nb * 8) >= 0.97
+    assert passes[1] > 0 and passes[2] > 0, passes  # the second and last passes had keys
+    keys, vals, st = f.keys[:drawn], f.values[:drawn], np.concatenate(all_st)
+    v, fd = g.lookup(keys, now)
+    fd = fd.cpu().numpy()
+    assert (fd == (st == K.ST_INSERTED)).all()
+    assert (np_vals(v)[fd] == vals[fd]).all()
+    assert len(download(g).live(now)) == stored
+
+
+@pytest.mark.parametrize("timers", [False, True])
 def test_single_batch_fill_to_lf095(timers, insert_launch):
     """One batch taking an empty table to LF 0.95 (heavy concurrent cuckoo
     displacement): every key INSERTED, invariants hold, the live set is exact."""
