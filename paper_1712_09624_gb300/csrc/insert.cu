@@ -342,9 +342,10 @@ __global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t
 // most); the second pass 192 buckets, 5 moves, and the last pass 2048 buckets,
 // 6 moves, one warp per key (few keys, so the time of one search matters
 // most; the sequential CPU reference searches 1024 buckets, 5 moves). Each
-// later pass takes on at most kSecondPassKeys / kLastPassKeys keys: more
-// failures than that mean the table is full, not contended, and the rest are
-// FULL without a search.
+// later pass takes on at most kSecondPassKeys / kLastPassKeys keys, which
+// bounds the time a batch spends on a table that is full: the rest are FULL
+// without a search. Near LF 0.98 the second pass still places about two
+// thirds of the keys it searches, so its share is wide.
 //
 // Within one insert call no bucket gains a free or dead slot: phase 1 fills
 // them, a path ends by filling one, every move along it vacates a slot that
@@ -352,8 +353,8 @@ __global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t
 // phase 1 found both its buckets without a free or dead slot, so the passes
 // search from them without re-checking the roots.
 constexpr int kP2Threads = 64;
-constexpr uint32_t kSecondPassKeys = 4096;  // keys the second pass takes on
-constexpr uint32_t kLastPassKeys = 128;     // keys the last pass takes on
+constexpr uint32_t kSecondPassKeys = 65536;  // keys the second pass takes on
+constexpr uint32_t kLastPassKeys = 1024;     // keys the last pass takes on
 constexpr int kMaxDepth = 6;
 constexpr int kPathBuckets = kMaxDepth + 1;
 constexpr int kMaxLocks = kPathBuckets + 1;   // the path plus the key's primary
