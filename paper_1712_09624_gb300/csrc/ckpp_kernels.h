@@ -36,7 +36,7 @@ inline int device_sm_count() {
 struct Workspace {
   uint32_t* counters;   // [0] pending count, [1] fixup count, [2] fixup overflow flag; list counts of the
                         // displacement passes: [3] after move1 (in `retry`), [5] after the grid search
-                        // (in `pending`), [6] after the block search (in `retry`)
+                        // (in `pending`), [6] after the second search (in `retry`)
   uint32_t* set;        // [2m] open-addressing set of batch keys; position p holds two words side by
                         // side (one line for both): the lowest batch index of the key (kEmpty when
                         // free) and the highest
@@ -52,6 +52,10 @@ struct Workspace {
 
   __device__ __forceinline__ uint32_t* first_at(uint32_t p) const { return set + 2 * (uint64_t)p; }
   __device__ __forceinline__ uint32_t* last_at(uint32_t p) const { return set + 2 * (uint64_t)p + 1; }
+  // both words of position p as one 64-bit word: first in the low half, last in the high half
+  __device__ __forceinline__ unsigned long long* pair_at(uint32_t p) const {
+    return reinterpret_cast<unsigned long long*>(set + 2 * (uint64_t)p);
+  }
 };
 
 // The table(s) a mutation batch works on: one table, or many (key i goes to

@@ -60,20 +60,32 @@ __device__ void dedup_one(const uint8_t* __restrict__ keys, const TableSet& ts, 
   const Key k = load_key(keys, i);
   const uint32_t tid = ts.id(i);
   uint32_t pos = (uint32_t)(hash_key(k, 0x51ED270B27A2B5E3ull ^ tid) >> 16) & ws.m_mask;
+  const uint32_t me = (uint32_t)i;
+  constexpr unsigned long long kFreePair = kEmpty;  // first kEmpty, last 0
   for (uint32_t probe = 0; probe <= ws.m_mask; ++probe) {
-    // the CAS claims a free position or returns the index of the key group holding it
-    const uint32_t cur = atomicCAS(ws.first_at(pos), kEmpty, (uint32_t)i);
-    if (cur == kEmpty) {
-      atomicMax(ws.last_at(pos), (uint32_t)i);
+    // one 64-bit CAS claims a free position (first = last = i) or returns the
+    // index range of the key group holding it
+    unsigned long long* pair = ws.pair_at(pos);
+    unsigned long long old = atomicCAS(pair, kFreePair, ((unsigned long long)me << 32) | me);
+    if (old == kFreePair) {
       ws.slot_of[i] = pos;
       return;
     }
-    // A first-index word only ever holds batch indices of one key group, so
-    // the key at index cur is that group's key even while atomicMin lowers cur.
+    // A position only ever holds batch indices of one key group, so the key
+    // at index cur is that group's key even while other members widen the range.
+    const uint32_t cur = (uint32_t)old;
     const Key o = load_key(keys, cur);
     if (o.k0 == k.k0 && o.k1 == k.k1 && ts.id(cur) == tid) {
-      atomicMin(ws.first_at(pos), (uint32_t)i);
-      atomicMax(ws.last_at(pos), (uint32_t)i);
+      // widen the group's range to include i; a CAS fails only when another
+      // member's succeeded, so this ends within the group's size
+      for (;;) {
+        const uint32_t f = (uint32_t)old, l = (uint32_t)(old >> 32);
+        const unsigned long long want = ((unsigned long long)(l > me ? l : me) << 32) | (f < me ? f : me);
+        if (want == old) break;
+        const unsigned long long seen = atomicCAS(pair, old, want);
+        if (seen == old) break;
+        old = seen;
+      }
       ws.slot_of[i] = pos;
       // both occurrences are flagged: the first to claim the position learns of the
       // group only here (every later occurrence's CAS returns a member of it)
@@ -1323,7 +1335,7 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
   e = launch_chained(insert_publish, grid_for(n, kThreads), kThreads, s, ts, n, ws);
   if (e != cudaSuccess) return e;
   // lists: phase 1 -> pending [0] -> move1 -> retry [3] -> grid search ->
-  // pending [5] -> block search -> retry [6] -> last search
+  // pending [5] -> second search -> retry [6] -> last search
   const unsigned sms = (unsigned)device_sm_count();
   e = launch_chained(insert_move1, sms * 16, kThreads, s, ts, keys, vals, now, expiry, status, ws,
                      (const uint32_t*)ws.pending, (const uint32_t*)(ws.counters + 0), ws.retry, ws.counters + 3);
