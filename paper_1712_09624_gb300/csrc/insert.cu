@@ -320,7 +320,7 @@ __device__ void phase1_one(const TableSet& ts, const uint8_t* __restrict__ keys,
   status[i] = r.status;
 }
 
-__global__ void __launch_bounds__(kThreads) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
+__global__ void __launch_bounds__(kThreads, 1) insert_phase1(TableSet ts, const uint8_t* __restrict__ keys,
                                                           const uint64_t* __restrict__ vals, uint64_t n,
                                                           uint32_t now, uint32_t expiry, uint8_t* __restrict__ status,
                                                           Workspace ws) {
