@@ -89,6 +89,8 @@ def parse():
                    help="served: coalesced inserts go out once this many keys wait (default: the loop's own)")
     p.add_argument("--serve-flush-us", type=float, default=None,
                    help="served: ... or once the oldest waiting insert burst is this old")
+    p.add_argument("--serve-hold-us", type=float, default=None,
+                   help="served: ... or once a lookup held behind waiting inserts is this old")
     p.add_argument("--tables", type=int, default=4096, help="batched: number of tables")
     p.add_argument("--record-traffic", metavar="CSV", default=None,
                    help="write profiles/lookup_traffic.json from an ncu --csv log of the lookup kernel and exit")
@@ -971,6 +973,8 @@ def run_served(args):
         cfg.insert_flush_keys = args.serve_flush_keys
     if args.serve_flush_us is not None:
         cfg.insert_flush_s = args.serve_flush_us * 1e-6
+    if args.serve_hold_us is not None:
+        cfg.lookup_hold_s = args.serve_hold_us * 1e-6
     if args.serve_max_inflight is not None:
         cfg.max_inflight = args.serve_max_inflight
     if args.serve_one_stream:
