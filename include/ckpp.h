@@ -311,7 +311,7 @@ int ckpp_bulk_delete(ckpp_table* table, const ckpp_key* keys, uint64_t n, uint32
 /* Bulk insert for callers that cannot allocate device memory. No counterpart
  * in the paper: it is ckpp_bulk_insert with the same semantics, arguments and
  * status codes, minus the workspace. Its scratch is a fixed device array built
- * into libckpp.so (about 3 MB, enough for CKPP_NOALLOC_MAX_KEYS keys), which
+ * into libckpp.so (about 6 MB, enough for CKPP_NOALLOC_MAX_KEYS keys), which
  * every GPU that loads the library holds until the process exits. It suits
  * callers that own no allocator when they insert: a data-plane thread that must
  * never call cudaMalloc/cudaFree (cudaFree can stall the whole device), or a

@@ -46,8 +46,13 @@ struct WsLayout {
 
 constexpr WsLayout ws_layout(uint64_t n) {
   WsLayout L;
+  // The dedup set probes linearly, and its longest probe sequence (a dependent
+  // key read and CAS per step) sets the dedup kernel's time: at load 1/2 about
+  // 30 steps for 32K keys, at 1/8 about 7. So m is a power of two of at least
+  // 8n up to 2^17 keys (at most 8 MB of set) and 4n above (at most 2^32).
   uint64_t m = 64;
-  while (m < 2 * n) m <<= 1;
+  const uint64_t want = n <= (1ull << 17) ? 8 * n : 4 * n;
+  while (m < want) m <<= 1;
   L.m = m;
   L.fix_cap = (uint32_t)(n < (1ull << 22) ? n : (1ull << 22)) + 64;
   size_t off = kAlign;  // counters

@@ -47,7 +47,7 @@ struct Workspace {
   unsigned long long* claim;  // [n] per key: (bucket << 32) | the ctrl bits its publication flips, or 0
                               // (the slot phase 1 claimed for it; written by phase 1 for every key)
   unsigned long long* fixup;  // [fix_cap] (table << 32 | bucket) whose moved counter fell to 0 off-lock
-  uint32_t m_mask;      // m - 1 (m a power of two >= 2n)
+  uint32_t m_mask;      // m - 1 (m a power of two >= 4n)
   uint32_t fix_cap;
 
   __device__ __forceinline__ uint32_t* first_at(uint32_t p) const { return set + 2 * (uint64_t)p; }
