@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t
 // Search budgets of the displacement passes after move1 (queue in shared
 // memory, at most 48 KB per block): the grid pass searches 96 buckets up to 4
 // moves deep, one thread per key (many keys, so the searches in flight matter
-// most); the second pass 192 buckets, 5 moves, and the last pass 2048 buckets,
+// most; a list of at most kGridWarpKeys keys runs one warp per key); the second pass 192 buckets, 5 moves, and the last pass 2048 buckets,
 // 6 moves, one warp per key (few keys, so the time of one search matters
 // most; the sequential CPU reference searches 1024 buckets, 5 moves). Each
 // later pass takes on at most kSecondPassKeys / kLastPassKeys keys, which
@@ -367,6 +367,9 @@ __global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t
 constexpr int kP2Threads = 64;
 constexpr uint32_t kSecondPassKeys = 65536;  // keys the second pass takes on
 constexpr uint32_t kLastPassKeys = 1024;     // keys the last pass takes on
+// A grid search list this short runs one warp per key: the slowest search sets
+// the pass's time, and a warp takes a level of a search in two round trips.
+constexpr uint32_t kGridWarpKeys = 1024;
 constexpr int kMaxDepth = 6;
 constexpr int kPathBuckets = kMaxDepth + 1;
 constexpr int kMaxLocks = kPathBuckets + 1;   // the path plus the key's primary
@@ -875,10 +878,9 @@ __global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint
 template <int kBfsNodes, int kBfsDepth>
 __device__ void phase2_range(const TableSet& ts, const uint8_t* __restrict__ keys, const uint64_t* __restrict__ vals,
                              uint32_t now, uint32_t expiry, uint8_t* __restrict__ status, const Workspace& ws,
-                             const uint32_t* list, const uint32_t* count_ptr, uint32_t* retry, uint32_t* retry_count,
+                             const uint32_t* list, uint32_t listed, uint32_t* retry, uint32_t* retry_count,
                              uint32_t max_keys, const Queue& q, uint32_t* seen, uint32_t worker, uint32_t workers) {
   static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
-  const uint32_t listed = ld32_cg(count_ptr);
   const uint32_t count = min(listed, max_keys);
   // A later pass searches wider but alone; when many keys reach it the table
   // is full rather than contended, and those beyond max_keys are FULL at once.
@@ -918,15 +920,15 @@ __device__ void phase2_range(const TableSet& ts, const uint8_t* __restrict__ key
 
 // phase2_range with one warp per key (bfs_warp): warp / warps are this warp's
 // index among the warps sharing the pass; q and seen are the warp's own.
+// listed: the list's length (read by the caller after the list was final).
 template <int kBfsNodes, int kBfsDepth>
 __device__ void phase2_range_warp(const TableSet& ts, const uint8_t* __restrict__ keys,
                                   const uint64_t* __restrict__ vals, uint32_t now, uint32_t expiry,
                                   uint8_t* __restrict__ status, const Workspace& ws, const uint32_t* list,
-                                  const uint32_t* count_ptr, uint32_t* retry, uint32_t* retry_count,
+                                  uint32_t listed, uint32_t* retry, uint32_t* retry_count,
                                   uint32_t max_keys, Node* q, uint32_t* seen, uint32_t warp, uint32_t warps) {
   static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t listed = ld32_cg(count_ptr);
   const uint32_t count = min(listed, max_keys);
   for (uint32_t j = count + warp * 32 + lane; j < listed; j += warps * 32) status[list[j]] = kStFull;
   for (uint32_t j = warp; j < count; j += warps) {
@@ -986,7 +988,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) insert_phase2_warp(TableSet ts
   __shared__ Node queues[kWarps][kBfsNodes];
   __shared__ uint32_t sets[kWarps][WarpSeen<kBfsNodes>::kSize];
   const uint32_t w = threadIdx.x >> 5;
-  phase2_range_warp<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, count_ptr, retry,
+  phase2_range_warp<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, ld32_cg(count_ptr), retry,
                                           retry_count, max_keys, queues[w], sets[w], blockIdx.x * kWarps + w,
                                           gridDim.x * kWarps);
 }
@@ -1004,10 +1006,25 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
   static_assert(kThreadsPerBlock * (kBfsNodes * sizeof(Node) + (kHashed ? SeenSet<kBfsNodes>::kSize * 4 : 0)) <=
                     48 * 1024,
                 "BFS state exceeds 48 KB");
-  __shared__ Node queues[kBfsNodes][kThreadsPerBlock];
+  static_assert(kThreadsPerBlock % 32 == 0 &&
+                    (kThreadsPerBlock / 32) * warp_search_bytes<kBfsNodes>() <= kBfsNodes * kThreadsPerBlock * sizeof(Node),
+                "the warp form's state does not fit in the queues");
+  __shared__ __align__(16) Node queues[kBfsNodes][kThreadsPerBlock];
+  const uint32_t listed = ld32_cg(count_ptr);
+  if (listed <= kGridWarpKeys) {
+    // a short list: one warp per key, each warp's queue and visited set carved from the block's queues
+    const uint32_t w = threadIdx.x >> 5;
+    uint8_t* mine = reinterpret_cast<uint8_t*>(&queues[0][0]) + w * warp_search_bytes<kBfsNodes>();
+    phase2_range_warp<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, listed, retry,
+                                            retry_count, max_keys, reinterpret_cast<Node*>(mine),
+                                            reinterpret_cast<uint32_t*>(mine + kBfsNodes * sizeof(Node)),
+                                            blockIdx.x * (kThreadsPerBlock / 32) + w,
+                                            gridDim.x * (kThreadsPerBlock / 32));
+    return;
+  }
   const Queue q{&queues[0][threadIdx.x], kThreadsPerBlock};
   uint32_t* seen = SeenStorage<kHashed, kThreadsPerBlock, SeenSet<kBfsNodes>::kSize>::get();
-  phase2_range<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, count_ptr, retry, retry_count,
+  phase2_range<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, listed, retry, retry_count,
                                      max_keys, q, seen, blockIdx.x * blockDim.x + threadIdx.x,
                                      gridDim.x * blockDim.x);
 }
@@ -1061,7 +1078,8 @@ __global__ void __launch_bounds__(kThreads) insert_fixup_finish(TableSet ts, uin
 // are resident at once (cooperative launch, grid sized by the occupancy the
 // kernel reaches), so the barrier cannot wait on a block that has not
 // started. Search queues live in 48 KB of dynamic shared memory per block: the
-// grid pass runs on 64 threads of every block (96 nodes each), the second pass
+// grid pass runs on 64 threads of every block (96 nodes each; on every warp
+// for a short list), the second pass
 // on every warp (192 nodes and a visited set each), the last on the first warp
 // of every block (2048 nodes and the visited set).
 constexpr int kSingleThreads = 256;
@@ -1072,6 +1090,8 @@ constexpr unsigned kSingleMinBlocks = 8;
 constexpr int kBarrierSpins = 1 << 22;
 
 static_assert(96 * 64 * sizeof(Node) <= kSingleSmem, "grid pass queues exceed the shared memory");
+static_assert((kSingleThreads / 32) * warp_search_bytes<96>() <= kSingleSmem,
+              "grid pass state (one warp per key) exceeds the shared memory");
 static_assert((kSingleThreads / 32) * warp_search_bytes<192>() <= kSingleSmem,
               "second pass state exceeds the shared memory");
 static_assert(warp_search_bytes<2048>() <= kSingleSmem, "last pass state exceeds the shared memory");
@@ -1138,19 +1158,25 @@ __global__ void __launch_bounds__(kSingleThreads, 2) insert_single_launch(TableS
     ok &= grid_barrier(bar_count, bar_gen);
   }
   Node* nodes = reinterpret_cast<Node*>(smem);
-  if (ld32_cg(ws.counters + 3)) {
-    if (threadIdx.x < 64) {
+  const uint32_t w = threadIdx.x >> 5;
+  if (const uint32_t listed = ld32_cg(ws.counters + 3)) {
+    if (listed <= kGridWarpKeys) {  // a short list: one warp per key
+      uint8_t* mine = smem + w * warp_search_bytes<96>();
+      phase2_range_warp<96, 4>(ts, keys, vals, now, expiry, status, ws, ws.retry, listed, ws.pending,
+                               ws.counters + 5, 0xFFFFFFFFu, reinterpret_cast<Node*>(mine),
+                               reinterpret_cast<uint32_t*>(mine + 96 * sizeof(Node)),
+                               blockIdx.x * (kSingleThreads / 32) + w, gridDim.x * (kSingleThreads / 32));
+    } else if (threadIdx.x < 64) {
       const Queue q{nodes + threadIdx.x, 64};
-      phase2_range<96, 4>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 3, ws.pending,
+      phase2_range<96, 4>(ts, keys, vals, now, expiry, status, ws, ws.retry, listed, ws.pending,
                           ws.counters + 5, 0xFFFFFFFFu, q, nullptr, blockIdx.x * 64 + threadIdx.x, gridDim.x * 64);
     }
     ok &= grid_barrier(bar_count, bar_gen);
   }
-  const uint32_t w = threadIdx.x >> 5;
   if (ld32_cg(ws.counters + 5)) {
     constexpr size_t kPer = warp_search_bytes<192>();
     uint8_t* mine = smem + w * kPer;
-    phase2_range_warp<192, 5>(ts, keys, vals, now, expiry, status, ws, ws.pending, ws.counters + 5, ws.retry,
+    phase2_range_warp<192, 5>(ts, keys, vals, now, expiry, status, ws, ws.pending, ld32_cg(ws.counters + 5), ws.retry,
                               ws.counters + 6, kSecondPassKeys, reinterpret_cast<Node*>(mine),
                               reinterpret_cast<uint32_t*>(mine + 192 * sizeof(Node)),
                               blockIdx.x * (kSingleThreads / 32) + w, gridDim.x * (kSingleThreads / 32));
@@ -1158,7 +1184,7 @@ __global__ void __launch_bounds__(kSingleThreads, 2) insert_single_launch(TableS
   }
   if (ld32_cg(ws.counters + 6)) {
     if (w == 0)
-      phase2_range_warp<2048, 6>(ts, keys, vals, now, expiry, status, ws, ws.retry, ws.counters + 6,
+      phase2_range_warp<2048, 6>(ts, keys, vals, now, expiry, status, ws, ws.retry, ld32_cg(ws.counters + 6),
                                  (uint32_t*)nullptr, (uint32_t*)nullptr, kLastPassKeys, nodes,
                                  reinterpret_cast<uint32_t*>(smem + 2048 * sizeof(Node)), blockIdx.x, gridDim.x);
     ok &= grid_barrier(bar_count, bar_gen);
