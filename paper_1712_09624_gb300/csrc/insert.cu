@@ -390,64 +390,22 @@ struct Queue {
   __device__ __forceinline__ Node& operator[](int i) const { return base[i * stride]; }
 };
 
-// Breadth-first search over buckets from b1 and b2 (lock-free reads; the path
-// is re-validated under its locks). Expanding a bucket issues the reads of its
-// control word and the keys of its 8 slots together (each entry's other bucket
-// takes one hash, chosen by its in_secondary bit), then the control-word (and
-// expiry) reads of the 8 buckets those entries can move to, so one level of
-// the search costs two memory round trips; a child with a free or dead slot ends the search (the
-// first such child in queue order, i.e. a shortest path). A bucket enters the
-// queue once: small searches test the queue itself, large ones an
-// open-addressing set of 2 x kBfsNodes bucket numbers (`seen`, shared memory).
-// Returns the node index of the bucket with the hole (in hole), or -1.
-template <int kBfsNodes>
-struct SeenSet {
-  static constexpr bool kHashed = kBfsNodes >= 512;
-  static constexpr uint32_t kSize = kHashed ? 2 * kBfsNodes : 1;
-  static_assert(!kHashed || (kSize & (kSize - 1)) == 0, "set size must be a power of two");
-};
-
-// Per-thread storage of the set, in shared memory; none for small searches.
-template <bool kHashed, int kThreadsPerBlock, uint32_t kSize>
-struct SeenStorage {
-  __device__ static uint32_t* get() {
-    __shared__ uint32_t sets[kThreadsPerBlock][kSize];
-    return sets[threadIdx.x];
-  }
-};
-template <int kThreadsPerBlock, uint32_t kSize>
-struct SeenStorage<false, kThreadsPerBlock, kSize> {
-  __device__ static uint32_t* get() { return nullptr; }
-};
-
-// Adds bucket b to the set; false if it was there already.
-template <int kBfsNodes>
-__device__ __forceinline__ bool seen_insert(uint32_t* seen, uint32_t b) {
-  constexpr uint32_t mask = SeenSet<kBfsNodes>::kSize - 1;
-  uint32_t h = (b * 0x9E3779B1u) & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    if (seen[h] == b) return false;
-    if (seen[h] == 0xFFFFFFFFu) {
-      seen[h] = b;
-      return true;
-    }
-    h = (h + 1) & mask;
-  }
-  return false;  // not reached: the set holds at most kBfsNodes of its 2 x kBfsNodes entries
-}
-
+// Breadth-first search over buckets from b1 and b2 by one thread (lock-free
+// reads; the path is re-validated under its locks). Expanding a bucket issues
+// the reads of its control word and the keys of its 8 slots together (each
+// entry's other bucket takes one hash, chosen by its in_secondary bit), then
+// the control-word (and expiry) reads of the 8 buckets those entries can move
+// to, so one level of the search costs two memory round trips; a child with a
+// free or dead slot ends the search (the first such child in queue order, i.e.
+// a shortest path). A bucket enters the queue once (the queue itself is the
+// visited set: this form runs small searches). Returns the node index of the
+// bucket with the hole (in hole), or -1.
 template <int kBfsNodes, int kBfsDepth>
-__device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue& q, uint32_t* seen,
-                    uint32_t& hole) {
-  constexpr bool kHashed = SeenSet<kBfsNodes>::kHashed;
+__device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue& q, uint32_t& hole) {
+  static_assert(kBfsNodes <= 256, "the thread form scans its queue for visited buckets");
   int nq = 0;
   q[nq++] = Node{a.b1, -1, 0, 0};
   q[nq++] = Node{a.b2, -1, 0, 0};
-  if (kHashed) {
-    for (uint32_t j = 0; j < SeenSet<kBfsNodes>::kSize; ++j) seen[j] = 0xFFFFFFFFu;
-    seen_insert<kBfsNodes>(seen, a.b1);
-    seen_insert<kBfsNodes>(seen, a.b2);
-  }
   // A hole is only ever found on a newly queued bucket, so the search ends
   // when the queue is full.
   for (int qi = 0; qi < nq && nq < kBfsNodes; ++qi) {
@@ -470,13 +428,8 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue&
       }
     }
     for (uint32_t sl = 0; sl < kSlots && nq < kBfsNodes; ++sl) {
-      bool fresh;
-      if (kHashed) {
-        fresh = seen_insert<kBfsNodes>(seen, y[sl]);
-      } else {
-        fresh = true;
-        for (int j = 0; j < nq; ++j) fresh &= (q[j].bucket != y[sl]);
-      }
+      bool fresh = true;
+      for (int j = 0; j < nq; ++j) fresh &= (q[j].bucket != y[sl]);
       if (!fresh) continue;
       q[nq] = Node{y[sl], (int16_t)qi, (uint8_t)sl, (uint8_t)(cur.depth + 1)};
       Snap s;
@@ -873,13 +826,12 @@ __global__ void __launch_bounds__(kThreads) insert_move1(TableSet ts, const uint
 
 // Displacement pass over `list` (count in *count). Keys that find no path
 // are appended to `retry` (when given) for a second, low-contention pass;
-// otherwise they are FULL. q: this thread's search queue; seen: its visited
-// set (searches of 512 nodes and more), or nullptr.
+// otherwise they are FULL. q: this thread's search queue.
 template <int kBfsNodes, int kBfsDepth>
 __device__ void phase2_range(const TableSet& ts, const uint8_t* __restrict__ keys, const uint64_t* __restrict__ vals,
                              uint32_t now, uint32_t expiry, uint8_t* __restrict__ status, const Workspace& ws,
                              const uint32_t* list, uint32_t listed, uint32_t* retry, uint32_t* retry_count,
-                             uint32_t max_keys, const Queue& q, uint32_t* seen, uint32_t worker, uint32_t workers) {
+                             uint32_t max_keys, const Queue& q, uint32_t worker, uint32_t workers) {
   static_assert(kBfsDepth <= kMaxDepth, "path longer than the lock set");
   const uint32_t count = min(listed, max_keys);
   // A later pass searches wider but alone; when many keys reach it the table
@@ -895,7 +847,7 @@ __device__ void phase2_range(const TableSet& ts, const uint8_t* __restrict__ key
     uint8_t st = kStFull;
     for (int attempt = 0; attempt < kPathAttempts; ++attempt) {
       uint32_t hole = 0;
-      const int end = bfs<kBfsNodes, kBfsDepth>(t, a, now, q, seen, hole);
+      const int end = bfs<kBfsNodes, kBfsDepth>(t, a, now, q, hole);
       if (end < 0) break;  // no cuckoo path within the search bound: FULL
       uint32_t path[kPathBuckets], slot[kPathBuckets];
       const int len = q[end].depth;
@@ -1002,10 +954,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
                                                                   uint32_t* retry_count, uint32_t max_keys) {
   pdl_wait();
   pdl_release();
-  constexpr bool kHashed = SeenSet<kBfsNodes>::kHashed;
-  static_assert(kThreadsPerBlock * (kBfsNodes * sizeof(Node) + (kHashed ? SeenSet<kBfsNodes>::kSize * 4 : 0)) <=
-                    48 * 1024,
-                "BFS state exceeds 48 KB");
+  static_assert(kThreadsPerBlock * kBfsNodes * sizeof(Node) <= 48 * 1024, "BFS state exceeds 48 KB");
   static_assert(kThreadsPerBlock % 32 == 0 &&
                     (kThreadsPerBlock / 32) * warp_search_bytes<kBfsNodes>() <= kBfsNodes * kThreadsPerBlock * sizeof(Node),
                 "the warp form's state does not fit in the queues");
@@ -1023,10 +972,8 @@ __global__ void __launch_bounds__(kThreadsPerBlock) insert_phase2(TableSet ts, c
     return;
   }
   const Queue q{&queues[0][threadIdx.x], kThreadsPerBlock};
-  uint32_t* seen = SeenStorage<kHashed, kThreadsPerBlock, SeenSet<kBfsNodes>::kSize>::get();
   phase2_range<kBfsNodes, kBfsDepth>(ts, keys, vals, now, expiry, status, ws, list, listed, retry, retry_count,
-                                     max_keys, q, seen, blockIdx.x * blockDim.x + threadIdx.x,
-                                     gridDim.x * blockDim.x);
+                                     max_keys, q, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ----------------------------------------------------- fixup and finish
@@ -1169,7 +1116,7 @@ __global__ void __launch_bounds__(kSingleThreads, 2) insert_single_launch(TableS
     } else if (threadIdx.x < 64) {
       const Queue q{nodes + threadIdx.x, 64};
       phase2_range<96, 4>(ts, keys, vals, now, expiry, status, ws, ws.retry, listed, ws.pending,
-                          ws.counters + 5, 0xFFFFFFFFu, q, nullptr, blockIdx.x * 64 + threadIdx.x, gridDim.x * 64);
+                          ws.counters + 5, 0xFFFFFFFFu, q, blockIdx.x * 64 + threadIdx.x, gridDim.x * 64);
     }
     ok &= grid_barrier(bar_count, bar_gen);
   }
