@@ -24,7 +24,8 @@
 //             path without locks (queue in shared memory), then lock every
 //             bucket of the path plus the key's primary, re-validate the path,
 //             and move the entries backwards and store the key, all under
-//             those locks; retry a bounded number of times. Keys still
+//             those locks; retry a bounded number of times. One thread per
+//             key, or one warp per key for a short list. Keys still
 //             unplaced get a wider search, then the widest, each run by a
 //             whole warp per key (a level of the search in two round trips);
 //             only then FULL.
@@ -351,9 +352,10 @@ __global__ void __launch_bounds__(kThreads) insert_publish(TableSet ts, uint64_t
 // Search budgets of the displacement passes after move1 (queue in shared
 // memory, at most 48 KB per block): the grid pass searches 96 buckets up to 4
 // moves deep, one thread per key (many keys, so the searches in flight matter
-// most; a list of at most kGridWarpKeys keys runs one warp per key); the second pass 192 buckets, 5 moves, and the last pass 2048 buckets,
-// 6 moves, one warp per key (few keys, so the time of one search matters
-// most; the sequential CPU reference searches 1024 buckets, 5 moves). Each
+// most; a list of at most kGridWarpKeys keys runs one warp per key); the
+// second pass 192 buckets, 5 moves, and the last pass 2048 buckets, 6 moves,
+// one warp per key (few keys, so the time of one search matters most; the
+// sequential CPU reference searches 1024 buckets, 5 moves). Each
 // later pass takes on at most kSecondPassKeys / kLastPassKeys keys, which
 // bounds the time a batch spends on a table that is full: the rest are FULL
 // without a search. Near LF 0.98 the second pass still places about two
