@@ -1320,7 +1320,7 @@ cudaError_t launch_insert(const TableSet& ts, const uint8_t* keys, const uint64_
                      0xFFFFFFFFu);
   if (e != cudaSuccess) return e;
   // second pass, one warp per key: the keys the grid pass could not place
-  e = launch_chained(insert_phase2_warp<8, 192, 5>, sms, 8 * 32, s, ts, keys, vals, now, expiry, status, ws,
+  e = launch_chained(insert_phase2_warp<8, 192, 5>, sms * 2, 8 * 32, s, ts, keys, vals, now, expiry, status, ws,
                      (const uint32_t*)ws.pending, (const uint32_t*)(ws.counters + 5), ws.retry, ws.counters + 6,
                      kSecondPassKeys);
   if (e != cudaSuccess) return e;
