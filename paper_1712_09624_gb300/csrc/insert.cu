@@ -399,12 +399,15 @@ struct Queue {
 // the control-word (and expiry) reads of the 8 buckets those entries can move
 // to, so one level of the search costs two memory round trips; a child with a
 // free or dead slot ends the search (the first such child in queue order, i.e.
-// a shortest path). A bucket enters the queue once (the queue itself is the
-// visited set: this form runs small searches). Returns the node index of the
-// bucket with the hole (in hole), or -1.
+// a shortest path). A child is not queued if it is one of the roots, a bucket
+// on its parent's path or an earlier sibling, so no path holds a bucket twice;
+// a bucket reached again by another branch takes a second queue node (a scan
+// of the whole queue for it cost more than the node: most repeats are an
+// entry's way back to the bucket it came from, which the path test catches).
+// Returns the node index of the bucket with the hole (in hole), or -1.
 template <int kBfsNodes, int kBfsDepth>
 __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue& q, uint32_t& hole) {
-  static_assert(kBfsNodes <= 256, "the thread form scans its queue for visited buckets");
+  static_assert(kBfsNodes < 32768, "parent index exceeds its field");
   int nq = 0;
   q[nq++] = Node{a.b1, -1, 0, 0};
   q[nq++] = Node{a.b2, -1, 0, 0};
@@ -429,10 +432,26 @@ __device__ int bfs(const TableView& t, const Addr& a, uint32_t now, const Queue&
         e0[sl] = e1[sl] = 0;
       }
     }
+    // children to skip: a root, a bucket on cur's path (cur and its ancestors), an earlier sibling
+    uint32_t path_b[kBfsDepth + 1];
+    int node = qi;
+#pragma unroll
+    for (int d = 0; d <= kBfsDepth; ++d) {
+      path_b[d] = node >= 0 ? q[node].bucket : a.b1;  // past the root: a root again, already tested
+      node = node >= 0 ? q[node].parent : -1;
+    }
+    uint32_t skip = 0;
+#pragma unroll
+    for (uint32_t sl = 0; sl < kSlots; ++sl) {
+      bool hit = y[sl] == a.b1 || y[sl] == a.b2;
+#pragma unroll
+      for (int d = 0; d <= kBfsDepth; ++d) hit |= path_b[d] == y[sl];
+#pragma unroll
+      for (uint32_t o = 0; o < sl; ++o) hit |= y[o] == y[sl];
+      skip |= (uint32_t)hit << sl;
+    }
     for (uint32_t sl = 0; sl < kSlots && nq < kBfsNodes; ++sl) {
-      bool fresh = true;
-      for (int j = 0; j < nq; ++j) fresh &= (q[j].bucket != y[sl]);
-      if (!fresh) continue;
+      if ((skip >> sl) & 1u) continue;
       q[nq] = Node{y[sl], (int16_t)qi, (uint8_t)sl, (uint8_t)(cur.depth + 1)};
       Snap s;
       s.e0 = e0[sl];
