@@ -69,7 +69,10 @@ def test_host_only_calls(K):
     wrong_slots = K.ckpp_geometry(1024, 4, 0, 0)
     assert K.ckpp_required_bytes(wrong_slots) == 0
     assert K.ckpp_workspace_bytes(0) > 0
-    assert K.ckpp_workspace_bytes(1 << 20) >= 8 * (1 << 21) + 8 * (1 << 20)
+    # the dedup set: 8 bytes per position, 8 positions per key up to 2^17 keys, 4 above
+    assert K.ckpp_workspace_bytes(1 << 20) >= 8 * (4 << 20) + 8 * (1 << 20)
+    assert K.ckpp_workspace_bytes(1 << 12) >= 8 * (8 << 12) + 8 * (1 << 12)
+    assert K.ckpp_workspace_bytes(1 << 30) >= 8 * (4 << 30)
     assert K.ckpp_workspace_bytes((1 << 30) + 1) == 0
     lib = K.library()
     assert lib.ckpp_error_string(-3).decode().startswith("more than 64512")
