@@ -61,7 +61,7 @@ class ServeConfig:
     duration_s: float = 0.2
     footprint_bytes: int = 256 << 20
     insert_flush_keys: int = 32768    # coalesced inserts go out once this many keys wait ...
-    insert_flush_s: float = 120e-6    # ... or the oldest has waited this long
+    insert_flush_s: float = 100e-6    # ... or the oldest has waited this long
     lookup_hold_s: float = 100e-6     # ... or a lookup held behind them has waited this long
     raw_fraction: float = 0.2         # share of lookup keys naming flows inserted earlier in the run
     max_inflight: int = 1             # turns queued on the device at most (0: no limit)
